@@ -1,0 +1,198 @@
+/*
+ * pnuc.h — C ABI of libpnuc: event-parallel Monte Carlo of non-elastic proton–nucleus
+ * interactions (20–250 MeV) on one GB300 GPU, after arXiv:1309.7963.
+ *
+ * One event = one incident proton on one target nucleus: an intranuclear cascade
+ * (paper §2.3) on a 15-shell Fermi-gas nucleus (§2.2, Eq. 1), then evaporation of
+ * n, p, d, t, 3He and alpha down to the residual nucleus (§2.4). Every event depends only
+ * on (seed, event id): its random numbers are the stream of Philox4x64-10 with key
+ * (seed, 0) and counters (j, event id, 0, 0), j = 0, 1, ... (the paper used CURAND
+ * states, §3.1).
+ *
+ * Conventions for every entry point:
+ *  - Pointers documented "device" must point to memory of the context's device (for
+ *    example tensors allocated by PyTorch); "host" pointers to host memory. The caller
+ *    owns all buffers it passes; the library never frees them.
+ *  - Functions return pnuc_status; PNUC_OK is 0. On error nothing is launched and
+ *    pnuc_last_error() gives a message. Argument checks happen on the host before any
+ *    launch.
+ *  - Launches are asynchronous on the caller's CUDA stream (cudaStream_t passed as
+ *    void*; NULL = the legacy default stream). Results are valid after that stream is
+ *    synchronised. A context is not thread-safe: use one context per host thread.
+ *  - Units: MeV, MeV/c, fm.
+ */
+#ifndef PNUC_H
+#define PNUC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PNUC_OK = 0,
+    PNUC_ERR_ARG = 1,      /* null pointer, bad enum, misaligned buffer, n too large */
+    PNUC_ERR_RANGE = 2,    /* (Z, A) outside the supported nuclei */
+    PNUC_ERR_CAPACITY = 3, /* a fixed-size resource is full (targets, output) */
+    PNUC_ERR_CUDA = 4,     /* a CUDA runtime call failed; see pnuc_last_error() */
+    PNUC_ERR_TIMEOUT = 5,  /* a bounded wait ran out */
+    PNUC_ERR_STATE = 6     /* call not valid in the object's current state */
+} pnuc_status;
+
+typedef enum {
+    PNUC_FP32 = 0, /* bulk transport, path and cross-section arithmetic in FP32; Lorentz
+                      boosts, energy/momentum bookkeeping and evaporation widths in FP64 */
+    PNUC_FP64 = 1  /* everything in FP64, no fused multiply-add: reproduces the CPU
+                      oracle event by event up to libm rounding */
+} pnuc_precision;
+
+typedef enum {
+    PNUC_PLAIN = 0,     /* one event per thread, one launch of n threads */
+    PNUC_PERSISTENT = 1 /* resident warps that refill finished lanes from a device queue */
+} pnuc_method;
+
+/* Secondary particle record, 32 bytes, 16-byte aligned array. */
+typedef struct {
+    uint32_t event;   /* index of the event in its batch (0 .. n-1) */
+    uint8_t species;  /* 0 n, 1 p, 2 d, 3 t, 4 3He, 5 alpha */
+    uint8_t origin;   /* 0 escaped from the cascade, 1 evaporated */
+    uint16_t index;   /* emission order within the event: cascade escapes, then evaporation */
+    double T;         /* lab kinetic energy, MeV */
+    float ux, uy, uz; /* lab direction (unit vector); the beam is along +z */
+    uint32_t reserved;
+} pnuc_secondary;
+
+/* Per-event residual record, 64 bytes. */
+typedef struct {
+    uint16_t Z_cascade, A_cascade; /* residual after the cascade */
+    uint16_t Z_final, A_final;     /* residual after evaporation */
+    uint16_t n_cascade;            /* secondaries escaped from the cascade */
+    uint16_t n_evaporated;         /* particles evaporated */
+    uint16_t n_collisions;         /* accepted (not Pauli-blocked) NN collisions */
+    uint16_t n_attempts;           /* entries drawn until the event was non-elastic */
+    uint32_t flags;                /* PNUC_FLAG_* */
+    uint32_t reserved;
+    double Estar_cascade;  /* excitation energy after the cascade (energy balance), MeV */
+    double Estar_final;    /* excitation left on the final residual, MeV */
+    float P_cascade[3];    /* momentum the static mean field took during the cascade, MeV/c */
+    float P_final[3];      /* recoil momentum of the final residual from evaporation, MeV/c */
+} pnuc_residual;
+
+#define PNUC_FLAG_BAD_INPUT 1u         /* energy outside [20, 250] MeV or unknown target id */
+#define PNUC_FLAG_ATTEMPT_CAP 2u       /* no non-elastic entry within max_attempts */
+#define PNUC_FLAG_STEP_CAP 4u          /* max_steps transport steps; particles in flight captured */
+#define PNUC_FLAG_STACK_OVERFLOW 8u    /* particle stack full; the particle was captured */
+#define PNUC_FLAG_BAD_RESIDUAL 16u     /* residual with Z < 1 or N < 1: no evaporation */
+#define PNUC_FLAG_NO_EXCITATION 32u    /* E* <= 0 after the cascade: no evaporation */
+#define PNUC_FLAG_EVAP_TRIAL_CAP 64u   /* emission-energy sampling gave up; evaporation stopped */
+#define PNUC_FLAG_EVAP_STEP_CAP 128u   /* max evaporation steps reached */
+#define PNUC_FLAG_OUTPUT_OVERFLOW 256u /* a secondary of this event did not fit the output */
+
+/* Work counters (optional output), summed over a batch. */
+enum {
+    PNUC_C_STEPS = 0, PNUC_C_CANDIDATES, PNUC_C_KINEMATICS, PNUC_C_PAULI_BLOCKED, PNUC_C_COLLISIONS,
+    PNUC_C_CROSSINGS, PNUC_C_REFLECTIONS, PNUC_C_ESCAPES, PNUC_C_CAPTURES, PNUC_C_ATTEMPTS,
+    PNUC_C_EVAP_STEPS, PNUC_C_EVAP_TRIALS, PNUC_C_DRAWS, PNUC_N_COUNTERS
+};
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal */
+    int32_t max_steps;         /* transport steps per event (default 100000) */
+    int32_t max_attempts;      /* entries per event until non-elastic (default 1000) */
+    int32_t max_evap_steps;    /* evaporation steps per event (default 64) */
+    int32_t max_evap_trials;   /* rejection trials per emission (default 10000) */
+} pnuc_config;
+
+/* One batch of incident protons. */
+typedef struct {
+    const double *energies;    /* device, n entries: incident kinetic energy, MeV */
+    const int32_t *target_ids; /* device, n entries: ids from pnuc_create_target */
+    uint64_t n;                /* events; at most 2^32 - 1 */
+    uint64_t seed;             /* Philox key word 0 */
+    uint64_t first_event_id;   /* event i of the batch has id first_event_id + i */
+} pnuc_batch;
+
+/* Where a batch's results go. */
+typedef struct {
+    pnuc_secondary *secondaries; /* device, capacity records, 16-byte aligned */
+    uint64_t capacity;
+    unsigned long long *count;   /* device, 1 entry: set to the number of secondaries the
+                                    batch produced, which may exceed capacity; records past
+                                    capacity are dropped and their events flagged
+                                    PNUC_FLAG_OUTPUT_OVERFLOW */
+    pnuc_residual *residuals;    /* device, n records (entry i = event i) */
+    unsigned long long *counters;/* device, PNUC_N_COUNTERS entries added to, or NULL */
+} pnuc_output;
+
+/* Launch tuning of the persistent method (the plain method uses block_size only). */
+typedef struct {
+    int32_t block_size;       /* threads per block: 64, 128, 256 or 512 */
+    int32_t blocks_per_sm;    /* resident blocks per SM for the persistent grid (<= occupancy) */
+    int32_t refill_threshold; /* a warp refills when at least this many lanes are idle (1..32) */
+    int32_t chunk;            /* events a warp takes from the queue per atomic (>= 32) */
+} pnuc_tuning;
+
+typedef struct pnuc_ctx pnuc_ctx;
+
+/* Fills *cfg with the defaults. */
+void pnuc_default_config(pnuc_config *cfg);
+
+/* Creates a context on cfg->device (cfg may be NULL for defaults): builds the nuclide mass
+ * table on the device (semi-empirical masses, §2.2). *out receives the context. */
+pnuc_status pnuc_create(const pnuc_config *cfg, pnuc_ctx **out);
+
+/* Releases the context and its device memory. Safe on NULL. */
+pnuc_status pnuc_destroy(pnuc_ctx *ctx);
+
+/* Human-readable name of a status; the last error message of a context. */
+const char *pnuc_status_string(pnuc_status s);
+pnuc_status pnuc_last_error(const pnuc_ctx *ctx, char *buf, size_t len);
+
+/* Builds the target table of nucleus (Z, A) on the device (§2.2, Eq. 1: 15-shell density
+ * steps of the Fermi distribution with c = 1.07 A^(1/3) fm, delta = 0.545 fm, radius
+ * c + 2.5 fm; two Fermi gases; potential = Fermi energy + SEMF separation energy; Coulomb
+ * barrier) and returns its id (0, 1, ...) in *target_id. Supported: 6 <= A <= 250,
+ * 2 <= Z <= 100, A - Z >= 2, positive SEMF separation energies (else PNUC_ERR_RANGE).
+ * At most 16 targets per context (PNUC_ERR_CAPACITY). Synchronous. Creating the same
+ * (Z, A) twice returns the existing id. */
+pnuc_status pnuc_create_target(pnuc_ctx *ctx, int32_t Z, int32_t A, int32_t *target_id);
+
+/* Host copy of a target table, for inspection (FP64 values as the kernels use them). */
+typedef struct {
+    int32_t Z, A;
+    double R, EC, M, S_n, S_p;
+    double r[16];
+    double rho[15], vF[15];
+    double pF[2][15], EF[2][15], V[2][15]; /* [0] neutrons, [1] protons */
+} pnuc_target_info;
+pnuc_status pnuc_target_table(pnuc_ctx *ctx, int32_t target_id, pnuc_target_info *out);
+
+/* Simulates batch->n events (the hot path: §2.3 cascade + §2.4 evaporation) with the
+ * given precision and method, writing out->residuals[0..n-1], the secondaries and
+ * *out->count. Asynchronous on stream. n = 0 writes *count = 0 and returns. Buffers must
+ * not overlap. Per-event problems are reported in residual flags, not in the status. */
+pnuc_status pnuc_simulate(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method,
+                          const pnuc_batch *batch, const pnuc_output *out, void *stream);
+
+/* pnuc_simulate with HOST buffers: energies/target_ids (host, n entries) are copied to
+ * device staging buffers the context owns (grown as needed), the batch runs, and the
+ * residuals (host, n entries), up to sec_capacity secondaries (host) and the produced
+ * count (host) are copied back. Synchronous: returns after the results are on the host.
+ * Returns PNUC_ERR_CAPACITY if *sec_count > sec_capacity (the first sec_capacity
+ * records are still written). */
+pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method,
+                               const double *energies, const int32_t *target_ids, uint64_t n,
+                               uint64_t seed, uint64_t first_event_id, pnuc_secondary *secondaries,
+                               uint64_t sec_capacity, uint64_t *sec_count, pnuc_residual *residuals,
+                               void *stream);
+
+/* Persistent-method tuning of the context (per precision). set checks the ranges above. */
+pnuc_status pnuc_get_tuning(const pnuc_ctx *ctx, pnuc_precision precision, pnuc_tuning *out);
+pnuc_status pnuc_set_tuning(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_tuning *t);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PNUC_H */

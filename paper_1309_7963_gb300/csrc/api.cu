@@ -1,0 +1,360 @@
+// Host side of the libpnuc C ABI (include/pnuc.h): contexts, target tables, batch
+// launches with device or host buffers, and launch tuning. All model arithmetic runs in
+// the kernels (tables.cu, kernel_fp32.cu, kernel_fp64.cu); this file checks arguments,
+// owns device-side tables and scratch, and orders the launches on the caller's stream.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pnuc_internal.h"
+
+using namespace pnuc;
+
+namespace {
+constexpr int kQueueSlots = 256;      // persistent launches of one context in flight at once
+constexpr int kQueueStride = 16;      // 128-byte spacing between queue heads
+}  // namespace
+
+struct pnuc_ctx {
+    pnuc_config cfg;
+    int sm_count = 0;
+    char err[512] = {0};
+    double *mass = nullptr;   // [kMassZ * kMassA]
+    double *cbrtA = nullptr;  // [kMassA]
+    TargetTable *tables = nullptr;  // [kMaxTargets]
+    std::vector<std::pair<int, int>> targets;
+    unsigned long long *queue = nullptr;  // [kQueueSlots * kQueueStride]
+    unsigned queue_next = 0;
+    pnuc_tuning tuning[2];
+    // staging for pnuc_simulate_host
+    double *h_energies = nullptr;
+    int32_t *h_tids = nullptr;
+    pnuc_residual *h_res = nullptr;
+    uint64_t h_events_cap = 0;
+    pnuc_secondary *h_sec = nullptr;
+    uint64_t h_sec_cap = 0;
+    unsigned long long *h_count = nullptr;
+};
+
+namespace {
+
+pnuc_status fail(pnuc_ctx *ctx, pnuc_status st, const char *fmt, ...)
+{
+    if (ctx) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(ctx->err, sizeof ctx->err, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+#define CU(ctx, call)                                                                                 \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(ctx, PNUC_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                          \
+    } while (0)
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t)
+{
+    if (!(t->block_size == 64 || t->block_size == 128 || t->block_size == 256 || t->block_size == 512))
+        return fail(ctx, PNUC_ERR_ARG, "block_size %d not in {64,128,256,512}", t->block_size);
+    if (t->blocks_per_sm < 1 || t->blocks_per_sm > 32)
+        return fail(ctx, PNUC_ERR_ARG, "blocks_per_sm %d not in [1,32]", t->blocks_per_sm);
+    if (t->refill_threshold < 1 || t->refill_threshold > 32)
+        return fail(ctx, PNUC_ERR_ARG, "refill_threshold %d not in [1,32]", t->refill_threshold);
+    if (t->chunk < 32 || t->chunk > (1 << 20))
+        return fail(ctx, PNUC_ERR_ARG, "chunk %d not in [32, 2^20]", t->chunk);
+    return PNUC_OK;
+}
+
+int occupancy(pnuc_precision prec, int block, bool count)
+{
+    return prec == PNUC_FP64 ? occupancy_persistent_fp64(block) : occupancy_persistent_fp32(block, count);
+}
+
+}  // namespace
+
+extern "C" {
+
+void pnuc_default_config(pnuc_config *cfg)
+{
+    if (!cfg) return;
+    cfg->device = 0;
+    cfg->max_steps = 100000;
+    cfg->max_attempts = 1000;
+    cfg->max_evap_steps = 64;
+    cfg->max_evap_trials = 10000;
+}
+
+const char *pnuc_status_string(pnuc_status s)
+{
+    switch (s) {
+    case PNUC_OK: return "ok";
+    case PNUC_ERR_ARG: return "invalid argument";
+    case PNUC_ERR_RANGE: return "out of range";
+    case PNUC_ERR_CAPACITY: return "capacity exceeded";
+    case PNUC_ERR_CUDA: return "CUDA error";
+    case PNUC_ERR_TIMEOUT: return "timeout";
+    case PNUC_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+pnuc_status pnuc_last_error(const pnuc_ctx *ctx, char *buf, size_t len)
+{
+    if (!ctx || !buf || len == 0) return PNUC_ERR_ARG;
+    snprintf(buf, len, "%s", ctx->err);
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
+{
+    if (!out) return PNUC_ERR_ARG;
+    *out = nullptr;
+    pnuc_config cfg;
+    pnuc_default_config(&cfg);
+    if (cfg_in) cfg = *cfg_in;
+    if (cfg.max_steps < 1 || cfg.max_attempts < 1 || cfg.max_evap_steps < 1 || cfg.max_evap_trials < 1)
+        return PNUC_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return PNUC_ERR_CUDA;
+    if (cfg.device < 0 || cfg.device >= ndev) return PNUC_ERR_ARG;
+    pnuc_ctx *ctx = new pnuc_ctx();
+    ctx->cfg = cfg;
+    pnuc_status st = PNUC_OK;
+    do {
+        if (cudaSetDevice(cfg.device) != cudaSuccess) { st = PNUC_ERR_CUDA; break; }
+        cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg.device);
+        if (cudaMalloc(&ctx->mass, sizeof(double) * kMassZ * kMassA) != cudaSuccess ||
+            cudaMalloc(&ctx->cbrtA, sizeof(double) * kMassA) != cudaSuccess ||
+            cudaMalloc(&ctx->tables, sizeof(TargetTable) * kMaxTargets) != cudaSuccess ||
+            cudaMalloc(&ctx->queue, sizeof(unsigned long long) * kQueueSlots * kQueueStride) != cudaSuccess) {
+            st = PNUC_ERR_CUDA;
+            break;
+        }
+        if (launch_mass_table(ctx->mass, ctx->cbrtA, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+            st = PNUC_ERR_CUDA;
+            break;
+        }
+        for (int p = 0; p < 2; ++p) {
+            pnuc_tuning &t = ctx->tuning[p];
+            t.block_size = 128;
+            t.refill_threshold = 8;
+            t.chunk = 256;
+            int occ = occupancy((pnuc_precision)p, t.block_size, false);
+            t.blocks_per_sm = occ > 0 ? occ : 1;
+        }
+    } while (0);
+    if (st != PNUC_OK) {
+        pnuc_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_destroy(pnuc_ctx *ctx)
+{
+    if (!ctx) return PNUC_OK;
+    cudaSetDevice(ctx->cfg.device);
+    cudaFree(ctx->mass);
+    cudaFree(ctx->cbrtA);
+    cudaFree(ctx->tables);
+    cudaFree(ctx->queue);
+    cudaFree(ctx->h_energies);
+    cudaFree(ctx->h_tids);
+    cudaFree(ctx->h_res);
+    cudaFree(ctx->h_sec);
+    cudaFree(ctx->h_count);
+    delete ctx;
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_create_target(pnuc_ctx *ctx, int32_t Z, int32_t A, int32_t *target_id)
+{
+    if (!ctx || !target_id) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    for (size_t k = 0; k < ctx->targets.size(); ++k)
+        if (ctx->targets[k].first == Z && ctx->targets[k].second == A) {
+            *target_id = (int32_t)k;
+            return PNUC_OK;
+        }
+    if (A < 6 || A > 250 || Z < 2 || A - Z < 2 || Z > 100)
+        return fail(ctx, PNUC_ERR_RANGE, "target Z=%d A=%d outside 6<=A<=250, 2<=Z<=100, A-Z>=2", Z, A);
+    if ((int)ctx->targets.size() >= kMaxTargets)
+        return fail(ctx, PNUC_ERR_CAPACITY, "at most %d targets per context", kMaxTargets);
+    CU(ctx, cudaSetDevice(ctx->cfg.device));
+    int id = (int)ctx->targets.size();
+    CU(ctx, launch_target_table(ctx->tables + id, Z, A, ctx->mass, 0));
+    CU(ctx, cudaDeviceSynchronize());
+    int32_t valid = 0;
+    CU(ctx, cudaMemcpy(&valid, &ctx->tables[id].valid, sizeof valid, cudaMemcpyDeviceToHost));
+    if (!valid) return fail(ctx, PNUC_ERR_RANGE, "target Z=%d A=%d has a non-positive separation energy", Z, A);
+    ctx->targets.push_back({Z, A});
+    *target_id = id;
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_target_table(pnuc_ctx *ctx, int32_t target_id, pnuc_target_info *out)
+{
+    if (!ctx || !out) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    if (target_id < 0 || target_id >= (int)ctx->targets.size())
+        return fail(ctx, PNUC_ERR_ARG, "unknown target id %d", target_id);
+    CU(ctx, cudaSetDevice(ctx->cfg.device));
+    TargetTable t;
+    CU(ctx, cudaMemcpy(&t, ctx->tables + target_id, sizeof t, cudaMemcpyDeviceToHost));
+    out->Z = t.Z;
+    out->A = t.A;
+    out->R = t.R;
+    out->EC = t.d.EC;
+    out->M = t.M;
+    out->S_n = t.S[0];
+    out->S_p = t.S[1];
+    memcpy(out->r, t.d.r, sizeof out->r);
+    memcpy(out->rho, t.d.rho, sizeof out->rho);
+    memcpy(out->vF, t.d.vF, sizeof out->vF);
+    memcpy(out->pF, t.d.pF, sizeof out->pF);
+    memcpy(out->EF, t.d.EF, sizeof out->EF);
+    memcpy(out->V, t.d.V, sizeof out->V);
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_get_tuning(const pnuc_ctx *ctx, pnuc_precision precision, pnuc_tuning *out)
+{
+    if (!ctx || !out || (precision != PNUC_FP32 && precision != PNUC_FP64)) return PNUC_ERR_ARG;
+    *out = ctx->tuning[precision];
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_set_tuning(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_tuning *t)
+{
+    if (!ctx || !t || (precision != PNUC_FP32 && precision != PNUC_FP64)) return fail(ctx, PNUC_ERR_ARG, "bad argument");
+    pnuc_status st = check_tuning(ctx, t);
+    if (st != PNUC_OK) return st;
+    ctx->tuning[precision] = *t;
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_simulate(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
+                          const pnuc_output *out, void *stream)
+{
+    if (!ctx || !batch || !out) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    if (precision != PNUC_FP32 && precision != PNUC_FP64) return fail(ctx, PNUC_ERR_ARG, "bad precision %d", precision);
+    if (method != PNUC_PLAIN && method != PNUC_PERSISTENT) return fail(ctx, PNUC_ERR_ARG, "bad method %d", method);
+    if (batch->n > 0xFFFFFFFFull) return fail(ctx, PNUC_ERR_ARG, "n = %llu exceeds 2^32-1", (unsigned long long)batch->n);
+    if (!out->count) return fail(ctx, PNUC_ERR_ARG, "out->count is null");
+    if (batch->n > 0 && (!batch->energies || !batch->target_ids || !out->residuals))
+        return fail(ctx, PNUC_ERR_ARG, "null energies, target_ids or residuals");
+    if (out->capacity > 0 && !out->secondaries) return fail(ctx, PNUC_ERR_ARG, "null secondaries with capacity > 0");
+    if (!aligned16(out->secondaries) || !aligned16(out->residuals))
+        return fail(ctx, PNUC_ERR_ARG, "secondaries and residuals must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(ctx, cudaSetDevice(ctx->cfg.device));
+    CU(ctx, cudaMemsetAsync(out->count, 0, sizeof(unsigned long long), s));
+    if (batch->n == 0) return PNUC_OK;
+    SimParams p;
+    p.energies = batch->energies;
+    p.target_ids = batch->target_ids;
+    p.n = batch->n;
+    p.seed = batch->seed;
+    p.first_event_id = batch->first_event_id;
+    p.sec = out->secondaries;
+    p.sec_cap = out->secondaries ? out->capacity : 0;
+    p.sec_count = out->count;
+    p.res = out->residuals;
+    p.counters = out->counters;
+    p.tables = ctx->tables;
+    p.n_targets = (int32_t)ctx->targets.size();
+    p.mass = ctx->mass;
+    p.cbrtA = ctx->cbrtA;
+    p.max_steps = ctx->cfg.max_steps;
+    p.max_attempts = ctx->cfg.max_attempts;
+    p.max_evap_steps = ctx->cfg.max_evap_steps;
+    p.max_evap_trials = ctx->cfg.max_evap_trials;
+    const pnuc_tuning &t = ctx->tuning[precision];
+    p.refill_threshold = t.refill_threshold;
+    p.chunk = t.chunk;
+    p.queue_head = nullptr;
+    const bool count = out->counters != nullptr;
+    cudaError_t e;
+    if (method == PNUC_PLAIN) {
+        e = precision == PNUC_FP64 ? launch_plain_fp64(p, t.block_size, s)
+                                   : launch_plain_fp32(p, t.block_size, count, s);
+    } else {
+        int occ = occupancy(precision, t.block_size, count);
+        int bps = std::min(t.blocks_per_sm, std::max(occ, 1));
+        unsigned long long grid = (unsigned long long)bps * ctx->sm_count;
+        unsigned long long need = (batch->n + t.block_size - 1) / t.block_size;
+        if (grid > need) grid = need;
+        p.queue_head = ctx->queue + (size_t)(ctx->queue_next++ % kQueueSlots) * kQueueStride;
+        CU(ctx, cudaMemsetAsync(p.queue_head, 0, sizeof(unsigned long long), s));
+        e = precision == PNUC_FP64 ? launch_persistent_fp64(p, (int)grid, t.block_size, s)
+                                   : launch_persistent_fp32(p, (int)grid, t.block_size, count, s);
+    }
+    if (e != cudaSuccess) return fail(ctx, PNUC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const double *energies,
+                               const int32_t *target_ids, uint64_t n, uint64_t seed, uint64_t first_event_id,
+                               pnuc_secondary *secondaries, uint64_t sec_capacity, uint64_t *sec_count,
+                               pnuc_residual *residuals, void *stream)
+{
+    if (!ctx || !sec_count) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    if (n > 0 && (!energies || !target_ids || !residuals)) return fail(ctx, PNUC_ERR_ARG, "null input/output");
+    if (sec_capacity > 0 && !secondaries) return fail(ctx, PNUC_ERR_ARG, "null secondaries with capacity > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    CU(ctx, cudaSetDevice(ctx->cfg.device));
+    if (n > ctx->h_events_cap) {
+        cudaFree(ctx->h_energies);
+        cudaFree(ctx->h_tids);
+        cudaFree(ctx->h_res);
+        ctx->h_energies = nullptr;
+        ctx->h_tids = nullptr;
+        ctx->h_res = nullptr;
+        ctx->h_events_cap = 0;
+        CU(ctx, cudaMalloc(&ctx->h_energies, sizeof(double) * n));
+        CU(ctx, cudaMalloc(&ctx->h_tids, sizeof(int32_t) * n));
+        CU(ctx, cudaMalloc(&ctx->h_res, sizeof(pnuc_residual) * n));
+        ctx->h_events_cap = n;
+    }
+    if (sec_capacity > ctx->h_sec_cap) {
+        cudaFree(ctx->h_sec);
+        ctx->h_sec = nullptr;
+        ctx->h_sec_cap = 0;
+        CU(ctx, cudaMalloc(&ctx->h_sec, sizeof(pnuc_secondary) * sec_capacity));
+        ctx->h_sec_cap = sec_capacity;
+    }
+    if (!ctx->h_count) CU(ctx, cudaMalloc(&ctx->h_count, sizeof(unsigned long long)));
+    if (n > 0) {
+        CU(ctx, cudaMemcpyAsync(ctx->h_energies, energies, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CU(ctx, cudaMemcpyAsync(ctx->h_tids, target_ids, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    }
+    pnuc_batch b = {ctx->h_energies, ctx->h_tids, n, seed, first_event_id};
+    pnuc_output o = {ctx->h_sec, sec_capacity, ctx->h_count, ctx->h_res, nullptr};
+    pnuc_status st = pnuc_simulate(ctx, precision, method, &b, &o, stream);
+    if (st != PNUC_OK) return st;
+    unsigned long long cnt = 0;
+    CU(ctx, cudaMemcpyAsync(&cnt, ctx->h_count, sizeof cnt, cudaMemcpyDeviceToHost, s));
+    if (n > 0) CU(ctx, cudaMemcpyAsync(residuals, ctx->h_res, sizeof(pnuc_residual) * n, cudaMemcpyDeviceToHost, s));
+    CU(ctx, cudaStreamSynchronize(s));
+    uint64_t ncopy = cnt < sec_capacity ? cnt : sec_capacity;
+    if (ncopy > 0) {
+        CU(ctx, cudaMemcpyAsync(secondaries, ctx->h_sec, sizeof(pnuc_secondary) * ncopy, cudaMemcpyDeviceToHost, s));
+        CU(ctx, cudaStreamSynchronize(s));
+    }
+    *sec_count = cnt;
+    if (cnt > sec_capacity)
+        return fail(ctx, PNUC_ERR_CAPACITY, "batch produced %llu secondaries, capacity %llu", cnt,
+                    (unsigned long long)sec_capacity);
+    return PNUC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,18 @@
+// FP64 deterministic mode: every step in double precision, compiled with --fmad=false so
+// that the arithmetic is the plain IEEE sequence of the CPU oracle (results differ only
+// where CUDA's and the host's libm round transcendental functions differently).
+#include "pnuc_kernels.cuh"
+
+namespace pnuc {
+
+cudaError_t launch_plain_fp64(const SimParams &p, int block, cudaStream_t s)
+{
+    return dev::launch_plain<double, true>(p, block, s);
+}
+cudaError_t launch_persistent_fp64(const SimParams &p, int grid, int block, cudaStream_t s)
+{
+    return dev::launch_persistent<double, true>(p, grid, block, s);
+}
+int occupancy_persistent_fp64(int block) { return dev::occupancy_persistent<double, true>(block); }
+
+}  // namespace pnuc

@@ -1,0 +1,796 @@
+// Device-side model of one event (paper §2): nucleon transport through the 15-shell
+// nucleus by delta tracking, NN collisions with Pauli blocking, cutoff and refraction,
+// energy-balance excitation, then Weisskopf–Ewing evaporation. Written as a per-lane
+// state machine so that the plain kernel (one event per thread) and the persistent
+// kernel (warps refilling finished lanes) run the same steps.
+//
+// Precision: R = double reproduces the CPU oracle event by event (compiled without FMA
+// contraction); R = float keeps transport, paths and cross sections in FP32 while the
+// Lorentz boosts, the event's energy/momentum bookkeeping and the evaporation widths stay
+// FP64.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "pnuc_internal.h"
+
+namespace pnuc {
+namespace dev {
+namespace {  // internal linkage: each kernel translation unit has its own copy
+
+namespace cg = cooperative_groups;
+
+constexpr double kE2 = 1.44;  // e^2, MeV fm
+constexpr double kMp = 938.272, kMn = 939.565;
+constexpr double kTwoPi = 6.283185307179586;
+
+// ejectiles n, p, d, t, 3He, alpha (§2.4: He and lighter)
+__constant__ double cEjM[6] = {939.565, 938.272, 1875.613, 2808.921, 2808.391, 3727.379};
+__constant__ double cEjG[6] = {2.0, 2.0, 3.0, 2.0, 2.0, 1.0};
+__constant__ int cEjZ[6] = {0, 1, 1, 1, 2, 2};
+__constant__ int cEjA[6] = {1, 1, 2, 3, 3, 4};
+
+enum Phase : int { kIdle = 0, kEntry = 1, kTransport = 2, kEvap = 3, kFinish = 4, kExhausted = 5 };
+
+// ------------------------------------------------------------------ Philox4x64-10
+// Salmon et al., SC'11: ten rounds, multipliers and Weyl key increments of the paper.
+__device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t k0, uint64_t k1, uint64_t &o0,
+                                              uint64_t &o1, uint64_t &o2, uint64_t &o3)
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    uint64_t c2 = 0, c3 = 0;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B97F4A7C15ULL;
+            k1 += 0xBB67AE8584CAA73BULL;
+        }
+        uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    o0 = c0;
+    o1 = c1;
+    o2 = c2;
+    o3 = c3;
+}
+
+template <typename R> __device__ __forceinline__ R to_uniform(uint64_t w);
+template <> __device__ __forceinline__ double to_uniform<double>(uint64_t w)
+{
+    return ((double)(w >> 12) + 0.5) * 0x1p-52;  // 52 bits + 1/2: exact, open interval
+}
+template <> __device__ __forceinline__ float to_uniform<float>(uint64_t w)
+{
+    return ((float)(uint32_t)(w >> 41) + 0.5f) * 0x1p-23f;  // 23 bits + 1/2: exact, open interval
+}
+
+// The event's draw stream: draw d is word d mod 4 of Philox((d div 4, event, 0, 0),
+// (seed, 0)). Four converted words are kept in registers and shifted out in order.
+template <typename R>
+struct Stream {
+    uint64_t seed, event;
+    uint32_t block;
+    int left;
+    R q0, q1, q2, q3;
+    __device__ void reset(uint64_t s, uint64_t e)
+    {
+        seed = s;
+        event = e;
+        block = 0;
+        left = 0;
+    }
+    __device__ R next()
+    {
+        if (left == 0) {
+            uint64_t w0, w1, w2, w3;
+            philox4x64_10(block, event, seed, 0, w0, w1, w2, w3);
+            ++block;
+            q0 = to_uniform<R>(w0);
+            q1 = to_uniform<R>(w1);
+            q2 = to_uniform<R>(w2);
+            q3 = to_uniform<R>(w3);
+            left = 4;
+        }
+        R u = q0;
+        q0 = q1;
+        q1 = q2;
+        q2 = q3;
+        --left;
+        return u;
+    }
+};
+
+// ------------------------------------------------------------------ small helpers
+template <typename R> __device__ __forceinline__ R dot3(const R *a, const R *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+// kinetic energy from |p|^2 without cancellation
+template <typename R> __device__ __forceinline__ R kinetic(R p2, R m) { return p2 / (sqrt(p2 + m * m) + m); }
+__device__ __forceinline__ double nucleon_mass(int s) { return s ? kMp : kMn; }
+
+// ------------------------------------------------------------------ NN cross sections (§2.3, Cugnon et al.)
+template <typename R> __device__ __forceinline__ R clamp_p(R p) { return p < R(0.1) ? R(0.1) : (p > R(2.0) ? R(2.0) : p); }
+
+template <typename R>
+__device__ R sigma_nn(bool like, R p)  // p in GeV/c -> mb
+{
+    p = clamp_p(p);
+    if (like) {
+        if (p < R(0.44)) return R(34.0) * pow(p / R(0.4), R(-2.104));
+        if (p < R(0.8)) {
+            R d = p - R(0.7);
+            return R(23.5) + R(1000.0) * d * d * d * d;
+        }
+        R d = p - R(1.3);
+        return R(1250.0) / (p + R(50.0)) - R(4.0) * d * d;
+    }
+    if (p < R(0.8)) return R(33.0) + R(196.0) * pow(fabs(p - R(0.95)), R(2.5));
+    return R(31.0) / sqrt(p);
+}
+
+__device__ double slope_nn(bool like, double p)  // (GeV/c)^-2
+{
+    if (like) {
+        double p8 = p * p;
+        p8 = p8 * p8;
+        p8 = p8 * p8;
+        return 5.5 * p8 / (7.7 + p8);
+    }
+    if (p < 0.225) return 0.0;
+    if (p < 0.6) return 16.53 * (p - 0.225);
+    if (p < 1.6) return 7.16 - 1.63 * p;
+    return 4.552;
+}
+
+// Majorant of sigma * v_rel * E1 (GeV mb) over the shell's Fermi partners (v <= vF):
+// p_lab lies in [p_lo, p_hi] and sigma v_rel E1 <= p_lab sigma(p_lab), bounded piecewise.
+template <typename R>
+__device__ R g_hat(R p1, R E1, R vF)
+{
+    R plo = (p1 - vF * E1) * R(1e-3);
+    if (plo < R(0)) plo = R(0);
+    R phi = (p1 + vF * E1) * R(1e-3) / sqrt((R(1) - vF) * (R(1) + vF));
+    R pc = clamp_p(plo);
+    R glo = pc < R(0.44) ? pc * sigma_nn<R>(true, pc) : R(0);
+    R ph = phi > R(0.8) ? phi : R(0.8);
+    R g1 = R(28.1) * ph;
+    R g2 = R(31.0) * ph / sqrt(ph < R(2.0) ? ph : R(2.0));
+    R g = R(31.0);
+    if (glo > g) g = glo;
+    if (g1 > g) g = g1;
+    if (g2 > g) g = g2;
+    return g;
+}
+
+// ------------------------------------------------------------------ geometry (§2.3)
+// Distance to the boundary of shell i along unit d; dir = -1 inward, +1 outward.
+template <typename R>
+__device__ R boundary_distance(const ShellTable<R> &t, int shell, const R *r, const R *d, int &dir)
+{
+    R beta = dot3(r, d), q = dot3(r, r);
+    if (shell > 0 && beta < R(0)) {
+        R ri = t.r[shell];
+        R c = q - ri * ri, D = beta * beta - c;
+        if (D > R(0)) {
+            dir = -1;
+            R s = c / (-beta + sqrt(D));
+            return s > R(0) ? s : R(0);
+        }
+    }
+    R ro = t.r[shell + 1];
+    R c = q - ro * ro, D = beta * beta - c;
+    if (D < R(0)) D = R(0);
+    dir = 1;
+    if (beta <= R(0)) return -beta + sqrt(D);
+    R s = -c / (beta + sqrt(D));
+    return s > R(0) ? s : R(0);
+}
+
+// Potential step (after Chen et al.): kinetic energy changes by dT at fixed tangential
+// momentum; reflection when that is impossible. Returns true if refracted.
+template <typename R>
+__device__ bool refract(const R *n, R *p, R m, R dT)
+{
+    R pp = dot3(p, p);
+    R T = kinetic(pp, m), Tn = T + dT;
+    R pn = dot3(p, n);
+    R q2 = pn * pn + (Tn - T) * (Tn + T + R(2) * m);
+    if (Tn <= R(0) || q2 <= R(0)) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) p[k] -= R(2) * pn * n[k];
+        return false;
+    }
+    R pnn = (pn >= R(0) ? R(1) : R(-1)) * sqrt(q2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] += (pnn - pn) * n[k];
+    return true;
+}
+
+// ------------------------------------------------------------------ NN collision kinematics (FP64)
+__device__ void boost(const double *beta, double gamma, double sign, double e, const double *p, double *po)
+{
+    double bp = dot3(beta, p);
+    double g2 = gamma * gamma / (gamma + 1.0);
+    double f = g2 * bp + sign * gamma * e;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) po[k] = p[k] + beta[k] * f;
+}
+
+__device__ void rotate(const double *n, double ct, double st, double phi, double *d)
+{
+    double rho = sqrt(n[0] * n[0] + n[1] * n[1]);
+    double sp, cp;
+    sincos(phi, &sp, &cp);
+    if (rho > 0.0) {
+        double e1x = n[0] * n[2] / rho, e1y = n[1] * n[2] / rho, e1z = -rho;
+        double e2x = -n[1] / rho, e2y = n[0] / rho;
+        d[0] = ct * n[0] + st * (cp * e1x + sp * e2x);
+        d[1] = ct * n[1] + st * (cp * e1y + sp * e2y);
+        d[2] = ct * n[2] + st * (cp * e1z + sp * 0.0);
+    } else {
+        d[0] = st * cp;
+        d[1] = st * sp;
+        d[2] = (n[2] >= 0.0 ? 1.0 : -1.0) * ct;
+    }
+}
+
+// Elastic collision of (s1, p1) on (s2, p2), relativistic; uniforms for t, phi*, flip.
+__device__ void collide(int s1, const double *p1, int s2, const double *p2, double ut, double uphi, double uf,
+                        double *q1, double *q2)
+{
+    double m1 = nucleon_mass(s1), m2 = nucleon_mass(s2);
+    bool like = s1 == s2;
+    double pp1 = dot3(p1, p1), pp2 = dot3(p2, p2);
+    double E1 = sqrt(pp1 + m1 * m1), E2 = sqrt(pp2 + m2 * m2);
+    double T1 = kinetic(pp1, m1), T2 = kinetic(pp2, m2);
+    double X = T1 * T2 + T1 * m2 + T2 * m1 - dot3(p1, p2);
+    if (X < 0.0) X = 0.0;
+    double k = sqrt(X * (X + 2.0 * m1 * m2));
+    double plab = k / m2;
+    double rs = sqrt((m1 + m2) * (m1 + m2) + 2.0 * X);
+    double pst = k / rs;
+    double Et = E1 + E2;
+    double beta[3] = {(p1[0] + p2[0]) / Et, (p1[1] + p2[1]) / Et, (p1[2] + p2[2]) / Et};
+    double gamma = Et / rs;
+    double p1c[3];
+    boost(beta, gamma, -1.0, E1, p1, p1c);
+    double nrm = sqrt(dot3(p1c, p1c));
+    double n[3] = {p1c[0] / nrm, p1c[1] / nrm, p1c[2] / nrm};
+    double B = slope_nn(like, plab * 1e-3);
+    double pg = pst * 1e-3;
+    double b = 4.0 * B * pg * pg;
+    double y = b > 0.0 ? -log1p(ut * expm1(-b)) / b : ut;
+    double ct = 1.0 - 2.0 * y;
+    if (!like) {
+        double pl = plab * 1e-3;
+        double a = pl <= 0.8 ? 1.0 : (0.8 / pl) * (0.8 / pl);
+        if (uf < a / (1.0 + a)) ct = -ct;
+    }
+    double st = sqrt((1.0 - ct) * (1.0 + ct));
+    double d[3];
+    rotate(n, ct, st, kTwoPi * uphi, d);
+    double k1[3] = {pst * d[0], pst * d[1], pst * d[2]};
+    double k2[3] = {-k1[0], -k1[1], -k1[2]};
+    double e1 = sqrt(pst * pst + m1 * m1), e2 = sqrt(pst * pst + m2 * m2);
+    boost(beta, gamma, 1.0, e1, k1, q1);
+    boost(beta, gamma, 1.0, e2, k2, q2);
+}
+
+// ------------------------------------------------------------------ evaporation (§2.4, FP64 widths)
+// F(x) = e^x (x^2 - 3x + 3) + x^2/2 - 3, G(x) = e^x (x - 1) + 1; series below x = 1.
+__device__ void width_FG(double x, double &F, double &G)
+{
+    if (x >= 1.0) {
+        double ex = exp(x);
+        F = ex * (x * x - 3.0 * x + 3.0) + 0.5 * x * x - 3.0;
+        G = ex * (x - 1.0) + 1.0;
+        return;
+    }
+    double term = x, f = 0.0, g = 0.0;  // term = x^n / n!
+#pragma unroll
+    for (int n = 2; n <= 20; ++n) {
+        term *= x / n;
+        g += (double)(n - 1) * term;
+        if (n >= 4) f += (double)((n - 1) * (n - 3)) * term;
+    }
+    F = f;
+    G = g;
+}
+
+struct Channel {
+    double width, V, b, Q, Md, a, x;
+};
+
+// Width and parameters of ejectile j from parent (Z, A, Estar); Mparent from the table.
+__device__ void channel(const SimParams &P, int Z, int A, double Mparent, double Estar, int j, Channel &c)
+{
+    c.width = 0.0;
+    c.x = 0.0;
+    int Zd = Z - cEjZ[j], Ad = A - cEjA[j];
+    if (Zd < 1 || Ad - Zd < 1 || Ad < 5) return;
+    double Md = __ldg(&P.mass[Zd * kMassA + Ad]);
+    double Q = Md + cEjM[j] - Mparent;
+    double A3 = __ldg(&P.cbrtA[Ad]);
+    double V, b, cj;
+    if (cEjZ[j] == 0) {
+        double alpha = 0.76 + 1.93 / A3;
+        double beta = (1.66 / (A3 * A3) - 0.05) / alpha;
+        V = beta < 0.0 ? -beta : 0.0;
+        b = beta > 0.0 ? beta : 0.0;
+        cj = alpha;
+    } else {
+        V = kE2 * cEjZ[j] * Zd / (1.5 * (__ldg(&P.cbrtA[cEjA[j]]) + A3));
+        b = 0.0;
+        cj = 1.0;
+    }
+    double X = Estar - Q, Y = X - V;
+    c.V = V;
+    c.b = b;
+    c.Q = Q;
+    c.Md = Md;
+    double a = Ad / 8.0;
+    c.a = a;
+    if (!(Y > 0.0)) return;
+    double x = 2.0 * sqrt(a * Y);
+    c.x = x;
+    double F, G;
+    width_FG(x, F, G);
+    double I = F / (4.0 * a * a) + b * G / (2.0 * a);
+    c.width = cEjG[j] * cEjM[j] * cj * (A3 * A3) * I;
+}
+
+// ------------------------------------------------------------------ per-lane state
+// Per-target scalars the steps need, staged in shared memory beside the shell tables.
+struct TargetScalars {
+    double M;  // SEMF mass of the target, MeV
+    double R;  // nuclear radius, fm
+    int32_t Z, A;
+};
+
+template <typename R>
+struct Particle {
+    R r[3], p[3];
+    int s, shell;
+};
+
+template <typename R>
+struct Lane {
+    Stream<R> rng;
+    uint32_t ev;
+    int tgt;
+    int phase;
+    double T0;
+    // particle in flight
+    R r[3], p[3];
+    int s, shell, sp;
+    // event bookkeeping (FP64)
+    int steps, attempts, n_coll, n_index, n_esc, n_p_esc, n_evap;
+    uint32_t flags;
+    double Esum, Px, Py, Pz;
+    // residual / evaporation
+    int Z, A, Zc, Ac;
+    double Estar, Estar_c, Er, Prx, Pry, Prz;
+};
+
+template <bool kCount>
+struct Counters {
+    unsigned long long *s;  // shared-memory block counters
+    __device__ void add(int k, unsigned v = 1)
+    {
+        if (kCount) atomicAdd(&s[k], (unsigned long long)v);
+    }
+};
+
+// Warp-aggregated reservation of one output slot per calling lane: one atomic per
+// converged group, then 2 x 16-byte stores of the 32-byte record.
+__device__ __forceinline__ void emit_secondary(const SimParams &P, uint32_t ev, int species, int origin, int index,
+                                               double T, float ux, float uy, float uz, uint32_t &flags)
+{
+    cg::coalesced_group g = cg::coalesced_threads();
+    unsigned long long base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(P.sec_count, (unsigned long long)g.size());
+    base = g.shfl(base, 0);
+    unsigned long long slot = base + g.thread_rank();
+    if (slot >= P.sec_cap) {
+        flags |= PNUC_FLAG_OUTPUT_OVERFLOW;
+        return;
+    }
+    unsigned long long tbits = (unsigned long long)__double_as_longlong(T);
+    uint4 a = make_uint4(ev, (uint32_t)species | ((uint32_t)origin << 8) | ((uint32_t)index << 16),
+                         (uint32_t)tbits, (uint32_t)(tbits >> 32));
+    uint4 b = make_uint4(__float_as_uint(ux), __float_as_uint(uy), __float_as_uint(uz), 0u);
+    uint4 *dst = reinterpret_cast<uint4 *>(P.sec + slot);
+    dst[0] = a;
+    dst[1] = b;
+}
+
+template <typename R>
+__device__ void write_residual(const SimParams &P, const Lane<R> &L)
+{
+    alignas(16) pnuc_residual o;
+    o.Z_cascade = (uint16_t)L.Zc;
+    o.A_cascade = (uint16_t)L.Ac;
+    o.Z_final = (uint16_t)L.Z;
+    o.A_final = (uint16_t)L.A;
+    o.n_cascade = (uint16_t)min(L.n_esc, 65535);
+    o.n_evaporated = (uint16_t)min(L.n_evap, 65535);
+    o.n_collisions = (uint16_t)min(L.n_coll, 65535);
+    o.n_attempts = (uint16_t)min(L.attempts, 65535);
+    o.flags = L.flags;
+    o.reserved = 0;
+    o.Estar_cascade = L.Estar_c;
+    o.Estar_final = L.Estar;
+    o.P_cascade[0] = (float)L.Px;  // set by end_cascade; zero for events without a cascade
+    o.P_cascade[1] = (float)L.Py;
+    o.P_cascade[2] = (float)L.Pz;
+    o.P_final[0] = (float)L.Prx;
+    o.P_final[1] = (float)L.Pry;
+    o.P_final[2] = (float)L.Prz;
+    const uint4 *src = reinterpret_cast<const uint4 *>(&o);
+    uint4 *dst = reinterpret_cast<uint4 *>(P.res + L.ev);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst[k] = src[k];
+}
+
+// Starts event ev in lane L (reads its energy and target id).
+template <typename R>
+__device__ void begin_event(const SimParams &P, const TargetScalars *tabs, Lane<R> &L, uint32_t ev)
+{
+    L.ev = ev;
+    L.rng.reset(P.seed, P.first_event_id + ev);
+    L.T0 = __ldg(&P.energies[ev]);
+    L.tgt = __ldg(&P.target_ids[ev]);
+    L.steps = L.attempts = L.n_coll = L.n_index = L.n_esc = L.n_p_esc = L.n_evap = 0;
+    L.flags = 0;
+    L.Esum = L.Px = L.Py = L.Pz = 0.0;
+    L.Estar = L.Estar_c = 0.0;
+    L.Er = L.Prx = L.Pry = L.Prz = 0.0;
+    L.sp = 0;
+    bool tgt_ok = L.tgt >= 0 && L.tgt < P.n_targets;
+    L.Z = L.Zc = tgt_ok ? tabs[L.tgt].Z : 0;
+    L.A = L.Ac = tgt_ok ? tabs[L.tgt].A : 0;
+    if (!tgt_ok || !(L.T0 >= 20.0 && L.T0 <= 250.0)) {
+        L.flags = PNUC_FLAG_BAD_INPUT;
+        L.phase = kFinish;
+        return;
+    }
+    L.phase = kEntry;
+}
+
+// Entry on the projected disk of radius R, refracted into the surface shell.
+template <typename R, bool kCount>
+__device__ void step_entry(const SimParams &P, const ShellTable<R> &t, double Rad, Lane<R> &L, Counters<kCount> &C)
+{
+    if (L.attempts >= P.max_attempts) {
+        L.flags |= PNUC_FLAG_ATTEMPT_CAP;
+        L.phase = kFinish;
+        return;
+    }
+    ++L.attempts;
+    C.add(PNUC_C_ATTEMPTS);
+    R Rr = (R)Rad;
+    R b = Rr * sqrt(L.rng.next());
+    R phi = R(kTwoPi) * L.rng.next();
+    R sphi, cphi;
+    sincos(phi, &sphi, &cphi);
+    L.r[0] = b * cphi;
+    L.r[1] = b * sphi;
+    L.r[2] = -sqrt(Rr * Rr - b * b);
+    double T0 = L.T0;
+    L.p[0] = R(0);
+    L.p[1] = R(0);
+    L.p[2] = (R)sqrt(T0 * T0 + 2.0 * T0 * kMp);
+    R rr = sqrt(dot3(L.r, L.r));
+    R n[3] = {L.r[0] / rr, L.r[1] / rr, L.r[2] / rr};
+    refract(n, L.p, (R)kMp, t.V[1][kShells - 1]);
+    L.s = 1;
+    L.shell = kShells - 1;
+    L.sp = 0;
+    L.phase = kTransport;
+}
+
+// The cascade of this attempt is over: retry if it was elastic (unless forced by the
+// step cap), else compute E* from the energy balance; the static mean field takes the
+// momentum imbalance (kept in Px..Pz from here on) and the residual evaporates from rest.
+template <typename R>
+__device__ void end_cascade(const SimParams &P, const TargetScalars &tab, Lane<R> &L, bool force)
+{
+    if (L.n_coll == 0 && !force) {
+        L.phase = kEntry;
+        return;
+    }
+    int Z = tab.Z + 1 - L.n_p_esc, A = tab.A + 1 - L.n_esc;
+    L.Z = L.Zc = Z;
+    L.A = L.Ac = A;
+    double p0 = sqrt(L.T0 * L.T0 + 2.0 * L.T0 * kMp);
+    L.Px = -L.Px;
+    L.Py = -L.Py;
+    L.Pz = p0 - L.Pz;
+    double Er = L.T0 + kMp + tab.M - L.Esum;
+    L.Er = Er;
+    L.Prx = L.Pry = L.Prz = 0.0;
+    if (Z < 1 || A - Z < 1) {
+        L.flags |= PNUC_FLAG_BAD_RESIDUAL;
+        L.phase = kFinish;
+        return;
+    }
+    double Estar = Er - __ldg(&P.mass[Z * kMassA + A]);
+    L.Estar = L.Estar_c = Estar;
+    if (!(Estar > 0.0)) {
+        L.flags |= PNUC_FLAG_NO_EXCITATION;
+        L.phase = kFinish;
+        return;
+    }
+    L.phase = kEvap;
+}
+
+// Pops the next particle of the stack, or ends the attempt.
+template <typename R>
+__device__ __forceinline__ void next_particle(const SimParams &P, const TargetScalars &tab, Lane<R> &L, Particle<R> *stack)
+{
+    if (L.sp > 0) {
+        const Particle<R> &q = stack[--L.sp];
+        L.r[0] = q.r[0];
+        L.r[1] = q.r[1];
+        L.r[2] = q.r[2];
+        L.p[0] = q.p[0];
+        L.p[1] = q.p[1];
+        L.p[2] = q.p[2];
+        L.s = q.s;
+        L.shell = q.shell;
+    } else {
+        end_cascade(P, tab, L, false);
+    }
+}
+
+// One transport step of the particle in flight (§2.3): a path from the majorant rate,
+// then a candidate collision or a boundary crossing.
+template <typename R, bool kCount>
+__device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const TargetScalars &tab, Lane<R> &L,
+                               Particle<R> *stack, Counters<kCount> &C)
+{
+    if (L.steps >= P.max_steps) {
+        // step cap: the particles in flight stay in the nucleus and the event goes on to
+        // its excitation energy with what has escaped so far
+        L.flags |= PNUC_FLAG_STEP_CAP;
+        L.sp = 0;
+        end_cascade(P, tab, L, true);
+        return;
+    }
+    ++L.steps;
+    C.add(PNUC_C_STEPS);
+    const int s1 = L.s, i = L.shell;
+    const R m1 = (R)nucleon_mass(s1);
+    const R pp = dot3(L.p, L.p), pm = sqrt(pp);
+    const R E1 = sqrt(pp + m1 * m1);
+    R d[3] = {L.p[0] / pm, L.p[1] / pm, L.p[2] / pm};
+    int dir;
+    R sb = boundary_distance(t, i, L.r, d, dir);
+    R gh = g_hat<R>(pm, E1, t.vF[i]);
+    R Sigma = R(0.1) * t.rho[i] * gh / (pm * R(1e-3));
+    R s = -log(L.rng.next()) / Sigma;
+    if (s < sb) {
+        // ---- candidate collision
+#pragma unroll
+        for (int k = 0; k < 3; ++k) L.r[k] += s * d[k];
+        C.add(PNUC_C_CANDIDATES);
+        int s2 = (L.rng.next() < t.ZoverA) ? 1 : 0;
+        R m2 = (R)nucleon_mass(s2);
+        R q = t.pF[s2][i] * cbrt(L.rng.next());
+        R ct = R(2) * L.rng.next() - R(1);
+        R sn = sqrt((R(1) - ct) * (R(1) + ct));
+        R ph = R(kTwoPi) * L.rng.next();
+        R sph, cph;
+        sincos(ph, &sph, &cph);
+        R p2[3] = {q * sn * cph, q * sn * sph, q * ct};
+        R T1 = kinetic(pp, m1), T2 = kinetic(q * q, m2);
+        R E2 = sqrt(q * q + m2 * m2);
+        R X = T1 * T2 + T1 * m2 + T2 * m1 - dot3(L.p, p2);
+        if (X < R(0)) X = R(0);
+        R kk = sqrt(X * (X + R(2) * m1 * m2));
+        R plab = kk / m2;
+        R vrel = kk / (E1 * E2);
+        R sig = sigma_nn<R>(s1 == s2, plab * R(1e-3));
+        R ua = L.rng.next();
+        if (!(ua * gh < sig * vrel * E1 * R(1e-3))) return;  // null collision
+        C.add(PNUC_C_KINEMATICS);
+        double ut = (double)L.rng.next(), uph = (double)L.rng.next(), uf = (double)L.rng.next();
+        double P1[3] = {(double)L.p[0], (double)L.p[1], (double)L.p[2]};
+        double P2[3] = {(double)p2[0], (double)p2[1], (double)p2[2]};
+        double Q1[3], Q2[3];
+        collide(s1, P1, s2, P2, ut, uph, uf, Q1, Q2);
+        double T1n = kinetic(dot3(Q1, Q1), nucleon_mass(s1));
+        double T2n = kinetic(dot3(Q2, Q2), nucleon_mass(s2));
+        if (!(T1n > (double)t.EF[s1][i] && T2n > (double)t.EF[s2][i])) {
+            C.add(PNUC_C_PAULI_BLOCKED);
+            return;
+        }
+        C.add(PNUC_C_COLLISIONS);
+        ++L.n_coll;
+        double cut2 = (double)t.V[s2][i] + (s2 == 1 ? (double)t.EC : 0.0);
+        double cut1 = (double)t.V[s1][i] + (s1 == 1 ? (double)t.EC : 0.0);
+        if (T2n < cut2) {
+            C.add(PNUC_C_CAPTURES);
+        } else if (L.sp >= kStackCap) {
+            L.flags |= PNUC_FLAG_STACK_OVERFLOW;
+            C.add(PNUC_C_CAPTURES);
+        } else {
+            Particle<R> &np = stack[L.sp++];
+            np.r[0] = L.r[0];
+            np.r[1] = L.r[1];
+            np.r[2] = L.r[2];
+            np.p[0] = (R)Q2[0];
+            np.p[1] = (R)Q2[1];
+            np.p[2] = (R)Q2[2];
+            np.s = s2;
+            np.shell = i;
+        }
+        L.p[0] = (R)Q1[0];
+        L.p[1] = (R)Q1[1];
+        L.p[2] = (R)Q1[2];
+        if (T1n < cut1) {
+            C.add(PNUC_C_CAPTURES);
+            next_particle(P, tab, L, stack);
+        }
+        return;
+    }
+    // ---- move to the boundary and cross it
+#pragma unroll
+    for (int k = 0; k < 3; ++k) L.r[k] += sb * d[k];
+    C.add(PNUC_C_CROSSINGS);
+    const int j = i + dir;  // kShells = outside
+    R dT = -t.V[s1][i] + (j == kShells ? R(0) : t.V[s1][j]);
+    R rr = sqrt(dot3(L.r, L.r));
+    R n[3] = {L.r[0] / rr, L.r[1] / rr, L.r[2] / rr};
+    R Tb = kinetic(pp, m1);
+    if (!refract(n, L.p, m1, dT)) {
+        C.add(PNUC_C_REFLECTIONS);
+        return;
+    }
+    L.shell = j;
+    if (j < kShells) return;
+    // escape: recorded only once the attempt is non-elastic
+    R Tout = Tb + dT;
+    if (L.n_coll > 0) {
+        C.add(PNUC_C_ESCAPES);
+        R pn = sqrt(dot3(L.p, L.p));
+        emit_secondary(P, L.ev, s1, 0, L.n_index++, (double)Tout, (float)(L.p[0] / pn), (float)(L.p[1] / pn),
+                       (float)(L.p[2] / pn), L.flags);
+        L.Esum += (double)Tout + nucleon_mass(s1);
+        L.Px += (double)L.p[0];
+        L.Py += (double)L.p[1];
+        L.Pz += (double)L.p[2];
+        ++L.n_esc;
+        if (s1 == 1) ++L.n_p_esc;
+    }
+    next_particle(P, tab, L, stack);
+}
+
+// Rejection sampler of t on [0, x] (four draws per trial); returns -1 after max_trials.
+template <typename R>
+__device__ R sample_t(Stream<R> &rng, R a, R x, R b, int max_trials, int &trials)
+{
+    R W1 = x * x / (R(2) * a), W2 = b * x;
+    bool small = x < R(2);
+    R pmix = small ? W1 * x / (W1 * x + R(2) * W2) : W1 / (W1 + W2);
+    for (int k = 0; k < max_trials; ++k) {
+        R um = rng.next(), u1 = rng.next(), u2 = rng.next(), ua = rng.next();
+        ++trials;
+        bool first = um < pmix;
+        R t;
+        if (small) t = first ? x * (u1 > u2 ? u1 : u2) : x * u1;
+        else t = first ? -log(u1 * u2) : -log(u1);
+        if (t >= x) continue;
+        R h = (t * (R(2) * x - t) / (R(4) * a) + b) * (x - t);
+        if (small) h *= exp(-t);
+        if (ua * (W1 * t + W2) < h) return t;
+    }
+    return R(-1);
+}
+
+// One evaporation step (§2.4): widths of the six channels, the channel draw, the emission
+// energy, and the two-body decay isotropic in the parent's rest frame, boosted to the lab.
+template <typename R, bool kCount>
+__device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
+{
+    if (L.n_evap >= P.max_evap_steps) {
+        L.flags |= PNUC_FLAG_EVAP_STEP_CAP;
+        L.phase = kFinish;
+        return;
+    }
+    const int Z = L.Z, A = L.A;
+    const double Mparent = __ldg(&P.mass[Z * kMassA + A]);
+    const double Estar = L.Estar;
+    double G[6], S = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        Channel c;
+        channel(P, Z, A, Mparent, Estar, j, c);
+        G[j] = c.width;
+        S += G[j];
+    }
+    if (!(S > 0.0)) {
+        L.phase = kFinish;
+        return;
+    }
+    C.add(PNUC_C_EVAP_STEPS);
+    double us = (double)L.rng.next() * S, cum = 0.0;
+    int ch = -1;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        cum += G[j];
+        if (ch < 0 && us < cum) ch = j;
+    }
+    if (ch < 0)
+        for (int j = 5; j >= 0; --j)
+            if (G[j] > 0.0) {
+                ch = j;
+                break;
+            }
+    Channel c;
+    channel(P, Z, A, Mparent, Estar, ch, c);
+    int trials = 0;
+    R tt = sample_t<R>(L.rng, (R)c.a, (R)c.x, (R)c.b, P.max_evap_trials, trials);
+    C.add(PNUC_C_EVAP_TRIALS, trials);
+    if (tt < R(0)) {
+        L.flags |= PNUC_FLAG_EVAP_TRIAL_CAP;
+        L.phase = kFinish;
+        return;
+    }
+    double xt = c.x - (double)tt;
+    double Ud = xt * xt / (4.0 * c.a);
+    double X = Estar - c.Q;
+    double eps = X - Ud;
+    double W = Mparent + Estar;
+    double m1 = cEjM[ch], m2 = c.Md + Ud;
+    double pd = sqrt(eps * (W + m1 + m2) * (W - m1 + m2) * (W + m1 - m2)) / (2.0 * W);
+    double ct = 2.0 * (double)L.rng.next() - 1.0;
+    double ph = kTwoPi * (double)L.rng.next();
+    double sn = sqrt((1.0 - ct) * (1.0 + ct));
+    double sph, cph;
+    sincos(ph, &sph, &cph);
+    double pv[3] = {pd * sn * cph, pd * sn * sph, pd * ct};
+    double e1 = sqrt(pd * pd + m1 * m1);
+    double Pr[3] = {L.Prx, L.Pry, L.Prz};
+    double Er = L.Er;
+    double Pm = sqrt(dot3(Pr, Pr));
+    double gamma = Er / sqrt((Er - Pm) * (Er + Pm));
+    double beta[3] = {Pr[0] / Er, Pr[1] / Er, Pr[2] / Er};
+    double pl[3];
+    boost(beta, gamma, 1.0, e1, pv, pl);
+    double el = gamma * (e1 + dot3(beta, pv));
+    double pl2 = dot3(pl, pl);
+    double Tl = kinetic(pl2, m1);
+    double pln = sqrt(pl2);
+    emit_secondary(P, L.ev, ch, 1, L.n_index++, Tl, (float)(pl[0] / pln), (float)(pl[1] / pln), (float)(pl[2] / pln),
+                   L.flags);
+    ++L.n_evap;
+    L.Er = Er - el;
+    L.Prx = Pr[0] - pl[0];
+    L.Pry = Pr[1] - pl[1];
+    L.Prz = Pr[2] - pl[2];
+    L.Z = Z - cEjZ[ch];
+    L.A = A - cEjA[ch];
+    L.Estar = Ud;
+}
+
+// Advances lane L by one step of its current phase.
+template <typename R, bool kCount>
+__device__ __forceinline__ void step(const SimParams &P, const ShellTable<R> *sh, const TargetScalars *tabs, Lane<R> &L,
+                                     Particle<R> *stack, Counters<kCount> &C)
+{
+    if (L.phase == kTransport) {
+        step_transport<R, kCount>(P, sh[L.tgt], tabs[L.tgt], L, stack, C);
+    } else if (L.phase == kEntry) {
+        step_entry<R, kCount>(P, sh[L.tgt], tabs[L.tgt].R, L, C);
+    } else if (L.phase == kEvap) {
+        step_evap<R, kCount>(P, L, C);
+    }
+}
+
+}  // namespace
+}  // namespace dev
+}  // namespace pnuc

@@ -1,0 +1,78 @@
+// Internal declarations shared by the libpnuc translation units (host API, table
+// kernels, and the FP32 / FP64 event kernels). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pnuc.h"
+
+namespace pnuc {
+
+constexpr int kShells = 15;      // equal-thickness density steps (paper §2.2)
+constexpr int kMaxTargets = 16;  // targets per context
+constexpr int kStackCap = 64;    // particles waiting in one event's cascade
+constexpr int kMassZ = 102;      // nuclide table covers Z in [0, 101]
+constexpr int kMassA = 252;      //                     and A in [0, 251]
+
+// One target's shell table in precision R (paper §2.2). Index [0] = neutrons, [1] = protons.
+template <typename R>
+struct ShellTable {
+    R r[16];        // shell radii r_k = k R / 15, fm
+    R rho[15];      // nucleon density of shell i, fm^-3
+    R vF[15];       // largest Fermi velocity of the two species in shell i (units of c)
+    R pF[2][15];    // Fermi momentum, MeV/c
+    R EF[2][15];    // Fermi kinetic energy, MeV
+    R V[2][15];     // well depth = Fermi energy + separation energy, MeV
+    R EC;           // Coulomb barrier e^2 (Z-1)/R, MeV
+    R ZoverA;       // probability that a partner is a proton
+    R pad[2];
+};
+
+// Device-resident description of one target: the shell table in both precisions plus
+// the FP64 scalars the bookkeeping needs.
+struct TargetTable {
+    ShellTable<double> d;
+    ShellTable<float> f;
+    double M;     // SEMF nuclear mass, MeV
+    double S[2];  // separation energies, MeV
+    double R;     // radius c + 2.5 fm
+    int32_t Z, A;
+    int32_t valid, pad;
+};
+
+// Everything a simulation launch reads; passed by value to the kernels.
+struct SimParams {
+    const double *energies;
+    const int32_t *target_ids;
+    uint64_t n;
+    uint64_t seed;
+    uint64_t first_event_id;
+    pnuc_secondary *sec;
+    uint64_t sec_cap;
+    unsigned long long *sec_count;
+    pnuc_residual *res;
+    unsigned long long *counters;  // may be null
+    const TargetTable *tables;     // n_targets entries
+    int32_t n_targets;
+    const double *mass;            // [kMassZ * kMassA] SEMF masses, MeV (0 where undefined)
+    const double *cbrtA;           // [kMassA] A^(1/3)
+    unsigned long long *queue_head;  // persistent method: next unclaimed event
+    int32_t max_steps, max_attempts, max_evap_steps, max_evap_trials;
+    int32_t refill_threshold, chunk;
+};
+
+// Launchers, one per compiled variant (kernel_fp32.cu, kernel_fp64.cu).
+cudaError_t launch_plain_fp64(const SimParams &p, int block, cudaStream_t s);
+cudaError_t launch_persistent_fp64(const SimParams &p, int grid, int block, cudaStream_t s);
+cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, cudaStream_t s);
+cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s);
+// Resident blocks per SM of the persistent kernels at a block size.
+int occupancy_persistent_fp64(int block);
+int occupancy_persistent_fp32(int block, bool count);
+
+// Table builders (tables.cu).
+cudaError_t launch_mass_table(double *mass, double *cbrtA, cudaStream_t s);
+cudaError_t launch_target_table(TargetTable *dst, int Z, int A, const double *mass, cudaStream_t s);
+
+}  // namespace pnuc

@@ -1,0 +1,125 @@
+// Nucleus set-up on the device (paper §2.2, Eq. 1): the nuclide mass table and the
+// 15-shell table of a target. Both run once per context / target; FP64 throughout.
+#include "pnuc_internal.h"
+
+namespace pnuc {
+namespace {
+
+constexpr double kHbarc = 197.3269804;  // MeV fm
+constexpr double kE2 = 1.44;            // e^2, MeV fm
+constexpr double kMp = 938.272, kMn = 939.565;
+constexpr double kPi = 3.141592653589793;
+
+// Semi-empirical nuclear mass (liquid drop with pairing), MeV.
+__device__ double semf(int Z, int A)
+{
+    double a = A, z = Z, n = A - Z;
+    double a13 = cbrt(a);
+    double asym = a - 2.0 * z;
+    double B = 15.75 * a - 17.8 * (a13 * a13) - 0.711 * z * (z - 1.0) / a13 - 23.7 * asym * asym / a;
+    bool zodd = Z & 1, nodd = (A - Z) & 1;
+    if (!zodd && !nodd) B += 11.18 / sqrt(a);
+    else if (zodd && nodd) B -= 11.18 / sqrt(a);
+    return z * kMp + n * kMn - B;
+}
+
+__global__ void mass_table_kernel(double *mass, double *cbrtA)
+{
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < kMassA) cbrtA[idx] = cbrt((double)idx);
+    if (idx >= kMassZ * kMassA) return;
+    int Z = idx / kMassA, A = idx % kMassA;
+    mass[idx] = (A >= 1 && Z <= A) ? semf(Z, A) : 0.0;
+}
+
+__device__ double fermi_density(double r, double c) { return 1.0 / (1.0 + exp((r - c) / 0.545)); }
+
+// One block of 15 warps: warp i integrates r^2 f(r) over shell i, each lane one 1/32 of it
+// with a 128-panel Simpson rule (4096 panels per shell), then lane 0.. fills the table.
+__global__ void target_table_kernel(TargetTable *dst, int Z, int A, const double *mass)
+{
+    __shared__ double I[kShells];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double c = 1.07 * cbrt((double)A);
+    const double R = c + 2.5;  // radius after Chen et al.
+    if (warp < kShells) {
+        double r0 = warp * R / kShells, r1 = (warp + 1) * R / kShells;
+        double h = (r1 - r0) / 4096.0;
+        double acc = 0.0;
+        for (int k = 0; k <= 128; ++k) {
+            int g = lane * 128 + k;  // global panel-point index in [0, 4096]
+            double r = r0 + g * h;
+            double w = (k == 0 || k == 128) ? 1.0 : ((k & 1) ? 4.0 : 2.0);
+            acc += w * r * r * fermi_density(r, c);
+        }
+        acc *= h / 3.0;
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+        if (lane == 0) I[warp] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double total = 0.0;
+    for (int i = 0; i < kShells; ++i) total += I[i];
+    TargetTable t;
+    t.Z = Z;
+    t.A = A;
+    t.R = R;
+    t.M = mass[Z * kMassA + A];
+    t.S[0] = mass[Z * kMassA + (A - 1)] + kMn - t.M;
+    t.S[1] = mass[(Z - 1) * kMassA + (A - 1)] + kMp - t.M;
+    t.valid = (t.S[0] > 0.0 && t.S[1] > 0.0) ? 1 : 0;
+    t.pad = 0;
+    t.d.EC = kE2 * (Z - 1) / R;
+    t.d.ZoverA = (double)Z / A;
+    t.d.pad[0] = t.d.pad[1] = 0.0;
+    for (int k = 0; k <= kShells; ++k) t.d.r[k] = k * R / kShells;
+    for (int i = 0; i < kShells; ++i) {
+        double r0 = t.d.r[i], r1 = t.d.r[i + 1];
+        double rho = 3.0 * A * I[i] / (4.0 * kPi * (r1 * r1 * r1 - r0 * r0 * r0) * total);
+        t.d.rho[i] = rho;
+        double vmax = 0.0;
+        for (int s = 0; s < 2; ++s) {
+            double m = s ? kMp : kMn;
+            double frac = s ? (double)Z / A : (double)(A - Z) / A;
+            double pf = kHbarc * cbrt(3.0 * kPi * kPi * (frac * rho));
+            t.d.pF[s][i] = pf;
+            t.d.EF[s][i] = pf * pf / (sqrt(pf * pf + m * m) + m);
+            t.d.V[s][i] = t.d.EF[s][i] + t.S[s];
+            double v = pf / sqrt(pf * pf + m * m);
+            vmax = v > vmax ? v : vmax;
+        }
+        t.d.vF[i] = vmax;
+    }
+    // FP32 mirror
+    for (int k = 0; k <= kShells; ++k) t.f.r[k] = (float)t.d.r[k];
+    for (int i = 0; i < kShells; ++i) {
+        t.f.rho[i] = (float)t.d.rho[i];
+        t.f.vF[i] = (float)t.d.vF[i];
+        for (int s = 0; s < 2; ++s) {
+            t.f.pF[s][i] = (float)t.d.pF[s][i];
+            t.f.EF[s][i] = (float)t.d.EF[s][i];
+            t.f.V[s][i] = (float)t.d.V[s][i];
+        }
+    }
+    t.f.EC = (float)t.d.EC;
+    t.f.ZoverA = (float)t.d.ZoverA;
+    t.f.pad[0] = t.f.pad[1] = 0.f;
+    *dst = t;
+}
+
+}  // namespace
+
+cudaError_t launch_mass_table(double *mass, double *cbrtA, cudaStream_t s)
+{
+    int n = kMassZ * kMassA;
+    mass_table_kernel<<<(n + 255) / 256, 256, 0, s>>>(mass, cbrtA);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_target_table(TargetTable *dst, int Z, int A, const double *mass, cudaStream_t s)
+{
+    target_table_kernel<<<1, 32 * kShells, 0, s>>>(dst, Z, A, mass);
+    return cudaGetLastError();
+}
+
+}  // namespace pnuc

@@ -1,0 +1,256 @@
+"""Python binding of libpnuc (include/pnuc.h): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels. Device buffers are torch
+tensors; streams are torch CUDA streams. There is no CPU fallback: constructing a Context
+raises if the library cannot be loaded or no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+SECONDARY_DTYPE = np.dtype([("event", "<u4"), ("species", "u1"), ("origin", "u1"), ("index", "<u2"),
+                            ("T", "<f8"), ("ux", "<f4"), ("uy", "<f4"), ("uz", "<f4"), ("reserved", "<u4")])
+RESIDUAL_DTYPE = np.dtype([("Z_cascade", "<u2"), ("A_cascade", "<u2"), ("Z_final", "<u2"), ("A_final", "<u2"),
+                           ("n_cascade", "<u2"), ("n_evaporated", "<u2"), ("n_collisions", "<u2"),
+                           ("n_attempts", "<u2"), ("flags", "<u4"), ("reserved", "<u4"),
+                           ("Estar_cascade", "<f8"), ("Estar_final", "<f8"), ("P_cascade", "<f4", (3,)),
+                           ("P_final", "<f4", (3,))])
+assert SECONDARY_DTYPE.itemsize == 32 and RESIDUAL_DTYPE.itemsize == 64
+
+COUNTER_NAMES = ("steps", "candidates", "kinematics", "pauli_blocked", "collisions", "crossings", "reflections",
+                 "escapes", "captures", "attempts", "evap_steps", "evap_trials", "draws")
+FLAGS = dict(bad_input=1, attempt_cap=2, step_cap=4, stack_overflow=8, bad_residual=16, no_excitation=32,
+             evap_trial_cap=64, evap_step_cap=128, output_overflow=256)
+PRECISION = {"fp32": 0, "fp64": 1}
+METHOD = {"plain": 0, "persistent": 1}
+STATUS = {0: "ok", 1: "invalid argument", 2: "out of range", 3: "capacity exceeded", 4: "CUDA error",
+          5: "timeout", 6: "invalid state"}
+
+
+class pnuc_config(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_steps", C.c_int32), ("max_attempts", C.c_int32),
+                ("max_evap_steps", C.c_int32), ("max_evap_trials", C.c_int32)]
+
+
+class pnuc_batch(C.Structure):
+    _fields_ = [("energies", C.c_void_p), ("target_ids", C.c_void_p), ("n", C.c_uint64), ("seed", C.c_uint64),
+                ("first_event_id", C.c_uint64)]
+
+
+class pnuc_output(C.Structure):
+    _fields_ = [("secondaries", C.c_void_p), ("capacity", C.c_uint64), ("count", C.c_void_p),
+                ("residuals", C.c_void_p), ("counters", C.c_void_p)]
+
+
+class pnuc_tuning(C.Structure):
+    _fields_ = [("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_threshold", C.c_int32),
+                ("chunk", C.c_int32)]
+
+
+class pnuc_target_info(C.Structure):
+    _fields_ = [("Z", C.c_int32), ("A", C.c_int32), ("R", C.c_double), ("EC", C.c_double), ("M", C.c_double),
+                ("S_n", C.c_double), ("S_p", C.c_double), ("r", C.c_double * 16), ("rho", C.c_double * 15),
+                ("vF", C.c_double * 15), ("pF", (C.c_double * 15) * 2), ("EF", (C.c_double * 15) * 2),
+                ("V", (C.c_double * 15) * 2)]
+
+
+class PnucError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"pnuc: {STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Loads libpnuc.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libpnuc not built: {_build.LIB} is missing")
+    L = C.CDLL(_build.LIB)
+    vp, u64, i32 = C.c_void_p, C.c_uint64, C.c_int32
+    L.pnuc_default_config.argtypes = [C.POINTER(pnuc_config)]
+    L.pnuc_default_config.restype = None
+    L.pnuc_create.argtypes = [C.POINTER(pnuc_config), C.POINTER(vp)]
+    L.pnuc_destroy.argtypes = [vp]
+    L.pnuc_status_string.argtypes = [C.c_int]
+    L.pnuc_status_string.restype = C.c_char_p
+    L.pnuc_last_error.argtypes = [vp, C.c_char_p, C.c_size_t]
+    L.pnuc_create_target.argtypes = [vp, i32, i32, C.POINTER(i32)]
+    L.pnuc_target_table.argtypes = [vp, i32, C.POINTER(pnuc_target_info)]
+    L.pnuc_simulate.argtypes = [vp, C.c_int, C.c_int, C.POINTER(pnuc_batch), C.POINTER(pnuc_output), vp]
+    L.pnuc_simulate_host.argtypes = [vp, C.c_int, C.c_int, vp, vp, u64, u64, u64, vp, u64, C.POINTER(u64), vp, vp]
+    L.pnuc_get_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
+    L.pnuc_set_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
+    for name in ("pnuc_create", "pnuc_destroy", "pnuc_last_error", "pnuc_create_target", "pnuc_target_table",
+                 "pnuc_simulate", "pnuc_simulate_host", "pnuc_get_tuning", "pnuc_set_tuning"):
+        getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _ptr(t) -> int:
+    return 0 if t is None else int(t.data_ptr())
+
+
+@dataclass
+class Result:
+    """Device outputs of one batch (torch tensors) and their host decoders."""
+    secondaries: "object"  # uint8 tensor (capacity, 32)
+    count: "object"        # int64 tensor (1,)
+    residuals: "object"    # uint8 tensor (n, 64)
+    counters: "object" = None
+
+    def n_secondaries(self) -> int:
+        return int(self.count.item())
+
+    def secondaries_np(self) -> np.ndarray:
+        k = min(self.n_secondaries(), self.secondaries.shape[0])
+        return self.secondaries[:k].cpu().numpy().reshape(-1).view(SECONDARY_DTYPE)
+
+    def residuals_np(self) -> np.ndarray:
+        return self.residuals.cpu().numpy().reshape(-1).view(RESIDUAL_DTYPE)
+
+    def counters_dict(self) -> dict:
+        if self.counters is None:
+            return {}
+        v = self.counters.cpu().numpy()
+        return {k: int(v[i]) for i, k in enumerate(COUNTER_NAMES)}
+
+
+class Context:
+    """A libpnuc context on one CUDA device: target tables, scratch, tuning."""
+
+    def __init__(self, device: int = 0, **limits):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("pnuc needs a CUDA device; none is available (there is no CPU fallback)")
+        self._torch = torch
+        self.lib = load()
+        cfg = pnuc_config()
+        self.lib.pnuc_default_config(C.byref(cfg))
+        cfg.device = device
+        for k, v in limits.items():
+            setattr(cfg, k, int(v))
+        h = C.c_void_p()
+        st = self.lib.pnuc_create(C.byref(cfg), C.byref(h))
+        if st != 0:
+            raise PnucError(st, "pnuc_create failed")
+        self.handle = h
+        self.device = device
+        self.targets: list[tuple[int, int]] = []
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.pnuc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != 0:
+            buf = C.create_string_buffer(512)
+            self.lib.pnuc_last_error(self.handle, buf, 512)
+            raise PnucError(st, buf.value.decode())
+
+    def create_target(self, Z: int, A: int) -> int:
+        tid = C.c_int32()
+        self._check(self.lib.pnuc_create_target(self.handle, Z, A, C.byref(tid)))
+        if tid.value == len(self.targets):
+            self.targets.append((Z, A))
+        return tid.value
+
+    def target_table(self, target_id: int) -> dict:
+        info = pnuc_target_info()
+        self._check(self.lib.pnuc_target_table(self.handle, target_id, C.byref(info)))
+        arr = lambda x: np.ctypeslib.as_array(x).copy()
+        return dict(Z=info.Z, A=info.A, R=info.R, EC=info.EC, M=info.M, S=np.array([info.S_n, info.S_p]),
+                    r=arr(info.r), rho=arr(info.rho), vF=arr(info.vF), pF=arr(info.pF), EF=arr(info.EF),
+                    V=arr(info.V))
+
+    def get_tuning(self, precision: str = "fp32") -> dict:
+        t = pnuc_tuning()
+        self._check(self.lib.pnuc_get_tuning(self.handle, PRECISION[precision], C.byref(t)))
+        return dict(block_size=t.block_size, blocks_per_sm=t.blocks_per_sm, refill_threshold=t.refill_threshold,
+                    chunk=t.chunk)
+
+    def set_tuning(self, precision: str = "fp32", **kw):
+        cur = self.get_tuning(precision)
+        cur.update(kw)
+        t = pnuc_tuning(**cur)
+        self._check(self.lib.pnuc_set_tuning(self.handle, PRECISION[precision], C.byref(t)))
+
+    def alloc(self, n: int, capacity: int | None = None, counters: bool = False) -> Result:
+        torch = self._torch
+        dev = torch.device("cuda", self.device)
+        cap = int(capacity if capacity is not None else max(64, 40 * n))
+        return Result(secondaries=torch.empty((cap, 32), dtype=torch.uint8, device=dev),
+                      count=torch.zeros(1, dtype=torch.int64, device=dev),
+                      residuals=torch.empty((max(n, 1), 64), dtype=torch.uint8, device=dev),
+                      counters=torch.zeros(len(COUNTER_NAMES), dtype=torch.int64, device=dev) if counters else None)
+
+    def simulate(self, energies, target_ids, seed: int, first_event_id: int = 0, precision: str = "fp32",
+                 method: str = "persistent", out: Result | None = None, capacity: int | None = None,
+                 counters: bool = False, stream=None) -> Result:
+        """Launches pnuc_simulate on device tensors (energies float64, target_ids int32).
+        Asynchronous on `stream` (default: torch's current stream)."""
+        torch = self._torch
+        n = int(energies.shape[0])
+        if energies.dtype != torch.float64 or target_ids.dtype != torch.int32:
+            raise TypeError("energies must be float64 and target_ids int32 CUDA tensors")
+        if not (energies.is_cuda and target_ids.is_cuda) or target_ids.shape[0] != n:
+            raise ValueError("energies and target_ids must be CUDA tensors of equal length")
+        energies = energies.contiguous()
+        target_ids = target_ids.contiguous()
+        if out is None:
+            out = self.alloc(n, capacity, counters)
+        b = pnuc_batch(_ptr(energies), _ptr(target_ids), n, seed, first_event_id)
+        o = pnuc_output(_ptr(out.secondaries), out.secondaries.shape[0], _ptr(out.count), _ptr(out.residuals),
+                        _ptr(out.counters))
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        self._check(self.lib.pnuc_simulate(self.handle, PRECISION[precision], METHOD[method], C.byref(b),
+                                           C.byref(o), C.c_void_p(s)))
+        return out
+
+    def simulate_host(self, energies: np.ndarray, target_ids: np.ndarray, seed: int, first_event_id: int = 0,
+                      precision: str = "fp32", method: str = "persistent", capacity: int | None = None,
+                      sec_out: np.ndarray | None = None, res_out: np.ndarray | None = None, stream=None):
+        """pnuc_simulate_host: host (ideally pinned) numpy buffers in and out; synchronous.
+        Returns (secondaries, residuals) as numpy structured arrays."""
+        torch = self._torch
+        e = np.ascontiguousarray(energies, np.float64)
+        t = np.ascontiguousarray(target_ids, np.int32)
+        n = e.shape[0]
+        cap = int(capacity if capacity is not None else max(64, 40 * n))
+        sec = sec_out if sec_out is not None else np.empty(cap, SECONDARY_DTYPE)
+        res = res_out if res_out is not None else np.empty(n, RESIDUAL_DTYPE)
+        cnt = C.c_uint64()
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        self._check(self.lib.pnuc_simulate_host(self.handle, PRECISION[precision], METHOD[method],
+                                                e.ctypes.data, t.ctypes.data, n, seed, first_event_id,
+                                                sec.ctypes.data, sec.shape[0], C.byref(cnt), res.ctypes.data,
+                                                C.c_void_p(s)))
+        return sec[: cnt.value], res[:n]
+
+
+def sort_secondaries(sec: np.ndarray) -> np.ndarray:
+    """Secondaries ordered by (event, index): the output order of a launch is not fixed."""
+    return sec[np.lexsort((sec["index"], sec["event"]))]

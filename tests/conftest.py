@@ -11,3 +11,15 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300); runs the CUDA path")
     config.addinivalue_line("markers", "slow: longer CPU test")
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    """One libpnuc context on cuda:0 for the GPU tests (built in-tree if needed)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1309_7963_gb300 import pnuc
+    c = pnuc.Context(0)
+    yield c
+    c.close()

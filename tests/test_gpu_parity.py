@@ -1,0 +1,182 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+FP64 mode: per event, integer outcomes (residual Z/A, multiplicities, emitted species and
+their order, flags) agree on >= 99.9% of events and energies within 1e-9 relative.
+FP32 mode: the same events agree in their integers on most events (rounding rarely changes
+a decision) and the binned spectra agree with the oracle's (chi-square).
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_1309_7963_gb300 import inputs, pnuc
+
+from .parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(ctx, w, precision, method, counters=False, capacity=None):
+    import torch
+    tids = [ctx.create_target(*za) for za in w.targets]
+    e = torch.tensor(w.energies, dtype=torch.float64, device="cuda")
+    t = torch.tensor(np.asarray(tids, np.int32)[w.tidx], dtype=torch.int32, device="cuda")
+    r = ctx.simulate(e, t, seed=w.seed, first_event_id=w.first_event_id, precision=precision, method=method,
+                     counters=counters, capacity=capacity)
+    torch.cuda.synchronize()
+    return r
+
+
+def run_oracle(w):
+    return oracle.simulate_parallel(w.targets, w.energies, w.tidx, seed=w.seed, first_event_id=w.first_event_id,
+                                    chunk=512)
+
+
+def test_target_tables_match_oracle(ctx):
+    for za in [(6, 12), (8, 16), (20, 40), (26, 56), (82, 208)]:
+        g = ctx.target_table(ctx.create_target(*za))
+        o = oracle.target(*za)
+        assert g["R"] == pytest.approx(o["R"], rel=1e-15)
+        for k in ("r", "rho", "vF", "pF", "EF", "V"):
+            assert np.allclose(g[k], o[k], rtol=2e-14, atol=0), k
+        assert np.allclose(g["S"], o["S"], rtol=1e-12)
+        assert g["EC"] == pytest.approx(o["EC"], rel=1e-14)
+
+
+@pytest.mark.parametrize("method", ["plain", "persistent"])
+def test_fp64_per_event_parity_o16_200MeV(ctx, method):
+    w = inputs.plain_fp64(10_000)
+    r = run_gpu(ctx, w, "fp64", method)
+    c = compare(r.residuals_np(), r.secondaries_np(), run_oracle(w), w.n)
+    assert c["frac_same"] >= 0.999, c["frac_same"]
+    assert c["max_rel_T"] <= 1e-9 and c["max_rel_Estar"] <= 1e-9, c
+    assert c["max_dir_err"] < 2e-7
+
+
+def test_fp64_per_event_parity_mixed_targets_and_energies(ctx):
+    w = inputs.mixed(6000, seed=3)
+    r = run_gpu(ctx, w, "fp64", "persistent")
+    c = compare(r.residuals_np(), r.secondaries_np(), run_oracle(w), w.n)
+    assert c["frac_same"] >= 0.999, c["frac_same"]
+    assert c["max_rel_T"] <= 1e-9 and c["max_rel_Estar"] <= 1e-9, c
+
+
+@pytest.mark.parametrize("za", [inputs.TI48, inputs.FE56, inputs.PB208])
+def test_fp64_per_event_parity_heavy(ctx, za):
+    w = inputs.heavy(za, 1500, seed=7)
+    r = run_gpu(ctx, w, "fp64", "persistent")
+    c = compare(r.residuals_np(), r.secondaries_np(), run_oracle(w), w.n)
+    assert c["frac_same"] >= 0.999, c["frac_same"]
+    assert c["max_rel_T"] <= 1e-9 and c["max_rel_Estar"] <= 1e-9, c
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_persistent_equals_plain_bitwise(ctx, precision):
+    w = inputs.mixed(20_000, seed=11)
+    a = run_gpu(ctx, w, precision, "plain")
+    b = run_gpu(ctx, w, precision, "persistent")
+    assert np.array_equal(a.residuals_np(), b.residuals_np())
+    sa, sb = pnuc.sort_secondaries(a.secondaries_np()), pnuc.sort_secondaries(b.secondaries_np())
+    assert np.array_equal(sa, sb)
+
+
+def test_gpu_counters_match_oracle_counters(ctx):
+    w = inputs.plain_fp64(3000)
+    r = run_gpu(ctx, w, "fp64", "persistent", counters=True)
+    g = r.counters_dict()
+    o = run_oracle(w)["counters"]
+    for k in ("steps", "candidates", "kinematics", "collisions", "attempts", "evap_steps", "draws"):
+        assert abs(g[k] - o[k]) <= 1e-3 * o[k] + 5, (k, g[k], o[k])
+
+
+def test_fp32_per_event_agreement_and_spectra(ctx):
+    w = inputs.oxygen_calcium(n_each=20_000)
+    r = run_gpu(ctx, w, "fp32", "persistent")
+    orc = run_oracle(w)
+    c = compare(r.residuals_np(), r.secondaries_np(), orc, w.n)
+    assert c["frac_same"] >= 0.97, c["frac_same"]
+    gs, os_ = r.secondaries_np(), orc["secondaries"]
+    for sp in range(6):
+        a, b = gs["T"][gs["species"] == sp], os_["T"][os_["species"] == sp]
+        if len(b) < 200:
+            continue
+        edges = np.linspace(0, 250, 126)
+        ha, _ = np.histogram(a, edges)
+        hb, _ = np.histogram(b, edges)
+        keep = (ha + hb) > 10
+        # correlated samples (same events), so the two-sample statistic is conservative
+        chi2 = (((ha - hb) ** 2) / (ha + hb))[keep].sum()
+        assert stats.chi2.sf(chi2, keep.sum() - 1) > 0.01, (sp, chi2, keep.sum())
+    for k in ("n_cascade", "n_evaporated"):
+        ok = "n_casc" if k == "n_cascade" else "n_evap"
+        gm, om = r.residuals_np()[k].mean(), orc["residuals"][ok].mean()
+        sd = orc["residuals"][ok].std() / np.sqrt(w.n)
+        assert abs(gm - om) < 3 * sd + 1e-12, (k, gm, om, sd)
+
+
+def test_edge_cases_empty_ragged_bad_inputs(ctx):
+    import torch
+    tid = ctx.create_target(8, 16)
+    # n = 0: count written 0, nothing else
+    r = ctx.simulate(torch.zeros(0, dtype=torch.float64, device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"),
+                     seed=0, precision="fp32", method="persistent")
+    torch.cuda.synchronize()
+    assert r.n_secondaries() == 0
+    # ragged sizes and bad inputs: energy out of range, unknown target id
+    for n in (1, 33, 127, 1025):
+        e = np.full(n, 150.0)
+        t = np.full(n, tid, np.int32)
+        e[::7] = 10.0
+        t[3::11] = 99
+        for method in ("plain", "persistent"):
+            g = ctx.simulate(torch.tensor(e, device="cuda"), torch.tensor(t, device="cuda"), seed=1, precision="fp64",
+                             method=method)
+            torch.cuda.synchronize()
+            res = g.residuals_np()
+            bad = (e < 20) | (t != tid)
+            assert np.all(res["flags"][bad] == 1) and np.all((res["flags"][~bad] & 1) == 0)
+            sec = g.secondaries_np()
+            assert not np.isin(sec["event"], np.where(bad)[0]).any()
+            assert set(np.unique(sec["event"])) <= set(np.where(~bad)[0])
+
+
+def test_output_capacity_overflow_is_reported(ctx):
+    import torch
+    tid = ctx.create_target(20, 40)
+    n = 2000
+    e = torch.full((n,), 200.0, dtype=torch.float64, device="cuda")
+    t = torch.full((n,), tid, dtype=torch.int32, device="cuda")
+    full = ctx.simulate(e, t, seed=2, precision="fp32", method="persistent")
+    small = ctx.simulate(e, t, seed=2, precision="fp32", method="persistent", capacity=1000)
+    torch.cuda.synchronize()
+    assert small.n_secondaries() == full.n_secondaries() > 1000
+    res = small.residuals_np()
+    flagged = (res["flags"] & 256) != 0
+    assert flagged.sum() > 0
+    # every record that was stored is a real record of the full run
+    got = small.secondaries_np()
+    assert len(got) == 1000
+    ref = {(int(a), int(b)) for a, b in zip(full.secondaries_np()["event"], full.secondaries_np()["index"])}
+    assert all((int(a), int(b)) in ref for a, b in zip(got["event"], got["index"]))
+
+
+def test_event_result_independent_of_batch(ctx):
+    w = inputs.mixed(4000, seed=9)
+    a = run_gpu(ctx, w, "fp32", "persistent")
+    sub = w.slice(1000, 1100)
+    b = run_gpu(ctx, sub, "fp32", "persistent")
+    assert np.array_equal(a.residuals_np()[1000:1100], b.residuals_np())
+    sa = pnuc.sort_secondaries(a.secondaries_np())
+    sa = sa[(sa["event"] >= 1000) & (sa["event"] < 1100)]
+    sb = pnuc.sort_secondaries(b.secondaries_np())
+    assert np.array_equal(sa["event"] - 1000, sb["event"]) and np.array_equal(sa["T"], sb["T"])
+
+
+def test_host_buffer_entry_point(ctx):
+    w = inputs.plain_fp64(2000)
+    tid = ctx.create_target(*w.targets[0])
+    sec, res = ctx.simulate_host(w.energies, np.full(w.n, tid, np.int32), seed=0, precision="fp64",
+                                 method="persistent")
+    c = compare(res, sec, run_oracle(w), w.n)
+    assert c["frac_same"] >= 0.999
