@@ -126,12 +126,15 @@ typedef struct {
     unsigned long long *counters;/* device, PNUC_N_COUNTERS entries added to, or NULL */
 } pnuc_output;
 
-/* Launch tuning of the persistent method (the plain method uses block_size only). */
+/* Launch tuning of the persistent method (the plain method uses block_size only). None of
+ * these changes any event's result, only the order in which lanes do their work. */
 typedef struct {
     int32_t block_size;       /* threads per block: 64, 128, 256 or 512 */
     int32_t blocks_per_sm;    /* resident blocks per SM for the persistent grid (<= occupancy) */
     int32_t refill_threshold; /* a warp refills when at least this many lanes are idle (1..32) */
-    int32_t chunk;            /* events a warp takes from the queue per atomic (>= 32) */
+    int32_t chunk;            /* events a warp takes from the queue per atomic (32 .. 2^20) */
+    int32_t kin_batch;        /* accepted collisions a warp gathers before their FP64 kinematics (1..32) */
+    int32_t evap_batch;       /* lanes in evaporation a warp gathers before an evaporation step (1..32) */
 } pnuc_tuning;
 
 typedef struct pnuc_ctx pnuc_ctx;
@@ -191,6 +194,17 @@ pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_met
 /* Persistent-method tuning of the context (per precision). set checks the ranges above. */
 pnuc_status pnuc_get_tuning(const pnuc_ctx *ctx, pnuc_precision precision, pnuc_tuning *out);
 pnuc_status pnuc_set_tuning(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_tuning *t);
+
+/* Measured throughput of the pipes the event kernels use, in lane operations per second
+ * (one fused multiply-add = one operation): FP32 FMA, FP64 FMA, special-function unit
+ * (reciprocal square root) and 32-bit integer multiply-add. Independent FMA chains on 8
+ * blocks of 256 threads per SM, timed with CUDA events. These are the denominators of
+ * the ALU roofline (the method has no dense contraction and its HBM traffic is small).
+ * Synchronous; takes about a second. Not part of the paper: measurement support. */
+typedef struct {
+    double fp32_fma, fp64_fma, mufu, int32_mad;
+} pnuc_peaks;
+pnuc_status pnuc_measure_peaks(pnuc_ctx *ctx, pnuc_peaks *out);
 
 #ifdef __cplusplus
 }

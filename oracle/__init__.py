@@ -274,11 +274,12 @@ def simulate(targets, energies, tidx, seed: int, first_event_id: int = 0, limits
 
 
 def simulate_parallel(targets, energies, tidx, seed: int, first_event_id: int = 0,
-                      threads: int | None = None, chunk: int = 2048, limits=None):
+                      threads: int | None = None, chunk: int = 2048, limits=None, keep: bool = True):
     """simulate() over event chunks on a thread pool (the C call releases the GIL).
 
     Results are identical to simulate(): every event depends only on (seed, event id).
-    Returns the same dict plus 'threads' (the number of worker threads used).
+    Returns the same dict plus 'threads' (the number of worker threads used). With
+    keep=False only the counters and the number of secondaries are returned (for timing).
     """
     if not isinstance(targets, np.ndarray) or targets.dtype != TARGET_DTYPE:
         targets = make_targets(targets)
@@ -292,11 +293,16 @@ def simulate_parallel(targets, energies, tidx, seed: int, first_event_id: int = 
         r = simulate(targets, e[s0:s0 + chunk], ti[s0:s0 + chunk], seed, first_event_id + s0,
                      limits=limits)
         r["secondaries"]["event"] += s0
+        if not keep:
+            r = dict(n_secondaries=len(r["secondaries"]), counters=r["counters"])
         return r
 
     lib()
     with ThreadPoolExecutor(max_workers=threads) as ex:
         parts = list(ex.map(run, starts))
+    if not keep:
+        counters = {k: sum(p["counters"][k] for p in parts) for k in COUNTER_NAMES}
+        return dict(n_secondaries=sum(p["n_secondaries"] for p in parts), counters=counters, threads=threads)
     sec = np.concatenate([p["secondaries"] for p in parts]) if parts else np.zeros(0, SECONDARY_DTYPE)
     res = np.concatenate([p["residuals"] for p in parts]) if parts else np.zeros(0, RESIDUAL_DTYPE)
     counters = {k: sum(p["counters"][k] for p in parts) for k in COUNTER_NAMES}

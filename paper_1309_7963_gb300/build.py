@@ -20,6 +20,7 @@ COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.pat
 UNITS = {
     "api.cu": [],
     "tables.cu": [],
+    "microbench.cu": [],
     "kernel_fp64.cu": ["--fmad=false"],
     "kernel_fp32.cu": ["--use_fast_math"],
 }

@@ -72,6 +72,8 @@ pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t)
         return fail(ctx, PNUC_ERR_ARG, "refill_threshold %d not in [1,32]", t->refill_threshold);
     if (t->chunk < 32 || t->chunk > (1 << 20))
         return fail(ctx, PNUC_ERR_ARG, "chunk %d not in [32, 2^20]", t->chunk);
+    if (t->kin_batch < 1 || t->kin_batch > 32 || t->evap_batch < 1 || t->evap_batch > 32)
+        return fail(ctx, PNUC_ERR_ARG, "kin_batch %d / evap_batch %d not in [1,32]", t->kin_batch, t->evap_batch);
     return PNUC_OK;
 }
 
@@ -149,6 +151,8 @@ pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
             t.block_size = 128;
             t.refill_threshold = 8;
             t.chunk = 256;
+            t.kin_batch = 16;
+            t.evap_batch = 8;
             int occ = occupancy((pnuc_precision)p, t.block_size, false);
             t.blocks_per_sm = occ > 0 ? occ : 1;
         }
@@ -281,6 +285,8 @@ pnuc_status pnuc_simulate(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method m
     const pnuc_tuning &t = ctx->tuning[precision];
     p.refill_threshold = t.refill_threshold;
     p.chunk = t.chunk;
+    p.kin_batch = t.kin_batch;
+    p.evap_batch = t.evap_batch;
     p.queue_head = nullptr;
     const bool count = out->counters != nullptr;
     cudaError_t e;
@@ -354,6 +360,19 @@ pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_met
     if (cnt > sec_capacity)
         return fail(ctx, PNUC_ERR_CAPACITY, "batch produced %llu secondaries, capacity %llu", cnt,
                     (unsigned long long)sec_capacity);
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_measure_peaks(pnuc_ctx *ctx, pnuc_peaks *out)
+{
+    if (!ctx || !out) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    CU(ctx, cudaSetDevice(ctx->cfg.device));
+    double v[4];
+    CU(ctx, measure_peaks(ctx->sm_count, v));
+    out->fp32_fma = v[0];
+    out->fp64_fma = v[1];
+    out->mufu = v[2];
+    out->int32_mad = v[3];
     return PNUC_OK;
 }
 

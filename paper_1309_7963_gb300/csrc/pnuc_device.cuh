@@ -30,7 +30,8 @@ __constant__ double cEjG[6] = {2.0, 2.0, 3.0, 2.0, 2.0, 1.0};
 __constant__ int cEjZ[6] = {0, 1, 1, 1, 2, 2};
 __constant__ int cEjA[6] = {1, 1, 2, 3, 3, 4};
 
-enum Phase : int { kIdle = 0, kEntry = 1, kTransport = 2, kEvap = 3, kFinish = 4, kExhausted = 5 };
+// kKinWait: an accepted candidate waits for its collision kinematics (batched per warp).
+enum Phase : int { kIdle = 0, kEntry = 1, kTransport = 2, kEvap = 3, kFinish = 4, kExhausted = 5, kKinWait = 6 };
 
 // ------------------------------------------------------------------ Philox4x64-10
 // Salmon et al., SC'11: ten rounds, multipliers and Weyl key increments of the paper.
@@ -279,69 +280,6 @@ __device__ void collide(int s1, const double *p1, int s2, const double *p2, doub
     boost(beta, gamma, 1.0, e2, k2, q2);
 }
 
-// ------------------------------------------------------------------ evaporation (§2.4, FP64 widths)
-// F(x) = e^x (x^2 - 3x + 3) + x^2/2 - 3, G(x) = e^x (x - 1) + 1; series below x = 1.
-__device__ void width_FG(double x, double &F, double &G)
-{
-    if (x >= 1.0) {
-        double ex = exp(x);
-        F = ex * (x * x - 3.0 * x + 3.0) + 0.5 * x * x - 3.0;
-        G = ex * (x - 1.0) + 1.0;
-        return;
-    }
-    double term = x, f = 0.0, g = 0.0;  // term = x^n / n!
-#pragma unroll
-    for (int n = 2; n <= 20; ++n) {
-        term *= x / n;
-        g += (double)(n - 1) * term;
-        if (n >= 4) f += (double)((n - 1) * (n - 3)) * term;
-    }
-    F = f;
-    G = g;
-}
-
-struct Channel {
-    double width, V, b, Q, Md, a, x;
-};
-
-// Width and parameters of ejectile j from parent (Z, A, Estar); Mparent from the table.
-__device__ void channel(const SimParams &P, int Z, int A, double Mparent, double Estar, int j, Channel &c)
-{
-    c.width = 0.0;
-    c.x = 0.0;
-    int Zd = Z - cEjZ[j], Ad = A - cEjA[j];
-    if (Zd < 1 || Ad - Zd < 1 || Ad < 5) return;
-    double Md = __ldg(&P.mass[Zd * kMassA + Ad]);
-    double Q = Md + cEjM[j] - Mparent;
-    double A3 = __ldg(&P.cbrtA[Ad]);
-    double V, b, cj;
-    if (cEjZ[j] == 0) {
-        double alpha = 0.76 + 1.93 / A3;
-        double beta = (1.66 / (A3 * A3) - 0.05) / alpha;
-        V = beta < 0.0 ? -beta : 0.0;
-        b = beta > 0.0 ? beta : 0.0;
-        cj = alpha;
-    } else {
-        V = kE2 * cEjZ[j] * Zd / (1.5 * (__ldg(&P.cbrtA[cEjA[j]]) + A3));
-        b = 0.0;
-        cj = 1.0;
-    }
-    double X = Estar - Q, Y = X - V;
-    c.V = V;
-    c.b = b;
-    c.Q = Q;
-    c.Md = Md;
-    double a = Ad / 8.0;
-    c.a = a;
-    if (!(Y > 0.0)) return;
-    double x = 2.0 * sqrt(a * Y);
-    c.x = x;
-    double F, G;
-    width_FG(x, F, G);
-    double I = F / (4.0 * a * a) + b * G / (2.0 * a);
-    c.width = cEjG[j] * cEjM[j] * cj * (A3 * A3) * I;
-}
-
 // ------------------------------------------------------------------ per-lane state
 // Per-target scalars the steps need, staged in shared memory beside the shell tables.
 struct TargetScalars {
@@ -366,6 +304,9 @@ struct Lane {
     // particle in flight
     R r[3], p[3];
     int s, shell, sp;
+    // accepted candidate waiting for its kinematics: the partner's momentum and species
+    R jp[3];
+    int js;
     // event bookkeeping (FP64)
     int steps, attempts, n_coll, n_index, n_esc, n_p_esc, n_evap;
     uint32_t flags;
@@ -547,7 +488,8 @@ __device__ __forceinline__ void next_particle(const SimParams &P, const TargetSc
 }
 
 // One transport step of the particle in flight (§2.3): a path from the majorant rate,
-// then a candidate collision or a boundary crossing.
+// then a candidate collision or a boundary crossing. An accepted candidate leaves the
+// lane in kKinWait with its partner stored; finish_collision() completes it.
 template <typename R, bool kCount>
 __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const TargetScalars &tab, Lane<R> &L,
                                Particle<R> *stack, Counters<kCount> &C)
@@ -597,44 +539,11 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
         R ua = L.rng.next();
         if (!(ua * gh < sig * vrel * E1 * R(1e-3))) return;  // null collision
         C.add(PNUC_C_KINEMATICS);
-        double ut = (double)L.rng.next(), uph = (double)L.rng.next(), uf = (double)L.rng.next();
-        double P1[3] = {(double)L.p[0], (double)L.p[1], (double)L.p[2]};
-        double P2[3] = {(double)p2[0], (double)p2[1], (double)p2[2]};
-        double Q1[3], Q2[3];
-        collide(s1, P1, s2, P2, ut, uph, uf, Q1, Q2);
-        double T1n = kinetic(dot3(Q1, Q1), nucleon_mass(s1));
-        double T2n = kinetic(dot3(Q2, Q2), nucleon_mass(s2));
-        if (!(T1n > (double)t.EF[s1][i] && T2n > (double)t.EF[s2][i])) {
-            C.add(PNUC_C_PAULI_BLOCKED);
-            return;
-        }
-        C.add(PNUC_C_COLLISIONS);
-        ++L.n_coll;
-        double cut2 = (double)t.V[s2][i] + (s2 == 1 ? (double)t.EC : 0.0);
-        double cut1 = (double)t.V[s1][i] + (s1 == 1 ? (double)t.EC : 0.0);
-        if (T2n < cut2) {
-            C.add(PNUC_C_CAPTURES);
-        } else if (L.sp >= kStackCap) {
-            L.flags |= PNUC_FLAG_STACK_OVERFLOW;
-            C.add(PNUC_C_CAPTURES);
-        } else {
-            Particle<R> &np = stack[L.sp++];
-            np.r[0] = L.r[0];
-            np.r[1] = L.r[1];
-            np.r[2] = L.r[2];
-            np.p[0] = (R)Q2[0];
-            np.p[1] = (R)Q2[1];
-            np.p[2] = (R)Q2[2];
-            np.s = s2;
-            np.shell = i;
-        }
-        L.p[0] = (R)Q1[0];
-        L.p[1] = (R)Q1[1];
-        L.p[2] = (R)Q1[2];
-        if (T1n < cut1) {
-            C.add(PNUC_C_CAPTURES);
-            next_particle(P, tab, L, stack);
-        }
+        L.jp[0] = p2[0];
+        L.jp[1] = p2[1];
+        L.jp[2] = p2[2];
+        L.js = s2;
+        L.phase = kKinWait;
         return;
     }
     // ---- move to the boundary and cross it
@@ -669,6 +578,147 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
     next_particle(P, tab, L, stack);
 }
 
+// ------------------------------------------------------------------ FP32-mode collision
+__device__ float slope_f(bool like, float p)
+{
+    if (like) {
+        float p8 = p * p;
+        p8 = p8 * p8;
+        p8 = p8 * p8;
+        return 5.5f * p8 / (7.7f + p8);
+    }
+    if (p < 0.225f) return 0.f;
+    if (p < 0.6f) return 16.53f * (p - 0.225f);
+    if (p < 1.6f) return 7.16f - 1.63f * p;
+    return 4.552f;
+}
+
+// FP32 mode: the pair energies, the boost into the pair's CM frame and back, and the
+// products' energies in FP64; the t sampling and the rotation in FP32. Energy and momentum
+// of the pair are conserved to FP64 rounding whatever the FP32 angle error.
+__device__ void collide_mixed(int s1, const float *p1, int s2, const float *p2, float ut, float uphi, float uf,
+                              float *q1, float *q2, double &T1n, double &T2n)
+{
+    const double m1 = nucleon_mass(s1), m2 = nucleon_mass(s2);
+    const bool like = s1 == s2;
+    const double P1[3] = {p1[0], p1[1], p1[2]}, P2[3] = {p2[0], p2[1], p2[2]};
+    const double E1 = sqrt(dot3(P1, P1) + m1 * m1), E2 = sqrt(dot3(P2, P2) + m2 * m2);
+    double X = E1 * E2 - dot3(P1, P2) - m1 * m2;  // four-product p1.p2 minus m1 m2
+    if (X < 0.0) X = 0.0;
+    const double rs = sqrt((m1 + m2) * (m1 + m2) + 2.0 * X);
+    const double k = sqrt(X * (X + 2.0 * m1 * m2));
+    const double pst = k / rs;
+    const double Et = E1 + E2, iEt = 1.0 / Et;
+    const double beta[3] = {(P1[0] + P2[0]) * iEt, (P1[1] + P2[1]) * iEt, (P1[2] + P2[2]) * iEt};
+    const double gamma = Et / rs;
+    const double g2 = gamma * gamma / (gamma + 1.0);
+    const double f = g2 * dot3(beta, P1) - gamma * E1;
+    float n[3] = {(float)(P1[0] + beta[0] * f), (float)(P1[1] + beta[1] * f), (float)(P1[2] + beta[2] * f)};
+    const float rn = rsqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    n[0] *= rn;
+    n[1] *= rn;
+    n[2] *= rn;
+    const float plab = (float)(k / m2) * 1e-3f;
+    const float pg = (float)pst * 1e-3f;
+    const float b = 4.f * slope_f(like, plab) * pg * pg;
+    const float y = b > 0.f ? -log1pf(ut * expm1f(-b)) / b : ut;
+    float ct = 1.f - 2.f * y;
+    if (!like) {
+        float a = plab <= 0.8f ? 1.f : (0.8f / plab) * (0.8f / plab);
+        if (uf < a / (1.f + a)) ct = -ct;
+    }
+    const float st = sqrtf((1.f - ct) * (1.f + ct));
+    float sp, cp;
+    __sincosf(6.2831853f * uphi, &sp, &cp);
+    float d[3];
+    const float rho = sqrtf(n[0] * n[0] + n[1] * n[1]);
+    if (rho > 0.f) {
+        const float ir = 1.f / rho;
+        d[0] = ct * n[0] + st * (cp * n[0] * n[2] * ir - sp * n[1] * ir);
+        d[1] = ct * n[1] + st * (cp * n[1] * n[2] * ir + sp * n[0] * ir);
+        d[2] = ct * n[2] - st * cp * rho;
+    } else {
+        d[0] = st * cp;
+        d[1] = st * sp;
+        d[2] = (n[2] >= 0.f ? 1.f : -1.f) * ct;
+    }
+    const double K[3] = {pst * d[0], pst * d[1], pst * d[2]};
+    const double e1 = sqrt(pst * pst + m1 * m1), e2 = sqrt(pst * pst + m2 * m2);
+    const double bk = dot3(beta, K);
+    const double f1 = g2 * bk + gamma * e1, f2 = -g2 * bk + gamma * e2;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        q1[c] = (float)(K[c] + beta[c] * f1);
+        q2[c] = (float)(-K[c] + beta[c] * f2);
+    }
+    T1n = gamma * (e1 + bk) - m1;
+    T2n = gamma * (e2 - bk) - m2;
+}
+
+template <typename R>
+__device__ void collide_lane(int s1, const R *p1, int s2, const R *p2, R ut, R uph, R uf, R *q1, R *q2, double &T1n,
+                             double &T2n);
+template <>
+__device__ void collide_lane<double>(int s1, const double *p1, int s2, const double *p2, double ut, double uph,
+                                     double uf, double *q1, double *q2, double &T1n, double &T2n)
+{
+    collide(s1, p1, s2, p2, ut, uph, uf, q1, q2);
+    T1n = kinetic(dot3(q1, q1), nucleon_mass(s1));
+    T2n = kinetic(dot3(q2, q2), nucleon_mass(s2));
+}
+template <>
+__device__ void collide_lane<float>(int s1, const float *p1, int s2, const float *p2, float ut, float uph, float uf,
+                                    float *q1, float *q2, double &T1n, double &T2n)
+{
+    collide_mixed(s1, p1, s2, p2, ut, uph, uf, q1, q2, T1n, T2n);
+}
+
+// Completes the lane's accepted candidate (§2.3): elastic kinematics, Pauli blocking,
+// then the cutoff of each product; the struck nucleon goes on the stack.
+template <typename R, bool kCount>
+__device__ void finish_collision(const SimParams &P, const ShellTable<R> &t, const TargetScalars &tab, Lane<R> &L,
+                                 Particle<R> *stack, Counters<kCount> &C)
+{
+    const int s1 = L.s, s2 = L.js, i = L.shell;
+    const R ut = L.rng.next(), uph = L.rng.next(), uf = L.rng.next();
+    R q1[3], q2[3];
+    double T1n, T2n;
+    collide_lane<R>(s1, L.p, s2, L.jp, ut, uph, uf, q1, q2, T1n, T2n);
+    L.phase = kTransport;
+    if (!(T1n > (double)t.EF[s1][i] && T2n > (double)t.EF[s2][i])) {
+        C.add(PNUC_C_PAULI_BLOCKED);
+        return;
+    }
+    C.add(PNUC_C_COLLISIONS);
+    ++L.n_coll;
+    double cut2 = (double)t.V[s2][i] + (s2 == 1 ? (double)t.EC : 0.0);
+    double cut1 = (double)t.V[s1][i] + (s1 == 1 ? (double)t.EC : 0.0);
+    if (T2n < cut2) {
+        C.add(PNUC_C_CAPTURES);
+    } else if (L.sp >= kStackCap) {
+        L.flags |= PNUC_FLAG_STACK_OVERFLOW;
+        C.add(PNUC_C_CAPTURES);
+    } else {
+        Particle<R> &np = stack[L.sp++];
+        np.r[0] = L.r[0];
+        np.r[1] = L.r[1];
+        np.r[2] = L.r[2];
+        np.p[0] = q2[0];
+        np.p[1] = q2[1];
+        np.p[2] = q2[2];
+        np.s = s2;
+        np.shell = i;
+    }
+    L.p[0] = q1[0];
+    L.p[1] = q1[1];
+    L.p[2] = q1[2];
+    if (T1n < cut1) {
+        C.add(PNUC_C_CAPTURES);
+        next_particle(P, tab, L, stack);
+    }
+}
+
+// ------------------------------------------------------------------ evaporation step
 // Rejection sampler of t on [0, x] (four draws per trial); returns -1 after max_trials.
 template <typename R>
 __device__ R sample_t(Stream<R> &rng, R a, R x, R b, int max_trials, int &trials)
@@ -691,6 +741,82 @@ __device__ R sample_t(Stream<R> &rng, R a, R x, R b, int max_trials, int &trials
     return R(-1);
 }
 
+// Channel parameters in precision R (Q-values and daughter masses in FP64).
+template <typename R>
+struct ChanP {
+    double Q, Md;
+    R V, b, a, x, w0;  // barrier, offset, level-density parameter, 2 sqrt(aY), g m c A^(2/3)
+    bool open;
+};
+
+template <typename R>
+__device__ void channel_params(const SimParams &P, int Z, int A, double Mparent, double Estar, int j, ChanP<R> &c)
+{
+    c.open = false;
+    c.x = R(0);
+    const int Zd = Z - cEjZ[j], Ad = A - cEjA[j];
+    if (Zd < 1 || Ad - Zd < 1 || Ad < 5) return;
+    const double Md = __ldg(&P.mass[Zd * kMassA + Ad]);
+    const double Q = Md + cEjM[j] - Mparent;
+    const R A3 = (R)__ldg(&P.cbrtA[Ad]);
+    R V, b, cj;
+    if (cEjZ[j] == 0) {
+        R alpha = R(0.76) + R(1.93) / A3;
+        R beta = (R(1.66) / (A3 * A3) - R(0.05)) / alpha;
+        V = beta < R(0) ? -beta : R(0);
+        b = beta > R(0) ? beta : R(0);
+        cj = alpha;
+    } else {
+        V = R(kE2) * cEjZ[j] * Zd / (R(1.5) * ((R)__ldg(&P.cbrtA[cEjA[j]]) + A3));
+        b = R(0);
+        cj = R(1);
+    }
+    const R X = (R)(Estar - Q);
+    const R Y = X - V;
+    c.Q = Q;
+    c.Md = Md;
+    c.V = V;
+    c.b = b;
+    c.a = R(Ad) / R(8);
+    if (!(Y > R(0))) return;
+    c.x = R(2) * sqrt(c.a * Y);
+    c.w0 = (R)cEjG[j] * (R)cEjM[j] * cj * (A3 * A3);
+    c.open = true;
+}
+
+// F(x) = e^x (x^2 - 3x + 3) + x^2/2 - 3 and G(x) = e^x (x - 1) + 1 with the exponential in
+// FP64 (it reaches e^160); the polynomials in precision R; series below x = 1.
+template <typename R>
+__device__ void width_FG_R(R x, double &F, double &G)
+{
+    if (x >= R(1)) {
+        double ex = exp((double)x);
+        F = ex * (double)(x * x - R(3) * x + R(3)) + (double)(R(0.5) * x * x) - 3.0;
+        G = ex * (double)(x - R(1)) + 1.0;
+        return;
+    }
+    R term = x, f = R(0), g = R(0);  // term = x^n / n!
+#pragma unroll 1
+    for (int n = 2; n <= 20; ++n) {
+        term *= x / R(n);
+        g += R(n - 1) * term;
+        if (n >= 4) f += R((n - 1) * (n - 3)) * term;
+    }
+    F = (double)f;
+    G = (double)g;
+}
+
+template <typename R>
+__device__ double channel_width(const ChanP<R> &c)
+{
+    if (!c.open) return 0.0;
+    double F, G;
+    width_FG_R<R>(c.x, F, G);
+    const double a = (double)c.a;
+    const double I = F / (4.0 * a * a) + (double)c.b * G / (2.0 * a);
+    return (double)c.w0 * I;
+}
+
 // One evaporation step (§2.4): widths of the six channels, the channel draw, the emission
 // energy, and the two-body decay isotropic in the parent's rest frame, boosted to the lab.
 template <typename R, bool kCount>
@@ -705,11 +831,11 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     const double Mparent = __ldg(&P.mass[Z * kMassA + A]);
     const double Estar = L.Estar;
     double G[6], S = 0.0;
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < 6; ++j) {
-        Channel c;
-        channel(P, Z, A, Mparent, Estar, j, c);
-        G[j] = c.width;
+        ChanP<R> c;
+        channel_params<R>(P, Z, A, Mparent, Estar, j, c);
+        G[j] = channel_width<R>(c);
         S += G[j];
     }
     if (!(S > 0.0)) {
@@ -719,7 +845,7 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     C.add(PNUC_C_EVAP_STEPS);
     double us = (double)L.rng.next() * S, cum = 0.0;
     int ch = -1;
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < 6; ++j) {
         cum += G[j];
         if (ch < 0 && us < cum) ch = j;
@@ -730,41 +856,41 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
                 ch = j;
                 break;
             }
-    Channel c;
-    channel(P, Z, A, Mparent, Estar, ch, c);
+    ChanP<R> c;
+    channel_params<R>(P, Z, A, Mparent, Estar, ch, c);
     int trials = 0;
-    R tt = sample_t<R>(L.rng, (R)c.a, (R)c.x, (R)c.b, P.max_evap_trials, trials);
+    R tt = sample_t<R>(L.rng, c.a, c.x, c.b, P.max_evap_trials, trials);
     C.add(PNUC_C_EVAP_TRIALS, trials);
     if (tt < R(0)) {
         L.flags |= PNUC_FLAG_EVAP_TRIAL_CAP;
         L.phase = kFinish;
         return;
     }
-    double xt = c.x - (double)tt;
-    double Ud = xt * xt / (4.0 * c.a);
-    double X = Estar - c.Q;
-    double eps = X - Ud;
-    double W = Mparent + Estar;
-    double m1 = cEjM[ch], m2 = c.Md + Ud;
-    double pd = sqrt(eps * (W + m1 + m2) * (W - m1 + m2) * (W + m1 - m2)) / (2.0 * W);
-    double ct = 2.0 * (double)L.rng.next() - 1.0;
-    double ph = kTwoPi * (double)L.rng.next();
-    double sn = sqrt((1.0 - ct) * (1.0 + ct));
-    double sph, cph;
-    sincos(ph, &sph, &cph);
-    double pv[3] = {pd * sn * cph, pd * sn * sph, pd * ct};
-    double e1 = sqrt(pd * pd + m1 * m1);
-    double Pr[3] = {L.Prx, L.Pry, L.Prz};
-    double Er = L.Er;
-    double Pm = sqrt(dot3(Pr, Pr));
-    double gamma = Er / sqrt((Er - Pm) * (Er + Pm));
-    double beta[3] = {Pr[0] / Er, Pr[1] / Er, Pr[2] / Er};
+    const double xt = (double)c.x - (double)tt;
+    const double Ud = xt * xt / (4.0 * (double)c.a);
+    const double X = Estar - c.Q;
+    const double eps = X - Ud;
+    const double W = Mparent + Estar;
+    const double m1 = cEjM[ch], m2 = c.Md + Ud;
+    const double pd = sqrt(eps * (W + m1 + m2) * (W - m1 + m2) * (W + m1 - m2)) / (2.0 * W);
+    const R ctr = R(2) * L.rng.next() - R(1);
+    const R phr = R(kTwoPi) * L.rng.next();
+    const R snr = sqrt((R(1) - ctr) * (R(1) + ctr));
+    R sphr, cphr;
+    sincos(phr, &sphr, &cphr);
+    const double pv[3] = {pd * (double)snr * (double)cphr, pd * (double)snr * (double)sphr, pd * (double)ctr};
+    const double e1 = sqrt(pd * pd + m1 * m1);
+    const double Pr[3] = {L.Prx, L.Pry, L.Prz};
+    const double Er = L.Er;
+    const double Pm = sqrt(dot3(Pr, Pr));
+    const double gamma = Er / sqrt((Er - Pm) * (Er + Pm));
+    const double beta[3] = {Pr[0] / Er, Pr[1] / Er, Pr[2] / Er};
     double pl[3];
     boost(beta, gamma, 1.0, e1, pv, pl);
-    double el = gamma * (e1 + dot3(beta, pv));
-    double pl2 = dot3(pl, pl);
-    double Tl = kinetic(pl2, m1);
-    double pln = sqrt(pl2);
+    const double el = gamma * (e1 + dot3(beta, pv));
+    const double pl2 = dot3(pl, pl);
+    const double Tl = kinetic(pl2, m1);
+    const double pln = sqrt(pl2);
     emit_secondary(P, L.ev, ch, 1, L.n_index++, Tl, (float)(pl[0] / pln), (float)(pl[1] / pln), (float)(pl[2] / pln),
                    L.flags);
     ++L.n_evap;
@@ -777,13 +903,15 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     L.Estar = Ud;
 }
 
-// Advances lane L by one step of its current phase.
+// Advances lane L by one step of its current phase (no batching: the plain kernel).
 template <typename R, bool kCount>
 __device__ __forceinline__ void step(const SimParams &P, const ShellTable<R> *sh, const TargetScalars *tabs, Lane<R> &L,
                                      Particle<R> *stack, Counters<kCount> &C)
 {
     if (L.phase == kTransport) {
         step_transport<R, kCount>(P, sh[L.tgt], tabs[L.tgt], L, stack, C);
+    } else if (L.phase == kKinWait) {
+        finish_collision<R, kCount>(P, sh[L.tgt], tabs[L.tgt], L, stack, C);
     } else if (L.phase == kEntry) {
         step_entry<R, kCount>(P, sh[L.tgt], tabs[L.tgt].R, L, C);
     } else if (L.phase == kEvap) {

@@ -60,6 +60,7 @@ struct SimParams {
     unsigned long long *queue_head;  // persistent method: next unclaimed event
     int32_t max_steps, max_attempts, max_evap_steps, max_evap_trials;
     int32_t refill_threshold, chunk;
+    int32_t kin_batch, evap_batch;  // persistent kernel: lanes a warp gathers before FP64-heavy work
 };
 
 // Launchers, one per compiled variant (kernel_fp32.cu, kernel_fp64.cu).
@@ -70,6 +71,9 @@ cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool
 // Resident blocks per SM of the persistent kernels at a block size.
 int occupancy_persistent_fp64(int block);
 int occupancy_persistent_fp32(int block, bool count);
+
+// Pipe microbenchmarks (microbench.cu): FP32 FMA, FP64 FMA, MUFU, INT32 MAD lane ops/s.
+cudaError_t measure_peaks(int sm_count, double out[4]);
 
 // Table builders (tables.cu).
 cudaError_t launch_mass_table(double *mass, double *cbrtA, cudaStream_t s);

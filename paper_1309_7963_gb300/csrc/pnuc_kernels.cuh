@@ -107,7 +107,8 @@ __global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
             L.phase = kIdle;
         }
         const unsigned idle = __ballot_sync(FULL, L.phase == kIdle);
-        const unsigned busy = __ballot_sync(FULL, L.phase == kEntry || L.phase == kTransport || L.phase == kEvap);
+        const unsigned busy = __ballot_sync(FULL, L.phase == kEntry || L.phase == kTransport || L.phase == kEvap ||
+                                                      L.phase == kKinWait);
         const int nidle = __popc(idle);
         if (nidle && (nidle >= P.refill_threshold || busy == 0 || drained)) {
             const unsigned rank = __popc(idle & ((1u << lane) - 1u));
@@ -138,7 +139,23 @@ __global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
             }
         }
         if (__all_sync(FULL, L.phase == kExhausted)) break;
-        step<R, kCount>(P, sh, ts, L, stack, C);
+        // FP64-heavy work (collision kinematics, evaporation steps) runs when enough lanes of
+        // the warp need it, or when nothing else can progress, so that it executes with many
+        // lanes active; the others keep transporting meanwhile.
+        const unsigned run = __ballot_sync(FULL, L.phase == kEntry || L.phase == kTransport);
+        const unsigned kin = __ballot_sync(FULL, L.phase == kKinWait);
+        const unsigned evp = __ballot_sync(FULL, L.phase == kEvap);
+        const bool do_kin = kin && (__popc(kin) >= P.kin_batch || run == 0);
+        const bool do_evap = evp && (__popc(evp) >= P.evap_batch || (run == 0 && kin == 0));
+        if (L.phase == kKinWait) {
+            if (do_kin) finish_collision<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+        } else if (L.phase == kEvap) {
+            if (do_evap) step_evap<R, kCount>(P, L, C);
+        } else if (L.phase == kTransport) {
+            step_transport<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+        } else if (L.phase == kEntry) {
+            step_entry<R, kCount>(P, sh[L.tgt], ts[L.tgt].R, L, C);
+        }
     }
     flush_counters<kCount>(P, cnt);
 }

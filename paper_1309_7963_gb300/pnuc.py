@@ -52,7 +52,7 @@ class pnuc_output(C.Structure):
 
 class pnuc_tuning(C.Structure):
     _fields_ = [("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_threshold", C.c_int32),
-                ("chunk", C.c_int32)]
+                ("chunk", C.c_int32), ("kin_batch", C.c_int32), ("evap_batch", C.c_int32)]
 
 
 class pnuc_target_info(C.Structure):
@@ -60,6 +60,10 @@ class pnuc_target_info(C.Structure):
                 ("S_n", C.c_double), ("S_p", C.c_double), ("r", C.c_double * 16), ("rho", C.c_double * 15),
                 ("vF", C.c_double * 15), ("pF", (C.c_double * 15) * 2), ("EF", (C.c_double * 15) * 2),
                 ("V", (C.c_double * 15) * 2)]
+
+
+class pnuc_peaks(C.Structure):
+    _fields_ = [("fp32_fma", C.c_double), ("fp64_fma", C.c_double), ("mufu", C.c_double), ("int32_mad", C.c_double)]
 
 
 class PnucError(RuntimeError):
@@ -96,8 +100,10 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_simulate_host.argtypes = [vp, C.c_int, C.c_int, vp, vp, u64, u64, u64, vp, u64, C.POINTER(u64), vp, vp]
     L.pnuc_get_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
     L.pnuc_set_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
+    L.pnuc_measure_peaks.argtypes = [vp, C.POINTER(pnuc_peaks)]
     for name in ("pnuc_create", "pnuc_destroy", "pnuc_last_error", "pnuc_create_target", "pnuc_target_table",
-                 "pnuc_simulate", "pnuc_simulate_host", "pnuc_get_tuning", "pnuc_set_tuning"):
+                 "pnuc_simulate", "pnuc_simulate_host", "pnuc_get_tuning", "pnuc_set_tuning",
+                 "pnuc_measure_peaks"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -189,14 +195,19 @@ class Context:
     def get_tuning(self, precision: str = "fp32") -> dict:
         t = pnuc_tuning()
         self._check(self.lib.pnuc_get_tuning(self.handle, PRECISION[precision], C.byref(t)))
-        return dict(block_size=t.block_size, blocks_per_sm=t.blocks_per_sm, refill_threshold=t.refill_threshold,
-                    chunk=t.chunk)
+        return {name: getattr(t, name) for name, _ in pnuc_tuning._fields_}
 
     def set_tuning(self, precision: str = "fp32", **kw):
         cur = self.get_tuning(precision)
         cur.update(kw)
         t = pnuc_tuning(**cur)
         self._check(self.lib.pnuc_set_tuning(self.handle, PRECISION[precision], C.byref(t)))
+
+    def measure_peaks(self) -> dict:
+        """Lane operations per second of the FP32 FMA, FP64 FMA, MUFU and INT32 MAD pipes."""
+        p = pnuc_peaks()
+        self._check(self.lib.pnuc_measure_peaks(self.handle, C.byref(p)))
+        return dict(fp32_fma=p.fp32_fma, fp64_fma=p.fp64_fma, mufu=p.mufu, int32_mad=p.int32_mad)
 
     def alloc(self, n: int, capacity: int | None = None, counters: bool = False) -> Result:
         torch = self._torch
