@@ -384,10 +384,13 @@ double orc_boundary_distance(const orc_target *t, int shell, const double r[3], 
         }
     }
     double ro = t->r[shell + 1];
-    double c = q - ro * ro, D = beta * beta - c;
-    if (D < 0.0) D = 0.0;
+    double c = q - ro * ro;
     *dir = 1;
-    if (beta <= 0.0) return -beta + sqrt(D);
+    /* moving inward, the particle is on or inside its outer sphere (it was reflected there
+     * or came from inside): rounding that puts it outside must not shorten the chord */
+    if (beta <= 0.0) return -beta + sqrt(beta * beta - (c > 0.0 ? 0.0 : c));
+    double D = beta * beta - c;
+    if (D < 0.0) D = 0.0;
     double s = -c / (beta + sqrt(D));
     return s > 0.0 ? s : 0.0;
 }

@@ -71,13 +71,15 @@ template <> __device__ __forceinline__ float to_uniform<float>(uint64_t w)
 }
 
 // The event's draw stream: draw d is word d mod 4 of Philox((d div 4, event, 0, 0),
-// (seed, 0)). Four converted words are kept in registers and shifted out in order.
+// (seed, 0)). Up to eight converted words wait in registers; next() shifts the oldest out.
+// Blocks are generated only at ensure(k) points (k <= 5), a few per step, so that lanes
+// at the same point of the step generate together and the Philox code exists a few times.
 template <typename R>
 struct Stream {
     uint64_t seed, event;
     uint32_t block;
     int left;
-    R q0, q1, q2, q3;
+    R q0, q1, q2, q3, q4, q5, q6, q7;
     __device__ void reset(uint64_t s, uint64_t e)
     {
         seed = s;
@@ -85,22 +87,43 @@ struct Stream {
         block = 0;
         left = 0;
     }
-    __device__ R next()
+    __device__ __forceinline__ void put(int k, R v)
     {
-        if (left == 0) {
+        switch (k) {
+        case 0: q0 = v; break;
+        case 1: q1 = v; break;
+        case 2: q2 = v; break;
+        case 3: q3 = v; break;
+        case 4: q4 = v; break;
+        case 5: q5 = v; break;
+        case 6: q6 = v; break;
+        default: q7 = v; break;
+        }
+    }
+    __device__ __forceinline__ void ensure(int k)
+    {
+#pragma unroll 1
+        while (left < k) {
             uint64_t w0, w1, w2, w3;
             philox4x64_10(block, event, seed, 0, w0, w1, w2, w3);
             ++block;
-            q0 = to_uniform<R>(w0);
-            q1 = to_uniform<R>(w1);
-            q2 = to_uniform<R>(w2);
-            q3 = to_uniform<R>(w3);
-            left = 4;
+            put(left, to_uniform<R>(w0));
+            put(left + 1, to_uniform<R>(w1));
+            put(left + 2, to_uniform<R>(w2));
+            put(left + 3, to_uniform<R>(w3));
+            left += 4;
         }
+    }
+    __device__ __forceinline__ R next()
+    {
         R u = q0;
         q0 = q1;
         q1 = q2;
         q2 = q3;
+        q3 = q4;
+        q4 = q5;
+        q5 = q6;
+        q6 = q7;
         --left;
         return u;
     }
@@ -182,10 +205,13 @@ __device__ R boundary_distance(const ShellTable<R> &t, int shell, const R *r, co
         }
     }
     R ro = t.r[shell + 1];
-    R c = q - ro * ro, D = beta * beta - c;
-    if (D < R(0)) D = R(0);
+    R c = q - ro * ro;
     dir = 1;
-    if (beta <= R(0)) return -beta + sqrt(D);
+    // moving inward the particle is on or inside its outer sphere: rounding that puts it
+    // outside must not shorten the chord (else it bounces in place at a grazing reflection)
+    if (beta <= R(0)) return -beta + sqrt(beta * beta - (c > R(0) ? R(0) : c));
+    R D = beta * beta - c;
+    if (D < R(0)) D = R(0);
     R s = -c / (beta + sqrt(D));
     return s > R(0) ? s : R(0);
 }
@@ -393,7 +419,8 @@ __device__ void begin_event(const SimParams &P, const TargetScalars *tabs, Lane<
     bool tgt_ok = L.tgt >= 0 && L.tgt < P.n_targets;
     L.Z = L.Zc = tgt_ok ? tabs[L.tgt].Z : 0;
     L.A = L.Ac = tgt_ok ? tabs[L.tgt].A : 0;
-    if (!tgt_ok || !(L.T0 >= 20.0 && L.T0 <= 250.0)) {
+    const R T0r = (R)L.T0;
+    if (!tgt_ok || !(T0r >= R(20) && T0r <= R(250))) {
         L.flags = PNUC_FLAG_BAD_INPUT;
         L.phase = kFinish;
         return;
@@ -412,6 +439,7 @@ __device__ void step_entry(const SimParams &P, const ShellTable<R> &t, double Ra
     }
     ++L.attempts;
     C.add(PNUC_C_ATTEMPTS);
+    L.rng.ensure(2);
     R Rr = (R)Rad;
     R b = Rr * sqrt(L.rng.next());
     R phi = R(kTwoPi) * L.rng.next();
@@ -420,10 +448,10 @@ __device__ void step_entry(const SimParams &P, const ShellTable<R> &t, double Ra
     L.r[0] = b * cphi;
     L.r[1] = b * sphi;
     L.r[2] = -sqrt(Rr * Rr - b * b);
-    double T0 = L.T0;
+    const R T0 = (R)L.T0;
     L.p[0] = R(0);
     L.p[1] = R(0);
-    L.p[2] = (R)sqrt(T0 * T0 + 2.0 * T0 * kMp);
+    L.p[2] = sqrt(T0 * T0 + R(2) * T0 * R(kMp));
     R rr = sqrt(dot3(L.r, L.r));
     R n[3] = {L.r[0] / rr, L.r[1] / rr, L.r[2] / rr};
     refract(n, L.p, (R)kMp, t.V[1][kShells - 1]);
@@ -513,12 +541,14 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
     R sb = boundary_distance(t, i, L.r, d, dir);
     R gh = g_hat<R>(pm, E1, t.vF[i]);
     R Sigma = R(0.1) * t.rho[i] * gh / (pm * R(1e-3));
+    L.rng.ensure(1);
     R s = -log(L.rng.next()) / Sigma;
     if (s < sb) {
         // ---- candidate collision
 #pragma unroll
         for (int k = 0; k < 3; ++k) L.r[k] += s * d[k];
         C.add(PNUC_C_CANDIDATES);
+        L.rng.ensure(5);
         int s2 = (L.rng.next() < t.ZoverA) ? 1 : 0;
         R m2 = (R)nucleon_mass(s2);
         R q = t.pF[s2][i] * cbrt(L.rng.next());
@@ -680,6 +710,7 @@ __device__ void finish_collision(const SimParams &P, const ShellTable<R> &t, con
                                  Particle<R> *stack, Counters<kCount> &C)
 {
     const int s1 = L.s, s2 = L.js, i = L.shell;
+    L.rng.ensure(3);
     const R ut = L.rng.next(), uph = L.rng.next(), uf = L.rng.next();
     R q1[3], q2[3];
     double T1n, T2n;
@@ -727,6 +758,7 @@ __device__ R sample_t(Stream<R> &rng, R a, R x, R b, int max_trials, int &trials
     bool small = x < R(2);
     R pmix = small ? W1 * x / (W1 * x + R(2) * W2) : W1 / (W1 + W2);
     for (int k = 0; k < max_trials; ++k) {
+        rng.ensure(4);
         R um = rng.next(), u1 = rng.next(), u2 = rng.next(), ua = rng.next();
         ++trials;
         bool first = um < pmix;
@@ -843,6 +875,7 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
         return;
     }
     C.add(PNUC_C_EVAP_STEPS);
+    L.rng.ensure(1);
     double us = (double)L.rng.next() * S, cum = 0.0;
     int ch = -1;
 #pragma unroll 1
@@ -873,6 +906,7 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     const double W = Mparent + Estar;
     const double m1 = cEjM[ch], m2 = c.Md + Ud;
     const double pd = sqrt(eps * (W + m1 + m2) * (W - m1 + m2) * (W + m1 - m2)) / (2.0 * W);
+    L.rng.ensure(2);
     const R ctr = R(2) * L.rng.next() - R(1);
     const R phr = R(kTwoPi) * L.rng.next();
     const R snr = sqrt((R(1) - ctr) * (R(1) + ctr));
