@@ -135,6 +135,8 @@ typedef struct {
     int32_t chunk;            /* events a warp takes from the queue per atomic (32 .. 2^20) */
     int32_t kin_batch;        /* accepted collisions a warp gathers before their FP64 kinematics (1..32) */
     int32_t evap_batch;       /* lanes in evaporation a warp gathers before an evaporation step (1..32) */
+    int32_t max_registers;    /* FP32 persistent kernel register cap: 128, 80 or 64 (80 and 64 need
+                                 block_size <= 128); FP64 and counting launches use 128 */
 } pnuc_tuning;
 
 typedef struct pnuc_ctx pnuc_ctx;
@@ -194,6 +196,42 @@ pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_met
 /* Persistent-method tuning of the context (per precision). set checks the ranges above. */
 pnuc_status pnuc_get_tuning(const pnuc_ctx *ctx, pnuc_precision precision, pnuc_tuning *out);
 pnuc_status pnuc_set_tuning(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_tuning *t);
+
+/* Autotuner of the persistent method: from the context's current tuning for `precision`,
+ * a coordinate search over max_registers, block_size, kin_batch, evap_batch,
+ * refill_threshold and chunk (two passes; each candidate timed with CUDA events over `reps`
+ * launches after one warm-up, on the given batch and output buffers, whose contents it
+ * overwrites). The fastest tuning is kept in the context and written to *best (and its
+ * mean launch time in ms to *best_ms); either may be NULL. Tuning never changes an event's
+ * result. Synchronous on `stream`. Errors: PNUC_ERR_ARG for an empty batch or reps outside
+ * [1, 100]; PNUC_ERR_CUDA if a launch fails. Not in the paper (its kernels were hand-sized);
+ * it serves the batched method. */
+pnuc_status pnuc_autotune(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_batch *batch, const pnuc_output *out,
+                          int32_t reps, pnuc_tuning *best, double *best_ms, void *stream);
+
+/* Tuning cache: pnuc_save_tuning writes both precisions' tunings of the context into the
+ * JSON file at `path` under the device's name, keeping other devices' entries (a malformed
+ * file is replaced). pnuc_load_tuning reads them back; PNUC_ERR_RANGE if the file is missing
+ * or has no entry for this device, PNUC_ERR_ARG if it is malformed or a stored tuning is
+ * invalid (the context is then unchanged). */
+pnuc_status pnuc_save_tuning(pnuc_ctx *ctx, const char *path);
+pnuc_status pnuc_load_tuning(pnuc_ctx *ctx, const char *path);
+
+/* CUDA-graph launch plans. pnuc_graph_create captures one pnuc_simulate launch (output
+ * count reset, queue-head reset, event kernel) for fixed batch and output buffers, the
+ * given precision and method and the context's current tuning; pnuc_graph_launch replays
+ * it on `stream` (asynchronous, same results as pnuc_simulate). pnuc_graph_update re-captures
+ * for new buffers, n or seed and updates the executable graph in place when CUDA allows,
+ * else re-instantiates it. A plan owns its queue head, so replays of different plans may run
+ * concurrently; replays of one plan must not overlap. Buffers must stay valid while a plan
+ * that uses them may run. The plan holds pointers into the context: destroy plans before
+ * their context. */
+typedef struct pnuc_graph pnuc_graph;
+pnuc_status pnuc_graph_create(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
+                              const pnuc_output *out, pnuc_graph **graph);
+pnuc_status pnuc_graph_update(pnuc_graph *graph, const pnuc_batch *batch, const pnuc_output *out);
+pnuc_status pnuc_graph_launch(pnuc_graph *graph, void *stream);
+pnuc_status pnuc_graph_destroy(pnuc_graph *graph);
 
 /* Measured throughput of the pipes the event kernels use, in lane operations per second
  * (one fused multiply-add = one operation): FP32 FMA, FP64 FMA, special-function unit

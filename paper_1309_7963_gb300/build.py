@@ -19,10 +19,13 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
 UNITS = {
     "api.cu": [],
+    "autotune.cu": [],
+    "graph.cu": [],
     "tables.cu": [],
     "microbench.cu": [],
     "kernel_fp64.cu": ["--fmad=false"],
     "kernel_fp32.cu": ["--use_fast_math"],
+    "kernel_fp32_capped.cu": ["--use_fast_math"],
 }
 
 

@@ -9,37 +9,9 @@
 #include <algorithm>
 #include <vector>
 
-#include "pnuc_internal.h"
+#include "api_internal.h"
 
-using namespace pnuc;
-
-namespace {
-constexpr int kQueueSlots = 256;      // persistent launches of one context in flight at once
-constexpr int kQueueStride = 16;      // 128-byte spacing between queue heads
-}  // namespace
-
-struct pnuc_ctx {
-    pnuc_config cfg;
-    int sm_count = 0;
-    char err[512] = {0};
-    double *mass = nullptr;   // [kMassZ * kMassA]
-    double *cbrtA = nullptr;  // [kMassA]
-    TargetTable *tables = nullptr;  // [kMaxTargets]
-    std::vector<std::pair<int, int>> targets;
-    unsigned long long *queue = nullptr;  // [kQueueSlots * kQueueStride]
-    unsigned queue_next = 0;
-    pnuc_tuning tuning[2];
-    // staging for pnuc_simulate_host
-    double *h_energies = nullptr;
-    int32_t *h_tids = nullptr;
-    pnuc_residual *h_res = nullptr;
-    uint64_t h_events_cap = 0;
-    pnuc_secondary *h_sec = nullptr;
-    uint64_t h_sec_cap = 0;
-    unsigned long long *h_count = nullptr;
-};
-
-namespace {
+namespace pnuc {
 
 pnuc_status fail(pnuc_ctx *ctx, pnuc_status st, const char *fmt, ...)
 {
@@ -52,15 +24,16 @@ pnuc_status fail(pnuc_ctx *ctx, pnuc_status st, const char *fmt, ...)
     return st;
 }
 
-#define CU(ctx, call)                                                                                 \
-    do {                                                                                              \
-        cudaError_t e_ = (call);                                                                      \
-        if (e_ != cudaSuccess)                                                                        \
-            return fail(ctx, PNUC_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
-                        __FILE__, __LINE__);                                                          \
-    } while (0)
-
+namespace {
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+int occupancy(pnuc_precision prec, int block, bool count, int max_registers)
+{
+    if (prec == PNUC_FP64) return occupancy_persistent_fp64(block);
+    if (!count && max_registers < 128) return occupancy_persistent_fp32_capped(block, max_registers);
+    return occupancy_persistent_fp32(block, count);
+}
+}  // namespace
 
 pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t)
 {
@@ -74,15 +47,84 @@ pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t)
         return fail(ctx, PNUC_ERR_ARG, "chunk %d not in [32, 2^20]", t->chunk);
     if (t->kin_batch < 1 || t->kin_batch > 32 || t->evap_batch < 1 || t->evap_batch > 32)
         return fail(ctx, PNUC_ERR_ARG, "kin_batch %d / evap_batch %d not in [1,32]", t->kin_batch, t->evap_batch);
+    if (t->max_registers != 128 && t->max_registers != 80 && t->max_registers != 64)
+        return fail(ctx, PNUC_ERR_ARG, "max_registers %d not in {128, 80, 64}", t->max_registers);
+    if (t->max_registers < 128 && t->block_size > 128)
+        return fail(ctx, PNUC_ERR_ARG, "max_registers %d needs block_size <= 128", t->max_registers);
     return PNUC_OK;
 }
 
-int occupancy(pnuc_precision prec, int block, bool count)
+pnuc_status check_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
+                        const pnuc_output *out)
 {
-    return prec == PNUC_FP64 ? occupancy_persistent_fp64(block) : occupancy_persistent_fp32(block, count);
+    if (!ctx || !batch || !out) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    if (precision != PNUC_FP32 && precision != PNUC_FP64) return fail(ctx, PNUC_ERR_ARG, "bad precision %d", precision);
+    if (method != PNUC_PLAIN && method != PNUC_PERSISTENT) return fail(ctx, PNUC_ERR_ARG, "bad method %d", method);
+    if (batch->n > 0xFFFFFFFFull) return fail(ctx, PNUC_ERR_ARG, "n = %llu exceeds 2^32-1", (unsigned long long)batch->n);
+    if (!out->count) return fail(ctx, PNUC_ERR_ARG, "out->count is null");
+    if (batch->n > 0 && (!batch->energies || !batch->target_ids || !out->residuals))
+        return fail(ctx, PNUC_ERR_ARG, "null energies, target_ids or residuals");
+    if (out->capacity > 0 && !out->secondaries) return fail(ctx, PNUC_ERR_ARG, "null secondaries with capacity > 0");
+    if (!aligned16(out->secondaries) || !aligned16(out->residuals))
+        return fail(ctx, PNUC_ERR_ARG, "secondaries and residuals must be 16-byte aligned");
+    return PNUC_OK;
 }
 
-}  // namespace
+pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
+                         const pnuc_output *out, cudaStream_t s, const pnuc_tuning &t, unsigned long long *queue_head)
+{
+    CU(ctx, cudaSetDevice(ctx->cfg.device));
+    CU(ctx, cudaMemsetAsync(out->count, 0, sizeof(unsigned long long), s));
+    if (batch->n == 0) return PNUC_OK;
+    SimParams p;
+    p.energies = batch->energies;
+    p.target_ids = batch->target_ids;
+    p.n = batch->n;
+    p.seed = batch->seed;
+    p.first_event_id = batch->first_event_id;
+    p.sec = out->secondaries;
+    p.sec_cap = out->secondaries ? out->capacity : 0;
+    p.sec_count = out->count;
+    p.res = out->residuals;
+    p.counters = out->counters;
+    p.tables = ctx->tables;
+    p.n_targets = (int32_t)ctx->targets.size();
+    p.mass = ctx->mass;
+    p.cbrtA = ctx->cbrtA;
+    p.max_steps = ctx->cfg.max_steps;
+    p.max_attempts = ctx->cfg.max_attempts;
+    p.max_evap_steps = ctx->cfg.max_evap_steps;
+    p.max_evap_trials = ctx->cfg.max_evap_trials;
+    p.refill_threshold = t.refill_threshold;
+    p.chunk = t.chunk;
+    p.kin_batch = t.kin_batch;
+    p.evap_batch = t.evap_batch;
+    p.queue_head = nullptr;
+    const bool count = out->counters != nullptr;
+    cudaError_t e;
+    if (method == PNUC_PLAIN) {
+        e = precision == PNUC_FP64 ? launch_plain_fp64(p, t.block_size, s)
+                                   : launch_plain_fp32(p, t.block_size, count, s);
+    } else {
+        const bool capped = precision == PNUC_FP32 && !count && t.max_registers < 128;
+        int occ = occupancy(precision, t.block_size, count, capped ? t.max_registers : 128);
+        int bps = std::min(t.blocks_per_sm, std::max(occ, 1));
+        unsigned long long grid = (unsigned long long)bps * ctx->sm_count;
+        unsigned long long need = (batch->n + t.block_size - 1) / t.block_size;
+        if (grid > need) grid = need;
+        p.queue_head = queue_head ? queue_head : ctx->queue + (size_t)(ctx->queue_next++ % kQueueSlots) * kQueueStride;
+        CU(ctx, cudaMemsetAsync(p.queue_head, 0, sizeof(unsigned long long), s));
+        if (precision == PNUC_FP64) e = launch_persistent_fp64(p, (int)grid, t.block_size, s);
+        else if (capped) e = launch_persistent_fp32_capped(p, (int)grid, t.block_size, t.max_registers, s);
+        else e = launch_persistent_fp32(p, (int)grid, t.block_size, count, s);
+    }
+    if (e != cudaSuccess) return fail(ctx, PNUC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+    return PNUC_OK;
+}
+
+}  // namespace pnuc
+
+using namespace pnuc;
 
 extern "C" {
 
@@ -135,6 +177,9 @@ pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
     do {
         if (cudaSetDevice(cfg.device) != cudaSuccess) { st = PNUC_ERR_CUDA; break; }
         cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, cfg.device);
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, cfg.device) == cudaSuccess)
+            snprintf(ctx->device_name, sizeof ctx->device_name, "%s", prop.name);
         if (cudaMalloc(&ctx->mass, sizeof(double) * kMassZ * kMassA) != cudaSuccess ||
             cudaMalloc(&ctx->cbrtA, sizeof(double) * kMassA) != cudaSuccess ||
             cudaMalloc(&ctx->tables, sizeof(TargetTable) * kMaxTargets) != cudaSuccess ||
@@ -149,11 +194,12 @@ pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
         for (int p = 0; p < 2; ++p) {
             pnuc_tuning &t = ctx->tuning[p];
             t.block_size = 128;
-            t.refill_threshold = 8;
             t.chunk = 256;
             t.kin_batch = 16;
-            t.evap_batch = 8;
-            int occ = occupancy((pnuc_precision)p, t.block_size, false);
+            t.evap_batch = 16;
+            t.refill_threshold = 4;
+            t.max_registers = 128;
+            int occ = occupancy((pnuc_precision)p, t.block_size, false, 128);
             t.blocks_per_sm = occ > 0 ? occ : 1;
         }
     } while (0);
@@ -249,63 +295,9 @@ pnuc_status pnuc_set_tuning(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_
 pnuc_status pnuc_simulate(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
                           const pnuc_output *out, void *stream)
 {
-    if (!ctx || !batch || !out) return fail(ctx, PNUC_ERR_ARG, "null argument");
-    if (precision != PNUC_FP32 && precision != PNUC_FP64) return fail(ctx, PNUC_ERR_ARG, "bad precision %d", precision);
-    if (method != PNUC_PLAIN && method != PNUC_PERSISTENT) return fail(ctx, PNUC_ERR_ARG, "bad method %d", method);
-    if (batch->n > 0xFFFFFFFFull) return fail(ctx, PNUC_ERR_ARG, "n = %llu exceeds 2^32-1", (unsigned long long)batch->n);
-    if (!out->count) return fail(ctx, PNUC_ERR_ARG, "out->count is null");
-    if (batch->n > 0 && (!batch->energies || !batch->target_ids || !out->residuals))
-        return fail(ctx, PNUC_ERR_ARG, "null energies, target_ids or residuals");
-    if (out->capacity > 0 && !out->secondaries) return fail(ctx, PNUC_ERR_ARG, "null secondaries with capacity > 0");
-    if (!aligned16(out->secondaries) || !aligned16(out->residuals))
-        return fail(ctx, PNUC_ERR_ARG, "secondaries and residuals must be 16-byte aligned");
-    cudaStream_t s = (cudaStream_t)stream;
-    CU(ctx, cudaSetDevice(ctx->cfg.device));
-    CU(ctx, cudaMemsetAsync(out->count, 0, sizeof(unsigned long long), s));
-    if (batch->n == 0) return PNUC_OK;
-    SimParams p;
-    p.energies = batch->energies;
-    p.target_ids = batch->target_ids;
-    p.n = batch->n;
-    p.seed = batch->seed;
-    p.first_event_id = batch->first_event_id;
-    p.sec = out->secondaries;
-    p.sec_cap = out->secondaries ? out->capacity : 0;
-    p.sec_count = out->count;
-    p.res = out->residuals;
-    p.counters = out->counters;
-    p.tables = ctx->tables;
-    p.n_targets = (int32_t)ctx->targets.size();
-    p.mass = ctx->mass;
-    p.cbrtA = ctx->cbrtA;
-    p.max_steps = ctx->cfg.max_steps;
-    p.max_attempts = ctx->cfg.max_attempts;
-    p.max_evap_steps = ctx->cfg.max_evap_steps;
-    p.max_evap_trials = ctx->cfg.max_evap_trials;
-    const pnuc_tuning &t = ctx->tuning[precision];
-    p.refill_threshold = t.refill_threshold;
-    p.chunk = t.chunk;
-    p.kin_batch = t.kin_batch;
-    p.evap_batch = t.evap_batch;
-    p.queue_head = nullptr;
-    const bool count = out->counters != nullptr;
-    cudaError_t e;
-    if (method == PNUC_PLAIN) {
-        e = precision == PNUC_FP64 ? launch_plain_fp64(p, t.block_size, s)
-                                   : launch_plain_fp32(p, t.block_size, count, s);
-    } else {
-        int occ = occupancy(precision, t.block_size, count);
-        int bps = std::min(t.blocks_per_sm, std::max(occ, 1));
-        unsigned long long grid = (unsigned long long)bps * ctx->sm_count;
-        unsigned long long need = (batch->n + t.block_size - 1) / t.block_size;
-        if (grid > need) grid = need;
-        p.queue_head = ctx->queue + (size_t)(ctx->queue_next++ % kQueueSlots) * kQueueStride;
-        CU(ctx, cudaMemsetAsync(p.queue_head, 0, sizeof(unsigned long long), s));
-        e = precision == PNUC_FP64 ? launch_persistent_fp64(p, (int)grid, t.block_size, s)
-                                   : launch_persistent_fp32(p, (int)grid, t.block_size, count, s);
-    }
-    if (e != cudaSuccess) return fail(ctx, PNUC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
-    return PNUC_OK;
+    pnuc_status st = check_batch(ctx, precision, method, batch, out);
+    if (st != PNUC_OK) return st;
+    return launch_batch(ctx, precision, method, batch, out, (cudaStream_t)stream, ctx->tuning[precision], nullptr);
 }
 
 pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const double *energies,

@@ -1,0 +1,61 @@
+// Host-side internals of libpnuc shared by the API translation units (api.cu,
+// autotune.cu, graph.cu): the context object, error helpers and the launch routine.
+#pragma once
+
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "pnuc_internal.h"
+
+namespace pnuc {
+constexpr int kQueueSlots = 256;  // persistent launches of one context in flight at once
+constexpr int kQueueStride = 16;  // 128-byte spacing between queue heads
+}  // namespace pnuc
+
+struct pnuc_ctx {
+    pnuc_config cfg;
+    int sm_count = 0;
+    char device_name[256] = {0};
+    char err[512] = {0};
+    double *mass = nullptr;              // [kMassZ * kMassA]
+    double *cbrtA = nullptr;             // [kMassA]
+    pnuc::TargetTable *tables = nullptr;  // [kMaxTargets]
+    std::vector<std::pair<int, int>> targets;
+    unsigned long long *queue = nullptr;  // [kQueueSlots * kQueueStride]
+    unsigned queue_next = 0;
+    pnuc_tuning tuning[2];
+    // staging for pnuc_simulate_host
+    double *h_energies = nullptr;
+    int32_t *h_tids = nullptr;
+    pnuc_residual *h_res = nullptr;
+    uint64_t h_events_cap = 0;
+    pnuc_secondary *h_sec = nullptr;
+    uint64_t h_sec_cap = 0;
+    unsigned long long *h_count = nullptr;
+};
+
+namespace pnuc {
+
+pnuc_status fail(pnuc_ctx *ctx, pnuc_status st, const char *fmt, ...);
+
+#define CU(ctx, call)                                                                                       \
+    do {                                                                                                    \
+        cudaError_t e_ = (call);                                                                            \
+        if (e_ != cudaSuccess)                                                                              \
+            return ::pnuc::fail(ctx, PNUC_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                __FILE__, __LINE__);                                                        \
+    } while (0)
+
+pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t);
+pnuc_status check_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
+                        const pnuc_output *out);
+// Enqueues the count reset, the queue-head reset and the kernel of one batch on stream s
+// with tuning t. queue_head: the persistent kernel's queue head, or null for the next slot of
+// the context's ring.
+pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
+                         const pnuc_output *out, cudaStream_t s, const pnuc_tuning &t,
+                         unsigned long long *queue_head);
+
+}  // namespace pnuc

@@ -71,35 +71,28 @@ template <> __device__ __forceinline__ float to_uniform<float>(uint64_t w)
 }
 
 // The event's draw stream: draw d is word d mod 4 of Philox((d div 4, event, 0, 0),
-// (seed, 0)). Up to eight converted words wait in registers; next() shifts the oldest out.
-// Blocks are generated only at ensure(k) points (k <= 5), a few per step, so that lanes
-// at the same point of the step generate together and the Philox code exists a few times.
+// (seed, 0)). Converted words wait in a 16-slot ring in shared memory (slot k of thread t
+// at buf[k * stride], stride = block size: conflict-free). Words are generated only by
+// ensure(k), which the kernels call once per loop iteration (and the evaporation sampler
+// once per trial), so lanes generate together and the Philox code exists twice.
+constexpr int kRing = 16;
+
 template <typename R>
 struct Stream {
     uint64_t seed, event;
     uint32_t block;
-    int left;
-    R q0, q1, q2, q3, q4, q5, q6, q7;
+    int left, head;
+    R *buf;
+    int stride;
     __device__ void reset(uint64_t s, uint64_t e)
     {
         seed = s;
         event = e;
         block = 0;
         left = 0;
+        head = 0;
     }
-    __device__ __forceinline__ void put(int k, R v)
-    {
-        switch (k) {
-        case 0: q0 = v; break;
-        case 1: q1 = v; break;
-        case 2: q2 = v; break;
-        case 3: q3 = v; break;
-        case 4: q4 = v; break;
-        case 5: q5 = v; break;
-        case 6: q6 = v; break;
-        default: q7 = v; break;
-        }
-    }
+    // at least k (<= kRing - 3) words available afterwards
     __device__ __forceinline__ void ensure(int k)
     {
 #pragma unroll 1
@@ -107,23 +100,18 @@ struct Stream {
             uint64_t w0, w1, w2, w3;
             philox4x64_10(block, event, seed, 0, w0, w1, w2, w3);
             ++block;
-            put(left, to_uniform<R>(w0));
-            put(left + 1, to_uniform<R>(w1));
-            put(left + 2, to_uniform<R>(w2));
-            put(left + 3, to_uniform<R>(w3));
+            const int t = head + left;
+            buf[((t + 0) & (kRing - 1)) * stride] = to_uniform<R>(w0);
+            buf[((t + 1) & (kRing - 1)) * stride] = to_uniform<R>(w1);
+            buf[((t + 2) & (kRing - 1)) * stride] = to_uniform<R>(w2);
+            buf[((t + 3) & (kRing - 1)) * stride] = to_uniform<R>(w3);
             left += 4;
         }
     }
     __device__ __forceinline__ R next()
     {
-        R u = q0;
-        q0 = q1;
-        q1 = q2;
-        q2 = q3;
-        q3 = q4;
-        q4 = q5;
-        q5 = q6;
-        q6 = q7;
+        R u = buf[head * stride];
+        head = (head + 1) & (kRing - 1);
         --left;
         return u;
     }
@@ -439,7 +427,6 @@ __device__ void step_entry(const SimParams &P, const ShellTable<R> &t, double Ra
     }
     ++L.attempts;
     C.add(PNUC_C_ATTEMPTS);
-    L.rng.ensure(2);
     R Rr = (R)Rad;
     R b = Rr * sqrt(L.rng.next());
     R phi = R(kTwoPi) * L.rng.next();
@@ -541,14 +528,12 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
     R sb = boundary_distance(t, i, L.r, d, dir);
     R gh = g_hat<R>(pm, E1, t.vF[i]);
     R Sigma = R(0.1) * t.rho[i] * gh / (pm * R(1e-3));
-    L.rng.ensure(1);
     R s = -log(L.rng.next()) / Sigma;
     if (s < sb) {
         // ---- candidate collision
 #pragma unroll
         for (int k = 0; k < 3; ++k) L.r[k] += s * d[k];
         C.add(PNUC_C_CANDIDATES);
-        L.rng.ensure(5);
         int s2 = (L.rng.next() < t.ZoverA) ? 1 : 0;
         R m2 = (R)nucleon_mass(s2);
         R q = t.pF[s2][i] * cbrt(L.rng.next());
@@ -623,24 +608,28 @@ __device__ float slope_f(bool like, float p)
     return 4.552f;
 }
 
-// FP32 mode: the pair energies, the boost into the pair's CM frame and back, and the
-// products' energies in FP64; the t sampling and the rotation in FP32. Energy and momentum
-// of the pair are conserved to FP64 rounding whatever the FP32 angle error.
+// FP32 mode: kinetic energies, the pair invariant and the angular sampling in FP32; the
+// boost of the pair into its CM frame and back and the products' energies in FP64. The
+// boost is built from E = m + T and the pair's own s = E_t^2 - P^2, so it is an exact
+// Lorentz transformation and conserves the pair's energy and momentum to FP64 rounding.
 __device__ void collide_mixed(int s1, const float *p1, int s2, const float *p2, float ut, float uphi, float uf,
                               float *q1, float *q2, double &T1n, double &T2n)
 {
     const double m1 = nucleon_mass(s1), m2 = nucleon_mass(s2);
+    const float m1f = (float)m1, m2f = (float)m2;
     const bool like = s1 == s2;
-    const double P1[3] = {p1[0], p1[1], p1[2]}, P2[3] = {p2[0], p2[1], p2[2]};
-    const double E1 = sqrt(dot3(P1, P1) + m1 * m1), E2 = sqrt(dot3(P2, P2) + m2 * m2);
-    double X = E1 * E2 - dot3(P1, P2) - m1 * m2;  // four-product p1.p2 minus m1 m2
-    if (X < 0.0) X = 0.0;
-    const double rs = sqrt((m1 + m2) * (m1 + m2) + 2.0 * X);
-    const double k = sqrt(X * (X + 2.0 * m1 * m2));
-    const double pst = k / rs;
-    const double Et = E1 + E2, iEt = 1.0 / Et;
-    const double beta[3] = {(P1[0] + P2[0]) * iEt, (P1[1] + P2[1]) * iEt, (P1[2] + P2[2]) * iEt};
-    const double gamma = Et / rs;
+    const float T1 = kinetic(dot3(p1, p1), m1f), T2 = kinetic(dot3(p2, p2), m2f);
+    float Xf = T1 * T2 + T1 * m2f + T2 * m1f - dot3(p1, p2);  // four-product p1.p2 - m1 m2
+    if (Xf < 0.f) Xf = 0.f;
+    const float kf = sqrtf(Xf * (Xf + 2.f * m1f * m2f));        // sqrt(s) p* = m2 p_lab
+    const double P1[3] = {p1[0], p1[1], p1[2]};
+    const double P[3] = {P1[0] + (double)p2[0], P1[1] + (double)p2[1], P1[2] + (double)p2[2]};
+    const double E1 = m1 + (double)T1, Et = E1 + (m2 + (double)T2);
+    const double s = Et * Et - dot3(P, P);
+    const double irs = rsqrt(s);
+    const double iEt = 1.0 / Et;
+    const double beta[3] = {P[0] * iEt, P[1] * iEt, P[2] * iEt};
+    const double gamma = Et * irs;
     const double g2 = gamma * gamma / (gamma + 1.0);
     const double f = g2 * dot3(beta, P1) - gamma * E1;
     float n[3] = {(float)(P1[0] + beta[0] * f), (float)(P1[1] + beta[1] * f), (float)(P1[2] + beta[2] * f)};
@@ -648,7 +637,8 @@ __device__ void collide_mixed(int s1, const float *p1, int s2, const float *p2, 
     n[0] *= rn;
     n[1] *= rn;
     n[2] *= rn;
-    const float plab = (float)(k / m2) * 1e-3f;
+    const float plab = kf / m2f * 1e-3f;
+    const double pst = (double)kf * irs;
     const float pg = (float)pst * 1e-3f;
     const float b = 4.f * slope_f(like, plab) * pg * pg;
     const float y = b > 0.f ? -log1pf(ut * expm1f(-b)) / b : ut;
@@ -673,7 +663,8 @@ __device__ void collide_mixed(int s1, const float *p1, int s2, const float *p2, 
         d[2] = (n[2] >= 0.f ? 1.f : -1.f) * ct;
     }
     const double K[3] = {pst * d[0], pst * d[1], pst * d[2]};
-    const double e1 = sqrt(pst * pst + m1 * m1), e2 = sqrt(pst * pst + m2 * m2);
+    const double hs = 0.5 * irs;
+    const double e1 = (s + m1 * m1 - m2 * m2) * hs, e2 = (s + m2 * m2 - m1 * m1) * hs;  // CM energies
     const double bk = dot3(beta, K);
     const double f1 = g2 * bk + gamma * e1, f2 = -g2 * bk + gamma * e2;
 #pragma unroll
@@ -710,7 +701,6 @@ __device__ void finish_collision(const SimParams &P, const ShellTable<R> &t, con
                                  Particle<R> *stack, Counters<kCount> &C)
 {
     const int s1 = L.s, s2 = L.js, i = L.shell;
-    L.rng.ensure(3);
     const R ut = L.rng.next(), uph = L.rng.next(), uf = L.rng.next();
     R q1[3], q2[3];
     double T1n, T2n;
@@ -758,7 +748,7 @@ __device__ R sample_t(Stream<R> &rng, R a, R x, R b, int max_trials, int &trials
     bool small = x < R(2);
     R pmix = small ? W1 * x / (W1 * x + R(2) * W2) : W1 / (W1 + W2);
     for (int k = 0; k < max_trials; ++k) {
-        rng.ensure(4);
+        rng.ensure(6);  // four for this trial, and the two decay angles if it is accepted
         R um = rng.next(), u1 = rng.next(), u2 = rng.next(), ua = rng.next();
         ++trials;
         bool first = um < pmix;
@@ -839,14 +829,91 @@ __device__ void width_FG_R(R x, double &F, double &G)
 }
 
 template <typename R>
-__device__ double channel_width(const ChanP<R> &c)
+__device__ double channel_width(const ChanP<R> &c);
+template <>
+__device__ double channel_width<double>(const ChanP<double> &c)
 {
     if (!c.open) return 0.0;
     double F, G;
-    width_FG_R<R>(c.x, F, G);
-    const double a = (double)c.a;
-    const double I = F / (4.0 * a * a) + (double)c.b * G / (2.0 * a);
-    return (double)c.w0 * I;
+    width_FG_R<double>(c.x, F, G);
+    const double a = c.a;
+    const double I = F / (4.0 * a * a) + c.b * G / (2.0 * a);
+    return c.w0 * I;
+}
+template <>
+__device__ double channel_width<float>(const ChanP<float> &c)
+{
+    if (!c.open) return 0.0;
+    double F, G;
+    width_FG_R<float>(c.x, F, G);
+    const float ia = 1.f / c.a;
+    return (double)c.w0 * (F * (double)(0.25f * ia * ia) + G * (double)(0.5f * c.b * ia));
+}
+
+// Two-body decay of the parent (invariant mass W) into an ejectile of mass m1 and a
+// daughter of mass m2 with kinetic energy release eps, isotropic in the parent's rest frame
+// (cos theta = ct, azimuth ph), boosted to the lab with the parent's four-momentum.
+// Writes the ejectile's lab momentum pl, energy el, kinetic energy Tl and direction u.
+template <typename R>
+__device__ void decay_to_lab(double W, double m1, double m2, double eps, R ct, R ph, const Lane<R> &L, double *pl,
+                             double &el, double &Tl, float *u);
+template <>
+__device__ void decay_to_lab<double>(double W, double m1, double m2, double eps, double ct, double ph,
+                                     const Lane<double> &L, double *pl, double &el, double &Tl, float *u)
+{
+    const double pd = sqrt(eps * (W + m1 + m2) * (W - m1 + m2) * (W + m1 - m2)) / (2.0 * W);
+    const double sn = sqrt((1.0 - ct) * (1.0 + ct));
+    double sph, cph;
+    sincos(ph, &sph, &cph);
+    const double pv[3] = {pd * sn * cph, pd * sn * sph, pd * ct};
+    const double e1 = sqrt(pd * pd + m1 * m1);
+    const double Pr[3] = {L.Prx, L.Pry, L.Prz};
+    const double Er = L.Er;
+    const double Pm = sqrt(dot3(Pr, Pr));
+    const double gamma = Er / sqrt((Er - Pm) * (Er + Pm));
+    const double beta[3] = {Pr[0] / Er, Pr[1] / Er, Pr[2] / Er};
+    boost(beta, gamma, 1.0, e1, pv, pl);
+    el = gamma * (e1 + dot3(beta, pv));
+    const double pl2 = dot3(pl, pl);
+    Tl = kinetic(pl2, m1);
+    const double pln = sqrt(pl2);
+    u[0] = (float)(pl[0] / pln);
+    u[1] = (float)(pl[1] / pln);
+    u[2] = (float)(pl[2] / pln);
+}
+// FP32 mode: rest-frame momentum and angles in FP32 (the factors of p^2 are all positive,
+// so there is no cancellation); the lab boost, the lab energy and the parent's four-momentum
+// bookkeeping in FP64.
+template <>
+__device__ void decay_to_lab<float>(double W, double m1, double m2, double eps, float ct, float ph,
+                                    const Lane<float> &L, double *pl, double &el, double &Tl, float *u)
+{
+    const float ef = (float)eps, m1f = (float)m1, m2f = (float)m2, Wf = (float)W;
+    const float pd2 = ef * (2.f * (m1f + m2f) + ef) * (2.f * m2f + ef) * (2.f * m1f + ef) / (4.f * Wf * Wf);
+    const float pd = sqrtf(pd2);
+    const float tcm = pd2 / (sqrtf(pd2 + m1f * m1f) + m1f);  // rest-frame kinetic energy
+    const float sn = sqrtf((1.f - ct) * (1.f + ct));
+    float sph, cph;
+    __sincosf(ph, &sph, &cph);
+    const double pv[3] = {(double)(pd * sn * cph), (double)(pd * sn * sph), (double)(pd * ct)};
+    const double e1 = m1 + (double)tcm;
+    const double Pr[3] = {L.Prx, L.Pry, L.Prz};
+    const double Er = L.Er;
+    const double M2 = Er * Er - dot3(Pr, Pr);
+    const double iEr = 1.0 / Er;
+    const double gamma = Er * rsqrt(M2);
+    const double beta[3] = {Pr[0] * iEr, Pr[1] * iEr, Pr[2] * iEr};
+    const double bp = dot3(beta, pv);
+    const double f = gamma * gamma / (gamma + 1.0) * bp + gamma * e1;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) pl[k] = pv[k] + beta[k] * f;
+    el = gamma * (e1 + bp);
+    Tl = el - m1;
+    const float plf[3] = {(float)pl[0], (float)pl[1], (float)pl[2]};
+    const float r = rsqrtf(plf[0] * plf[0] + plf[1] * plf[1] + plf[2] * plf[2]);
+    u[0] = plf[0] * r;
+    u[1] = plf[1] * r;
+    u[2] = plf[2] * r;
 }
 
 // One evaporation step (§2.4): widths of the six channels, the channel draw, the emission
@@ -863,11 +930,11 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     const double Mparent = __ldg(&P.mass[Z * kMassA + A]);
     const double Estar = L.Estar;
     double G[6], S = 0.0;
+    ChanP<R> chans[6];  // kept for the chosen channel
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) {
-        ChanP<R> c;
-        channel_params<R>(P, Z, A, Mparent, Estar, j, c);
-        G[j] = channel_width<R>(c);
+        channel_params<R>(P, Z, A, Mparent, Estar, j, chans[j]);
+        G[j] = channel_width<R>(chans[j]);
         S += G[j];
     }
     if (!(S > 0.0)) {
@@ -875,7 +942,6 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
         return;
     }
     C.add(PNUC_C_EVAP_STEPS);
-    L.rng.ensure(1);
     double us = (double)L.rng.next() * S, cum = 0.0;
     int ch = -1;
 #pragma unroll 1
@@ -889,8 +955,7 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
                 ch = j;
                 break;
             }
-    ChanP<R> c;
-    channel_params<R>(P, Z, A, Mparent, Estar, ch, c);
+    const ChanP<R> c = chans[ch];
     int trials = 0;
     R tt = sample_t<R>(L.rng, c.a, c.x, c.b, P.max_evap_trials, trials);
     C.add(PNUC_C_EVAP_TRIALS, trials);
@@ -901,37 +966,18 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     }
     const double xt = (double)c.x - (double)tt;
     const double Ud = xt * xt / (4.0 * (double)c.a);
-    const double X = Estar - c.Q;
-    const double eps = X - Ud;
-    const double W = Mparent + Estar;
-    const double m1 = cEjM[ch], m2 = c.Md + Ud;
-    const double pd = sqrt(eps * (W + m1 + m2) * (W - m1 + m2) * (W + m1 - m2)) / (2.0 * W);
-    L.rng.ensure(2);
+    const double eps = (Estar - c.Q) - Ud;
     const R ctr = R(2) * L.rng.next() - R(1);
     const R phr = R(kTwoPi) * L.rng.next();
-    const R snr = sqrt((R(1) - ctr) * (R(1) + ctr));
-    R sphr, cphr;
-    sincos(phr, &sphr, &cphr);
-    const double pv[3] = {pd * (double)snr * (double)cphr, pd * (double)snr * (double)sphr, pd * (double)ctr};
-    const double e1 = sqrt(pd * pd + m1 * m1);
-    const double Pr[3] = {L.Prx, L.Pry, L.Prz};
-    const double Er = L.Er;
-    const double Pm = sqrt(dot3(Pr, Pr));
-    const double gamma = Er / sqrt((Er - Pm) * (Er + Pm));
-    const double beta[3] = {Pr[0] / Er, Pr[1] / Er, Pr[2] / Er};
-    double pl[3];
-    boost(beta, gamma, 1.0, e1, pv, pl);
-    const double el = gamma * (e1 + dot3(beta, pv));
-    const double pl2 = dot3(pl, pl);
-    const double Tl = kinetic(pl2, m1);
-    const double pln = sqrt(pl2);
-    emit_secondary(P, L.ev, ch, 1, L.n_index++, Tl, (float)(pl[0] / pln), (float)(pl[1] / pln), (float)(pl[2] / pln),
-                   L.flags);
+    double pl[3], el, Tl;
+    float u[3];
+    decay_to_lab(Mparent + Estar, cEjM[ch], c.Md + Ud, eps, ctr, phr, L, pl, el, Tl, u);
+    emit_secondary(P, L.ev, ch, 1, L.n_index++, Tl, u[0], u[1], u[2], L.flags);
     ++L.n_evap;
-    L.Er = Er - el;
-    L.Prx = Pr[0] - pl[0];
-    L.Pry = Pr[1] - pl[1];
-    L.Prz = Pr[2] - pl[2];
+    L.Er -= el;
+    L.Prx -= pl[0];
+    L.Pry -= pl[1];
+    L.Prz -= pl[2];
     L.Z = Z - cEjZ[ch];
     L.A = A - cEjA[ch];
     L.Estar = Ud;

@@ -37,6 +37,19 @@ __host__ __device__ constexpr size_t table_smem_bytes(int n_targets)
     return (size_t)n_targets * (sizeof(ShellTable<R>) + sizeof(TargetScalars));
 }
 
+// dynamic shared memory: target tables, then each thread's draw ring
+template <typename R>
+__host__ __device__ constexpr size_t smem_bytes(int n_targets, int block)
+{
+    return (table_smem_bytes<R>(n_targets) + 15) / 16 * 16 + (size_t)kRing * sizeof(R) * block;
+}
+
+template <typename R>
+__device__ __forceinline__ R *ring_base(const SimParams &P, unsigned char *smem)
+{
+    return reinterpret_cast<R *>(smem + (table_smem_bytes<R>(P.n_targets) + 15) / 16 * 16) + threadIdx.x;
+}
+
 template <bool kCount>
 __device__ void flush_counters(const SimParams &P, unsigned long long *cnt)
 {
@@ -51,7 +64,7 @@ template <typename R, bool kCount>
 __device__ __forceinline__ void finish_event(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
 {
     write_residual(P, L);
-    C.add(PNUC_C_DRAWS, 4u * L.rng.block - (unsigned)L.rng.left);
+    C.add(PNUC_C_DRAWS, 4u * L.rng.block - (unsigned)L.rng.left);  // generated minus unused
 }
 
 template <typename R, bool kCount>
@@ -70,8 +83,13 @@ __global__ void __launch_bounds__(512) plain_kernel(const SimParams P)
     if (i < P.n) {
         Lane<R> L;
         Particle<R> stack[kStackCap];
+        L.rng.buf = ring_base<R>(P, smem);
+        L.rng.stride = blockDim.x;
         begin_event<R>(P, ts, L, (uint32_t)i);
-        while (L.phase != kFinish) step<R, kCount>(P, sh, ts, L, stack, C);
+        while (L.phase != kFinish) {
+            L.rng.ensure(8);
+            step<R, kCount>(P, sh, ts, L, stack, C);
+        }
         finish_event<R, kCount>(P, L, C);
     }
     flush_counters<kCount>(P, cnt);
@@ -82,7 +100,7 @@ __global__ void __launch_bounds__(512) plain_kernel(const SimParams P)
 // (or no lane is busy) the idle lanes take events from it, and the warp claims a new chunk
 // with one atomicAdd on the queue head when it runs short.
 template <typename R, bool kCount>
-__global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
+__device__ __forceinline__ void persistent_body(const SimParams &P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long cnt[PNUC_N_COUNTERS];
@@ -97,6 +115,8 @@ __global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
     const unsigned lane = threadIdx.x & 31;
     Lane<R> L;
     L.phase = kIdle;
+    L.rng.buf = ring_base<R>(P, smem);
+    L.rng.stride = blockDim.x;
     Particle<R> stack[kStackCap];
     unsigned long long wnext = 0, wend = 0;  // warp-uniform
     bool drained = false;                    // warp-uniform: the queue returned nothing
@@ -147,6 +167,11 @@ __global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
         const unsigned evp = __ballot_sync(FULL, L.phase == kEvap);
         const bool do_kin = kin && (__popc(kin) >= P.kin_batch || run == 0);
         const bool do_evap = evp && (__popc(evp) >= P.evap_batch || (run == 0 && kin == 0));
+        // the iteration's draws: at most 6 in a transport step, 3 in a collision, 2 at an
+        // entry, 1 before the evaporation sampler (which ensures its own)
+        if ((L.phase == kKinWait && do_kin) || (L.phase == kEvap && do_evap) || L.phase == kTransport ||
+            L.phase == kEntry)
+            L.rng.ensure(8);
         if (L.phase == kKinWait) {
             if (do_kin) finish_collision<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
         } else if (L.phase == kEvap) {
@@ -161,10 +186,33 @@ __global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
 }
 
 template <typename R, bool kCount>
+__global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
+{
+    persistent_body<R, kCount>(P);
+}
+
+// Register-capped variants (blocks of at most 128 threads; kMinBlocks resident blocks per
+// SM): 128 / kMinBlocks registers per thread trade spills for resident warps.
+template <typename R, bool kCount, int kMinBlocks>
+__global__ void __launch_bounds__(128, kMinBlocks) persistent_kernel_capped(const SimParams P)
+{
+    persistent_body<R, kCount>(P);
+}
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R, bool kCount>
 cudaError_t launch_plain(const SimParams &p, int block, cudaStream_t s)
 {
     if (p.n == 0) return cudaSuccess;
-    size_t smem = table_smem_bytes<R>(p.n_targets);
+    size_t smem = smem_bytes<R>(p.n_targets, block);
+    cudaError_t e = allow_smem(plain_kernel<R, kCount>, smem);
+    if (e != cudaSuccess) return e;
     unsigned long long grid = (p.n + block - 1) / block;
     plain_kernel<R, kCount><<<(unsigned)grid, block, smem, s>>>(p);
     return cudaGetLastError();
@@ -174,17 +222,41 @@ template <typename R, bool kCount>
 cudaError_t launch_persistent(const SimParams &p, int grid, int block, cudaStream_t s)
 {
     if (p.n == 0) return cudaSuccess;
-    size_t smem = table_smem_bytes<R>(p.n_targets);
+    size_t smem = smem_bytes<R>(p.n_targets, block);
+    cudaError_t e = allow_smem(persistent_kernel<R, kCount>, smem);
+    if (e != cudaSuccess) return e;
     persistent_kernel<R, kCount><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+template <typename R, bool kCount, int kMinBlocks>
+cudaError_t launch_persistent_capped(const SimParams &p, int grid, int block, cudaStream_t s)
+{
+    if (p.n == 0) return cudaSuccess;
+    size_t smem = smem_bytes<R>(p.n_targets, block);
+    cudaError_t e = allow_smem(persistent_kernel_capped<R, kCount, kMinBlocks>, smem);
+    if (e != cudaSuccess) return e;
+    persistent_kernel_capped<R, kCount, kMinBlocks><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename R, bool kCount, int kMinBlocks>
+int occupancy_persistent_capped(int block)
+{
+    int nb = 0;
+    allow_smem(persistent_kernel_capped<R, kCount, kMinBlocks>, smem_bytes<R>(kMaxTargets, block));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel_capped<R, kCount, kMinBlocks>, block,
+                                                  smem_bytes<R>(kMaxTargets, block));
+    return nb;
 }
 
 template <typename R, bool kCount>
 int occupancy_persistent(int block)
 {
     int nb = 0;
+    allow_smem(persistent_kernel<R, kCount>, smem_bytes<R>(kMaxTargets, block));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<R, kCount>, block,
-                                                  table_smem_bytes<R>(kMaxTargets));
+                                                  smem_bytes<R>(kMaxTargets, block));
     return nb;
 }
 

@@ -52,7 +52,8 @@ class pnuc_output(C.Structure):
 
 class pnuc_tuning(C.Structure):
     _fields_ = [("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_threshold", C.c_int32),
-                ("chunk", C.c_int32), ("kin_batch", C.c_int32), ("evap_batch", C.c_int32)]
+                ("chunk", C.c_int32), ("kin_batch", C.c_int32), ("evap_batch", C.c_int32),
+                ("max_registers", C.c_int32)]
 
 
 class pnuc_target_info(C.Structure):
@@ -101,9 +102,18 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_get_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
     L.pnuc_set_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
     L.pnuc_measure_peaks.argtypes = [vp, C.POINTER(pnuc_peaks)]
+    L.pnuc_autotune.argtypes = [vp, C.c_int, C.POINTER(pnuc_batch), C.POINTER(pnuc_output), C.c_int32,
+                                C.POINTER(pnuc_tuning), C.POINTER(C.c_double), vp]
+    L.pnuc_save_tuning.argtypes = [vp, C.c_char_p]
+    L.pnuc_load_tuning.argtypes = [vp, C.c_char_p]
+    L.pnuc_graph_create.argtypes = [vp, C.c_int, C.c_int, C.POINTER(pnuc_batch), C.POINTER(pnuc_output), C.POINTER(vp)]
+    L.pnuc_graph_update.argtypes = [vp, C.POINTER(pnuc_batch), C.POINTER(pnuc_output)]
+    L.pnuc_graph_launch.argtypes = [vp, vp]
+    L.pnuc_graph_destroy.argtypes = [vp]
     for name in ("pnuc_create", "pnuc_destroy", "pnuc_last_error", "pnuc_create_target", "pnuc_target_table",
                  "pnuc_simulate", "pnuc_simulate_host", "pnuc_get_tuning", "pnuc_set_tuning",
-                 "pnuc_measure_peaks"):
+                 "pnuc_measure_peaks", "pnuc_autotune", "pnuc_save_tuning", "pnuc_load_tuning",
+                 "pnuc_graph_create", "pnuc_graph_update", "pnuc_graph_launch", "pnuc_graph_destroy"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -209,6 +219,35 @@ class Context:
         self._check(self.lib.pnuc_measure_peaks(self.handle, C.byref(p)))
         return dict(fp32_fma=p.fp32_fma, fp64_fma=p.fp64_fma, mufu=p.mufu, int32_mad=p.int32_mad)
 
+    def _structs(self, energies, target_ids, seed, first_event_id, out):
+        b = pnuc_batch(_ptr(energies), _ptr(target_ids), int(energies.shape[0]), seed, first_event_id)
+        o = pnuc_output(_ptr(out.secondaries), out.secondaries.shape[0], _ptr(out.count), _ptr(out.residuals),
+                        _ptr(out.counters))
+        return b, o
+
+    def autotune(self, energies, target_ids, seed: int, precision: str = "fp32", reps: int = 2,
+                 out: "Result | None" = None, stream=None) -> tuple[dict, float]:
+        """pnuc_autotune on device tensors; returns (best tuning, its mean launch time in ms)."""
+        torch = self._torch
+        out = out or self.alloc(int(energies.shape[0]))
+        b, o = self._structs(energies, target_ids, seed, 0, out)
+        t, ms = pnuc_tuning(), C.c_double()
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        self._check(self.lib.pnuc_autotune(self.handle, PRECISION[precision], C.byref(b), C.byref(o), reps,
+                                           C.byref(t), C.byref(ms), C.c_void_p(s)))
+        return {name: getattr(t, name) for name, _ in pnuc_tuning._fields_}, ms.value
+
+    def save_tuning(self, path: str):
+        self._check(self.lib.pnuc_save_tuning(self.handle, os.fsencode(path)))
+
+    def load_tuning(self, path: str):
+        self._check(self.lib.pnuc_load_tuning(self.handle, os.fsencode(path)))
+
+    def graph(self, energies, target_ids, seed: int, out: "Result", first_event_id: int = 0,
+              precision: str = "fp32", method: str = "persistent") -> "Graph":
+        """pnuc_graph_create: a CUDA-graph plan of one launch for fixed buffers."""
+        return Graph(self, energies, target_ids, seed, out, first_event_id, precision, method)
+
     def alloc(self, n: int, capacity: int | None = None, counters: bool = False) -> Result:
         torch = self._torch
         dev = torch.device("cuda", self.device)
@@ -260,6 +299,41 @@ class Context:
                                                 sec.ctypes.data, sec.shape[0], C.byref(cnt), res.ctypes.data,
                                                 C.c_void_p(s)))
         return sec[: cnt.value], res[:n]
+
+
+class Graph:
+    """A CUDA-graph launch plan (pnuc_graph_*); keeps its buffers alive."""
+
+    def __init__(self, ctx: Context, energies, target_ids, seed, out, first_event_id, precision, method):
+        self.ctx, self.handle = ctx, C.c_void_p()
+        self._keep = (energies, target_ids, out)
+        b, o = ctx._structs(energies, target_ids, seed, first_event_id, out)
+        ctx._check(ctx.lib.pnuc_graph_create(ctx.handle, PRECISION[precision], METHOD[method], C.byref(b), C.byref(o),
+                                             C.byref(self.handle)))
+        self.out = out
+
+    def update(self, energies, target_ids, seed, out, first_event_id=0):
+        b, o = self.ctx._structs(energies, target_ids, seed, first_event_id, out)
+        self.ctx._check(self.ctx.lib.pnuc_graph_update(self.handle, C.byref(b), C.byref(o)))
+        self._keep = (energies, target_ids, out)
+        self.out = out
+
+    def launch(self, stream=None):
+        torch = self.ctx._torch
+        s = (stream or torch.cuda.current_stream(self.ctx.device)).cuda_stream
+        self.ctx._check(self.ctx.lib.pnuc_graph_launch(self.handle, C.c_void_p(s)))
+        return self.out
+
+    def close(self):
+        if self.handle:
+            self.ctx.lib.pnuc_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sort_secondaries(sec: np.ndarray) -> np.ndarray:

@@ -1,0 +1,104 @@
+"""Batched method: tuning never changes results; CUDA-graph plans replay the launch exactly;
+the autotuner and its JSON cache (through the C ABI)."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_1309_7963_gb300 import inputs, pnuc
+
+pytestmark = pytest.mark.gpu
+
+
+def device_inputs(ctx, w):
+    import torch
+    tids = np.array([ctx.create_target(*za) for za in w.targets], np.int32)
+    return (torch.tensor(w.energies, dtype=torch.float64, device="cuda"),
+            torch.tensor(tids[w.tidx], dtype=torch.int32, device="cuda"))
+
+
+def results(r):
+    return r.residuals_np().copy(), pnuc.sort_secondaries(r.secondaries_np())
+
+
+def same(a, b):
+    return np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_tuning_variants_give_identical_results(ctx):
+    import torch
+    w = inputs.mixed(30_000, seed=21)
+    e, t = device_inputs(ctx, w)
+    saved = ctx.get_tuning("fp32")
+    try:
+        ref = results(ctx.simulate(e, t, seed=21, precision="fp32", method="plain"))
+        for tun in [dict(max_registers=128, block_size=256, kin_batch=1, evap_batch=1, refill_threshold=1, chunk=64),
+                    dict(max_registers=80, block_size=128, kin_batch=32, evap_batch=32, refill_threshold=16, chunk=1024),
+                    dict(max_registers=64, block_size=64, kin_batch=8, evap_batch=24, refill_threshold=4, chunk=256)]:
+            ctx.set_tuning("fp32", **tun)
+            got = results(ctx.simulate(e, t, seed=21, precision="fp32", method="persistent"))
+            torch.cuda.synchronize()
+            assert same(got, ref), tun
+    finally:
+        ctx.set_tuning("fp32", **saved)
+
+
+def test_invalid_tuning_rejected(ctx):
+    for bad in [dict(block_size=96), dict(kin_batch=0), dict(evap_batch=33), dict(max_registers=70),
+                dict(max_registers=64, block_size=256), dict(chunk=8), dict(refill_threshold=40)]:
+        with pytest.raises(pnuc.PnucError):
+            ctx.set_tuning("fp32", **bad)
+
+
+def test_graph_plan_replays_and_updates(ctx):
+    import torch
+    w = inputs.mixed(20_000, seed=4)
+    e, t = device_inputs(ctx, w)
+    out = ctx.alloc(w.n)
+    g = ctx.graph(e, t, seed=4, out=out)
+    for _ in range(2):
+        g.launch()
+        torch.cuda.synchronize()
+        got = results(out)
+        ref = results(ctx.simulate(e, t, seed=4, precision="fp32", method="persistent"))
+        assert same(got, ref)
+    # new seed and new buffers through an update
+    w2 = inputs.mixed(7_000, seed=5)
+    e2, t2 = device_inputs(ctx, w2)
+    out2 = ctx.alloc(w2.n)
+    g.update(e2, t2, seed=5, out=out2, first_event_id=1000)
+    g.launch()
+    torch.cuda.synchronize()
+    ref2 = results(ctx.simulate(e2, t2, seed=5, first_event_id=1000, precision="fp32", method="persistent"))
+    assert same(results(out2), ref2)
+    g.close()
+
+
+def test_autotune_and_cache_roundtrip(ctx, tmp_path):
+    import torch
+    w = inputs.oxygen_calcium(n_each=40_000)
+    e, t = device_inputs(ctx, w)
+    saved = ctx.get_tuning("fp32")
+    try:
+        best, ms = ctx.autotune(e, t, seed=0, precision="fp32", reps=1)
+        assert ms > 0 and best == {**ctx.get_tuning("fp32")}
+        ref = results(ctx.simulate(e, t, seed=0, precision="fp32", method="plain"))
+        got = results(ctx.simulate(e, t, seed=0, precision="fp32", method="persistent"))
+        torch.cuda.synchronize()
+        assert same(got, ref)
+        path = tmp_path / "tuning.json"
+        path.write_text(json.dumps({"Some Other GPU": {"fp32": {"block_size": 64}}}))
+        ctx.save_tuning(str(path))
+        data = json.loads(path.read_text())
+        assert "Some Other GPU" in data and len(data) == 2
+        ctx.set_tuning("fp32", kin_batch=3)
+        ctx.load_tuning(str(path))
+        assert ctx.get_tuning("fp32") == best
+        # a cache without this device's entry is refused and leaves the tuning alone
+        other = tmp_path / "other.json"
+        other.write_text(json.dumps({"Some Other GPU": {"fp32": {"block_size": 64}}}))
+        with pytest.raises(pnuc.PnucError):
+            ctx.load_tuning(str(other))
+        assert ctx.get_tuning("fp32") == best
+    finally:
+        ctx.set_tuning("fp32", **saved)
