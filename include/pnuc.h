@@ -193,6 +193,29 @@ pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_met
                                uint64_t sec_capacity, uint64_t *sec_count, pnuc_residual *residuals,
                                void *stream);
 
+/* pnuc_simulate_host without any device allocation (the paper has no counterpart: this
+ * serves embedding). For callers that cannot call cudaMalloc at simulation time: host
+ * applications whose device memory is owned by another allocator (a framework's caching
+ * allocator or a pre-reserved pool) or that must not grow their device footprint while
+ * running, which pnuc_simulate_host would do the first time it meets a larger batch.
+ *
+ * Same arguments, results and errors as pnuc_simulate_host, but the device copies of the
+ * inputs and outputs and the persistent kernel's queue head live in one static device
+ * array of PNUC_NOALLOC_SCRATCH_BYTES (8 MiB) that every GPU loading this library holds
+ * until the process exits. A batch whose layout does not fit (about 8 MiB / (76 + 32 k)
+ * events for room for k secondaries per event: 24,000 events at k = 8) is rejected with
+ * PNUC_ERR_CAPACITY before anything runs. The entry point calls no cudaMalloc, cudaFree or
+ * allocating library routine. Its first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture. Every call shares the array and it keeps the last call's contents; the
+ * call clears what must start at zero. Calls whose work overlaps on the GPU (several host
+ * threads, or several contexts of one device) race on the array: serialise them. */
+#define PNUC_NOALLOC_SCRATCH_BYTES (8u << 20)
+pnuc_status pnuc_simulate_host_noalloc(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method,
+                                       const double *energies, const int32_t *target_ids, uint64_t n, uint64_t seed,
+                                       uint64_t first_event_id, pnuc_secondary *secondaries, uint64_t sec_capacity,
+                                       uint64_t *sec_count, pnuc_residual *residuals, void *stream);
+
 /* Persistent-method tuning of the context (per precision). set checks the ranges above. */
 pnuc_status pnuc_get_tuning(const pnuc_ctx *ctx, pnuc_precision precision, pnuc_tuning *out);
 pnuc_status pnuc_set_tuning(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_tuning *t);

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "api_internal.h"
@@ -346,6 +347,90 @@ pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_met
     uint64_t ncopy = cnt < sec_capacity ? cnt : sec_capacity;
     if (ncopy > 0) {
         CU(ctx, cudaMemcpyAsync(secondaries, ctx->h_sec, sizeof(pnuc_secondary) * ncopy, cudaMemcpyDeviceToHost, s));
+        CU(ctx, cudaStreamSynchronize(s));
+    }
+    *sec_count = cnt;
+    if (cnt > sec_capacity)
+        return fail(ctx, PNUC_ERR_CAPACITY, "batch produced %llu secondaries, capacity %llu", cnt,
+                    (unsigned long long)sec_capacity);
+    return PNUC_OK;
+}
+
+// ---------------------------------------------------------------- no-allocation entry point
+// Device scratch of pnuc_simulate_host_noalloc: every GPU that loads this library holds
+// these 8 MiB until the process exits. In host code the symbol is only a stand-in; the
+// device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PNUC_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_ptr[64] = {nullptr};  // per device ordinal, set on first use
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+
+pnuc_status pnuc_simulate_host_noalloc(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method,
+                                       const double *energies, const int32_t *target_ids, uint64_t n, uint64_t seed,
+                                       uint64_t first_event_id, pnuc_secondary *secondaries, uint64_t sec_capacity,
+                                       uint64_t *sec_count, pnuc_residual *residuals, void *stream)
+{
+    if (!ctx || !sec_count) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    if (n > 0 && (!energies || !target_ids || !residuals)) return fail(ctx, PNUC_ERR_ARG, "null input/output");
+    if (sec_capacity > 0 && !secondaries) return fail(ctx, PNUC_ERR_ARG, "null secondaries with capacity > 0");
+    // scratch layout: [queue head | count], energies, target ids, residuals, secondaries
+    const size_t off_e = 256;
+    const size_t off_t = off_e + round256(sizeof(double) * n);
+    const size_t off_r = off_t + round256(sizeof(int32_t) * n);
+    const size_t off_s = off_r + round256(sizeof(pnuc_residual) * n);
+    const size_t need = off_s + round256(sizeof(pnuc_secondary) * sec_capacity);
+    if (n > PNUC_NOALLOC_SCRATCH_BYTES || sec_capacity > PNUC_NOALLOC_SCRATCH_BYTES || need > PNUC_NOALLOC_SCRATCH_BYTES)
+        return fail(ctx, PNUC_ERR_CAPACITY,
+                    "pnuc_simulate_host_noalloc: %llu events with room for %llu secondaries need %llu bytes of "
+                    "device scratch; its static scratch holds %llu bytes (use pnuc_simulate_host for larger batches)",
+                    (unsigned long long)n, (unsigned long long)sec_capacity, (unsigned long long)need,
+                    (unsigned long long)PNUC_NOALLOC_SCRATCH_BYTES);
+    const int dev = ctx->cfg.device;
+    if (dev < 0 || dev >= 64) return fail(ctx, PNUC_ERR_ARG, "device %d outside the scratch table", dev);
+    CU(ctx, cudaSetDevice(dev));
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess)
+                return fail(ctx, PNUC_ERR_CUDA, "cudaGetSymbolAddress of the no-allocation scratch failed: %s",
+                            cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = (unsigned char *)ptr;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *head = (unsigned long long *)base;
+    unsigned long long *count = (unsigned long long *)(base + 128);
+    double *d_e = (double *)(base + off_e);
+    int32_t *d_t = (int32_t *)(base + off_t);
+    pnuc_residual *d_r = (pnuc_residual *)(base + off_r);
+    pnuc_secondary *d_s = (pnuc_secondary *)(base + off_s);
+    // the scratch keeps the previous call's contents: the queue head and count restart at 0
+    // (launch_batch clears both on the stream before the kernel)
+    if (n > 0) {
+        CU(ctx, cudaMemcpyAsync(d_e, energies, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+        CU(ctx, cudaMemcpyAsync(d_t, target_ids, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    }
+    pnuc_batch b = {d_e, d_t, n, seed, first_event_id};
+    pnuc_output o = {sec_capacity ? d_s : nullptr, sec_capacity, count, d_r, nullptr};
+    pnuc_status st = check_batch(ctx, precision, method, &b, &o);
+    if (st != PNUC_OK) return st;
+    st = launch_batch(ctx, precision, method, &b, &o, s, ctx->tuning[precision], head);
+    if (st != PNUC_OK) return st;
+    unsigned long long cnt = 0;
+    CU(ctx, cudaMemcpyAsync(&cnt, count, sizeof cnt, cudaMemcpyDeviceToHost, s));
+    if (n > 0) CU(ctx, cudaMemcpyAsync(residuals, d_r, sizeof(pnuc_residual) * n, cudaMemcpyDeviceToHost, s));
+    CU(ctx, cudaStreamSynchronize(s));
+    uint64_t ncopy = cnt < sec_capacity ? cnt : sec_capacity;
+    if (ncopy > 0) {
+        CU(ctx, cudaMemcpyAsync(secondaries, d_s, sizeof(pnuc_secondary) * ncopy, cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaStreamSynchronize(s));
     }
     *sec_count = cnt;

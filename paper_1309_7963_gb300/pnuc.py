@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_target_table.argtypes = [vp, i32, C.POINTER(pnuc_target_info)]
     L.pnuc_simulate.argtypes = [vp, C.c_int, C.c_int, C.POINTER(pnuc_batch), C.POINTER(pnuc_output), vp]
     L.pnuc_simulate_host.argtypes = [vp, C.c_int, C.c_int, vp, vp, u64, u64, u64, vp, u64, C.POINTER(u64), vp, vp]
+    L.pnuc_simulate_host_noalloc.argtypes = [vp, C.c_int, C.c_int, vp, vp, u64, u64, u64, vp, u64, C.POINTER(u64),
+                                             vp, vp]
     L.pnuc_get_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
     L.pnuc_set_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
     L.pnuc_measure_peaks.argtypes = [vp, C.POINTER(pnuc_peaks)]
@@ -111,7 +113,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_graph_launch.argtypes = [vp, vp]
     L.pnuc_graph_destroy.argtypes = [vp]
     for name in ("pnuc_create", "pnuc_destroy", "pnuc_last_error", "pnuc_create_target", "pnuc_target_table",
-                 "pnuc_simulate", "pnuc_simulate_host", "pnuc_get_tuning", "pnuc_set_tuning",
+                 "pnuc_simulate", "pnuc_simulate_host", "pnuc_simulate_host_noalloc", "pnuc_get_tuning",
+                 "pnuc_set_tuning",
                  "pnuc_measure_peaks", "pnuc_autotune", "pnuc_save_tuning", "pnuc_load_tuning",
                  "pnuc_graph_create", "pnuc_graph_update", "pnuc_graph_launch", "pnuc_graph_destroy"):
         getattr(L, name).restype = C.c_int
