@@ -57,13 +57,14 @@ def fp64_ops_per_event(counters: dict, n_events: int) -> float:
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-each", type=int, default=N_EACH)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -125,6 +126,39 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def serving_bench(ctx, seconds: float = 1.5) -> dict:
+    """The serving loop under the synthetic transport driver: capacity from a saturating
+    burst, then Poisson arrivals at 50% and 90% of it; p50/p99 from submit to results."""
+    import time as _t
+
+    from paper_1309_7963_gb300 import driver, inputs, pnuc
+    tids = np.array([ctx.create_target(*za) for za in inputs.SERVING_TARGETS], np.int32)
+    srv = pnuc.Server(ctx, precision="fp32", streams=4, arena_bytes=2 << 30)
+    try:
+        burst = inputs.serving_requests(64, rate_hz=1e9, seed=101)
+        rep = driver.run(srv, burst, tids, seed=7)
+        capacity = rep["events_per_s"]
+        mean_events = float(np.mean([len(r["energies"]) for r in burst]))
+        runs = []
+        for load in (0.5, 0.9):
+            rate = load * capacity / mean_events
+            n_req = max(40, int(rate * seconds))
+            reqs = inputs.serving_requests(n_req, rate_hz=rate, seed=200 + int(100 * load))
+            srv.reset_stats()
+            r = driver.run(srv, reqs, tids, seed=7)
+            st = srv.stats()
+            runs.append({"load": load, "offered_events_per_s": rate * mean_events, "requests": r["requests"],
+                         "events_per_s": r["events_per_s"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
+                         "max_ms": r["max_ms"], "server_p50_ms": st["latency_p50_ms"],
+                         "server_p99_ms": st["latency_p99_ms"], "queue_p99_ms": st["queue_p99_ms"],
+                         "reruns": st["reruns"]})
+        return {"capacity_events_per_s": capacity, "mean_request_events": mean_events,
+                "config": "Poisson arrivals, 1e3-1e5 events log-uniform, 20-250 MeV, 12C/16O/40Ca/48Ti/56Fe, "
+                          "4 streams, 2 GiB arenas, FP32", "runs": runs}
+    finally:
+        srv.close()
 
 
 def cpu_baseline(n_each: int, threads: int | None = None) -> dict:
@@ -265,6 +299,7 @@ def main():
                 "fp64_ops_per_event": ops_ev, "peak_source": "pnuc_measure_peaks (FP64 FMA lanes/s, this run)",
                 "peaks_lane_ops_per_s": peaks,
                 "work_per_event": {k: v / n for k, v in counters.items()}}
+    serving = None if (args.no_serving or world > 1) else serving_bench(ctx)
     if rank != 0:
         return
     cb = None if args.no_cpu else cpu_baseline(500_000)
@@ -279,6 +314,9 @@ def main():
         "launch_ms": launch_ms, "secondaries_per_step": n_sec,
         "flags_nonzero_fraction": float(np.mean(res["flags"] != 0)),
         "plain": plain, "batched_vs_plain": (value / plain["value"]) if plain else None,
+        "p50_ms": serving["runs"][-1]["p50_ms"] if serving else None,
+        "p99_ms": serving["runs"][-1]["p99_ms"] if serving else None,
+        "serving": serving,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cb, "clocks": clk, "gpu_launches": args.steps,
     }
     print(json.dumps(line))

@@ -135,8 +135,6 @@ typedef struct {
     int32_t chunk;            /* events a warp takes from the queue per atomic (32 .. 2^20) */
     int32_t kin_batch;        /* accepted collisions a warp gathers before their FP64 kinematics (1..32) */
     int32_t evap_batch;       /* lanes in evaporation a warp gathers before an evaporation step (1..32) */
-    int32_t max_registers;    /* FP32 persistent kernel register cap: 128, 80 or 64 (80 and 64 need
-                                 block_size <= 128); FP64 and counting launches use 128 */
 } pnuc_tuning;
 
 typedef struct pnuc_ctx pnuc_ctx;
@@ -221,7 +219,7 @@ pnuc_status pnuc_get_tuning(const pnuc_ctx *ctx, pnuc_precision precision, pnuc_
 pnuc_status pnuc_set_tuning(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_tuning *t);
 
 /* Autotuner of the persistent method: from the context's current tuning for `precision`,
- * a coordinate search over max_registers, block_size, kin_batch, evap_batch,
+ * a coordinate search over block_size, kin_batch, evap_batch,
  * refill_threshold and chunk (two passes; each candidate timed with CUDA events over `reps`
  * launches after one warm-up, on the given batch and output buffers, whose contents it
  * overwrites). The fastest tuning is kept in the context and written to *best (and its
@@ -255,6 +253,58 @@ pnuc_status pnuc_graph_create(pnuc_ctx *ctx, pnuc_precision precision, pnuc_meth
 pnuc_status pnuc_graph_update(pnuc_graph *graph, const pnuc_batch *batch, const pnuc_output *out);
 pnuc_status pnuc_graph_launch(pnuc_graph *graph, void *stream);
 pnuc_status pnuc_graph_destroy(pnuc_graph *graph);
+
+/* Serving loop (not in the paper: it motivates the code as a component of a GPU proton
+ * transport Monte Carlo, §1 and §4.2). A transport driver submits interaction requests as
+ * they arise; a scheduler thread admits queued requests in order whenever one of `streams`
+ * CUDA streams is free and both the device output arena and a pinned host arena of
+ * arena_bytes have room for the request's inputs, residuals and sec_per_event secondaries
+ * per event (memory-based admission). Each admitted request is one persistent launch on its
+ * own stream, so requests that arrive while others run are admitted as streams and memory
+ * free up and their work overlaps on the GPU (continuous batching). A request that produces
+ * more secondaries than reserved is run again with room for exactly its count; as results
+ * depend only on (seed, event id), every request's results equal those of a lone
+ * pnuc_simulate call. Latency is measured from submit to results ready on the host. */
+typedef struct {
+    int32_t precision;           /* pnuc_precision */
+    int32_t streams;             /* requests in flight at once, 1..16 (default 4) */
+    uint64_t arena_bytes;        /* device arena and pinned host arena, each (default 1 GiB, >= 1 MiB) */
+    uint32_t sec_per_event;      /* secondaries reserved per event at admission, 1..256 (default 12) */
+    uint32_t max_pending;        /* queued requests before submit refuses (default 4096) */
+    uint64_t max_request_events; /* largest request accepted (default 2^24) */
+} pnuc_server_config;
+
+typedef struct {
+    uint64_t completed, failed, reruns, events, pending;
+    double latency_p50_ms, latency_p99_ms, latency_max_ms; /* submit -> results on the host */
+    double queue_p50_ms, queue_p99_ms;                     /* submit -> admission */
+    double elapsed_s, events_per_s;                        /* since creation or the last reset */
+    uint64_t arena_peak_bytes;
+} pnuc_server_stats;
+
+typedef struct pnuc_server pnuc_server;
+void pnuc_server_default_config(pnuc_server_config *cfg);
+/* Allocates the arenas (device and pinned host), the streams and the scheduler thread. */
+pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg, pnuc_server **server);
+/* Queues a request of n events (host inputs, copied before returning; target ids from
+ * pnuc_create_target) and returns its ticket. PNUC_ERR_ARG if n is 0, above
+ * max_request_events or can never fit the arena; PNUC_ERR_CAPACITY if max_pending requests
+ * are queued (submit again later). Thread-safe. */
+pnuc_status pnuc_server_submit(pnuc_server *server, const double *energies, const int32_t *target_ids, uint64_t n,
+                               uint64_t seed, uint64_t first_event_id, uint64_t *ticket);
+/* Waits up to timeout_ms (negative: no limit) for the request; PNUC_ERR_TIMEOUT if it is not
+ * done by then, else the request's status, and *n_secondaries its number of secondaries. */
+pnuc_status pnuc_server_wait(pnuc_server *server, uint64_t ticket, int32_t timeout_ms, uint64_t *n_secondaries);
+/* Copies a finished request's residuals (n records) and secondaries (host buffers; capacity
+ * at least its count, else PNUC_ERR_CAPACITY and nothing is released) and releases it.
+ * PNUC_ERR_STATE if it is not finished; a failed request returns its error and is released.
+ * Finished requests hold pinned host memory until fetched. */
+pnuc_status pnuc_server_fetch(pnuc_server *server, uint64_t ticket, pnuc_secondary *secondaries, uint64_t capacity,
+                              pnuc_residual *residuals);
+pnuc_status pnuc_server_get_stats(pnuc_server *server, pnuc_server_stats *out);
+pnuc_status pnuc_server_reset_stats(pnuc_server *server);
+/* Drops queued requests, waits for those in flight, frees everything. Safe on NULL. */
+pnuc_status pnuc_server_destroy(pnuc_server *server);
 
 /* Measured throughput of the pipes the event kernels use, in lane operations per second
  * (one fused multiply-add = one operation): FP32 FMA, FP64 FMA, special-function unit

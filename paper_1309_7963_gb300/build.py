@@ -21,11 +21,11 @@ UNITS = {
     "api.cu": [],
     "autotune.cu": [],
     "graph.cu": [],
+    "server.cu": [],
     "tables.cu": [],
     "microbench.cu": [],
     "kernel_fp64.cu": ["--fmad=false"],
     "kernel_fp32.cu": ["--use_fast_math"],
-    "kernel_fp32_capped.cu": ["--use_fast_math"],
 }
 
 

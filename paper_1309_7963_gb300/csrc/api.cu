@@ -28,11 +28,9 @@ pnuc_status fail(pnuc_ctx *ctx, pnuc_status st, const char *fmt, ...)
 namespace {
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-int occupancy(pnuc_precision prec, int block, bool count, int max_registers)
+int occupancy(pnuc_precision prec, int block, bool count)
 {
-    if (prec == PNUC_FP64) return occupancy_persistent_fp64(block);
-    if (!count && max_registers < 128) return occupancy_persistent_fp32_capped(block, max_registers);
-    return occupancy_persistent_fp32(block, count);
+    return prec == PNUC_FP64 ? occupancy_persistent_fp64(block) : occupancy_persistent_fp32(block, count);
 }
 }  // namespace
 
@@ -48,10 +46,6 @@ pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t)
         return fail(ctx, PNUC_ERR_ARG, "chunk %d not in [32, 2^20]", t->chunk);
     if (t->kin_batch < 1 || t->kin_batch > 32 || t->evap_batch < 1 || t->evap_batch > 32)
         return fail(ctx, PNUC_ERR_ARG, "kin_batch %d / evap_batch %d not in [1,32]", t->kin_batch, t->evap_batch);
-    if (t->max_registers != 128 && t->max_registers != 80 && t->max_registers != 64)
-        return fail(ctx, PNUC_ERR_ARG, "max_registers %d not in {128, 80, 64}", t->max_registers);
-    if (t->max_registers < 128 && t->block_size > 128)
-        return fail(ctx, PNUC_ERR_ARG, "max_registers %d needs block_size <= 128", t->max_registers);
     return PNUC_OK;
 }
 
@@ -107,17 +101,15 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
         e = precision == PNUC_FP64 ? launch_plain_fp64(p, t.block_size, s)
                                    : launch_plain_fp32(p, t.block_size, count, s);
     } else {
-        const bool capped = precision == PNUC_FP32 && !count && t.max_registers < 128;
-        int occ = occupancy(precision, t.block_size, count, capped ? t.max_registers : 128);
+        int occ = occupancy(precision, t.block_size, count);
         int bps = std::min(t.blocks_per_sm, std::max(occ, 1));
         unsigned long long grid = (unsigned long long)bps * ctx->sm_count;
         unsigned long long need = (batch->n + t.block_size - 1) / t.block_size;
         if (grid > need) grid = need;
         p.queue_head = queue_head ? queue_head : ctx->queue + (size_t)(ctx->queue_next++ % kQueueSlots) * kQueueStride;
         CU(ctx, cudaMemsetAsync(p.queue_head, 0, sizeof(unsigned long long), s));
-        if (precision == PNUC_FP64) e = launch_persistent_fp64(p, (int)grid, t.block_size, s);
-        else if (capped) e = launch_persistent_fp32_capped(p, (int)grid, t.block_size, t.max_registers, s);
-        else e = launch_persistent_fp32(p, (int)grid, t.block_size, count, s);
+        e = precision == PNUC_FP64 ? launch_persistent_fp64(p, (int)grid, t.block_size, s)
+                                   : launch_persistent_fp32(p, (int)grid, t.block_size, count, s);
     }
     if (e != cudaSuccess) return fail(ctx, PNUC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     return PNUC_OK;
@@ -199,8 +191,7 @@ pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
             t.kin_batch = 16;
             t.evap_batch = 16;
             t.refill_threshold = 4;
-            t.max_registers = 128;
-            int occ = occupancy((pnuc_precision)p, t.block_size, false, 128);
+            int occ = occupancy((pnuc_precision)p, t.block_size, false);
             t.blocks_per_sm = occ > 0 ? occ : 1;
         }
     } while (0);

@@ -1,6 +1,6 @@
 // Autotuner of the persistent method and its on-disk cache (host code).
 //
-// The persistent kernel's tuning (block size, register cap, refill threshold, queue chunk,
+// The persistent kernel's tuning (block size, refill threshold, queue chunk,
 // and the collision / evaporation batch sizes) changes only the order in which lanes do
 // their work, never an event's result, so it can be chosen by timing alone. The search is
 // a coordinate descent from the context's current tuning: each parameter in turn takes each
@@ -20,23 +20,21 @@ namespace {
 int32_t *field(pnuc_tuning &t, int k)
 {
     switch (k) {
-    case 0: return &t.max_registers;
-    case 1: return &t.block_size;
-    case 2: return &t.kin_batch;
-    case 3: return &t.evap_batch;
-    case 4: return &t.refill_threshold;
+    case 0: return &t.block_size;
+    case 1: return &t.kin_batch;
+    case 2: return &t.evap_batch;
+    case 3: return &t.refill_threshold;
     default: return &t.chunk;
     }
 }
 
-std::vector<int32_t> candidates(int k, pnuc_precision prec)
+std::vector<int32_t> candidates(int k)
 {
     switch (k) {
-    case 0: return prec == PNUC_FP32 ? std::vector<int32_t>{128, 80, 64} : std::vector<int32_t>{128};
-    case 1: return {64, 128, 256};
+    case 0: return {64, 128, 256};
+    case 1: return {1, 8, 16, 24, 32};
     case 2: return {1, 8, 16, 24, 32};
-    case 3: return {1, 8, 16, 24, 32};
-    case 4: return {1, 2, 4, 8, 16};
+    case 3: return {1, 2, 4, 8, 16};
     default: return {64, 256, 1024};
     }
 }
@@ -94,8 +92,7 @@ struct Json {
     }
 };
 
-const char *kKeys[7] = {"block_size", "blocks_per_sm", "refill_threshold", "chunk", "kin_batch", "evap_batch",
-                        "max_registers"};
+const char *kKeys[6] = {"block_size", "blocks_per_sm", "refill_threshold", "chunk", "kin_batch", "evap_batch"};
 
 int32_t *by_name(pnuc_tuning &t, const std::string &k)
 {
@@ -105,7 +102,6 @@ int32_t *by_name(pnuc_tuning &t, const std::string &k)
     if (k == kKeys[3]) return &t.chunk;
     if (k == kKeys[4]) return &t.kin_batch;
     if (k == kKeys[5]) return &t.evap_batch;
-    if (k == kKeys[6]) return &t.max_registers;
     return nullptr;
 }
 
@@ -181,8 +177,8 @@ pnuc_status pnuc_autotune(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_ba
     cur.blocks_per_sm = 32;  // the launch clamps to the kernel's occupancy
     double cur_ms = time_tuning(ctx, precision, batch, out, cur, reps, s, e0, e1);
     for (int pass = 0; pass < 2 && cur_ms > 0; ++pass) {
-        for (int k = 0; k < 6; ++k) {
-            for (int32_t v : candidates(k, precision)) {
+        for (int k = 0; k < 5; ++k) {
+            for (int32_t v : candidates(k)) {
                 pnuc_tuning t = cur;
                 *field(t, k) = v;
                 if (*field(cur, k) == v || check_tuning(nullptr, &t) != PNUC_OK) continue;
@@ -238,7 +234,7 @@ pnuc_status pnuc_save_tuning(pnuc_ctx *ctx, const char *path)
             if (!entries[i].has[p]) continue;
             pnuc_tuning &t = entries[i].t[p];
             fprintf(f, "%s\n    \"%s\": {", first ? "" : ",", p ? "fp64" : "fp32");
-            for (int k = 0; k < 7; ++k) fprintf(f, "%s\"%s\": %d", k ? ", " : "", kKeys[k], *by_name(t, kKeys[k]));
+            for (int k = 0; k < 6; ++k) fprintf(f, "%s\"%s\": %d", k ? ", " : "", kKeys[k], *by_name(t, kKeys[k]));
             fprintf(f, "}");
             first = false;
         }

@@ -68,9 +68,6 @@ cudaError_t launch_plain_fp64(const SimParams &p, int block, cudaStream_t s);
 cudaError_t launch_persistent_fp64(const SimParams &p, int grid, int block, cudaStream_t s);
 cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, cudaStream_t s);
 cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s);
-// FP32 persistent kernel capped at 80 or 64 registers per thread (blocks <= 128 threads).
-cudaError_t launch_persistent_fp32_capped(const SimParams &p, int grid, int block, int max_registers, cudaStream_t s);
-int occupancy_persistent_fp32_capped(int block, int max_registers);
 // Resident blocks per SM of the persistent kernels at a block size.
 int occupancy_persistent_fp64(int block);
 int occupancy_persistent_fp32(int block, bool count);

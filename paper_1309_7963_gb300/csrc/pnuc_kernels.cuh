@@ -191,14 +191,6 @@ __global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
     persistent_body<R, kCount>(P);
 }
 
-// Register-capped variants (blocks of at most 128 threads; kMinBlocks resident blocks per
-// SM): 128 / kMinBlocks registers per thread trade spills for resident warps.
-template <typename R, bool kCount, int kMinBlocks>
-__global__ void __launch_bounds__(128, kMinBlocks) persistent_kernel_capped(const SimParams P)
-{
-    persistent_body<R, kCount>(P);
-}
-
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes)
 {
@@ -227,27 +219,6 @@ cudaError_t launch_persistent(const SimParams &p, int grid, int block, cudaStrea
     if (e != cudaSuccess) return e;
     persistent_kernel<R, kCount><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
-}
-
-template <typename R, bool kCount, int kMinBlocks>
-cudaError_t launch_persistent_capped(const SimParams &p, int grid, int block, cudaStream_t s)
-{
-    if (p.n == 0) return cudaSuccess;
-    size_t smem = smem_bytes<R>(p.n_targets, block);
-    cudaError_t e = allow_smem(persistent_kernel_capped<R, kCount, kMinBlocks>, smem);
-    if (e != cudaSuccess) return e;
-    persistent_kernel_capped<R, kCount, kMinBlocks><<<grid, block, smem, s>>>(p);
-    return cudaGetLastError();
-}
-
-template <typename R, bool kCount, int kMinBlocks>
-int occupancy_persistent_capped(int block)
-{
-    int nb = 0;
-    allow_smem(persistent_kernel_capped<R, kCount, kMinBlocks>, smem_bytes<R>(kMaxTargets, block));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel_capped<R, kCount, kMinBlocks>, block,
-                                                  smem_bytes<R>(kMaxTargets, block));
-    return nb;
 }
 
 template <typename R, bool kCount>

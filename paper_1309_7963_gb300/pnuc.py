@@ -52,8 +52,7 @@ class pnuc_output(C.Structure):
 
 class pnuc_tuning(C.Structure):
     _fields_ = [("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_threshold", C.c_int32),
-                ("chunk", C.c_int32), ("kin_batch", C.c_int32), ("evap_batch", C.c_int32),
-                ("max_registers", C.c_int32)]
+                ("chunk", C.c_int32), ("kin_batch", C.c_int32), ("evap_batch", C.c_int32)]
 
 
 class pnuc_target_info(C.Structure):
@@ -65,6 +64,18 @@ class pnuc_target_info(C.Structure):
 
 class pnuc_peaks(C.Structure):
     _fields_ = [("fp32_fma", C.c_double), ("fp64_fma", C.c_double), ("mufu", C.c_double), ("int32_mad", C.c_double)]
+
+
+class pnuc_server_config(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("streams", C.c_int32), ("arena_bytes", C.c_uint64),
+                ("sec_per_event", C.c_uint32), ("max_pending", C.c_uint32), ("max_request_events", C.c_uint64)]
+
+
+class pnuc_server_stats(C.Structure):
+    _fields_ = [("completed", C.c_uint64), ("failed", C.c_uint64), ("reruns", C.c_uint64), ("events", C.c_uint64),
+                ("pending", C.c_uint64), ("latency_p50_ms", C.c_double), ("latency_p99_ms", C.c_double),
+                ("latency_max_ms", C.c_double), ("queue_p50_ms", C.c_double), ("queue_p99_ms", C.c_double),
+                ("elapsed_s", C.c_double), ("events_per_s", C.c_double), ("arena_peak_bytes", C.c_uint64)]
 
 
 class PnucError(RuntimeError):
@@ -112,11 +123,22 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_graph_update.argtypes = [vp, C.POINTER(pnuc_batch), C.POINTER(pnuc_output)]
     L.pnuc_graph_launch.argtypes = [vp, vp]
     L.pnuc_graph_destroy.argtypes = [vp]
+    L.pnuc_server_default_config.argtypes = [C.POINTER(pnuc_server_config)]
+    L.pnuc_server_default_config.restype = None
+    L.pnuc_server_create.argtypes = [vp, C.POINTER(pnuc_server_config), C.POINTER(vp)]
+    L.pnuc_server_submit.argtypes = [vp, vp, vp, u64, u64, u64, C.POINTER(u64)]
+    L.pnuc_server_wait.argtypes = [vp, u64, C.c_int32, C.POINTER(u64)]
+    L.pnuc_server_fetch.argtypes = [vp, u64, vp, u64, vp]
+    L.pnuc_server_get_stats.argtypes = [vp, C.POINTER(pnuc_server_stats)]
+    L.pnuc_server_reset_stats.argtypes = [vp]
+    L.pnuc_server_destroy.argtypes = [vp]
     for name in ("pnuc_create", "pnuc_destroy", "pnuc_last_error", "pnuc_create_target", "pnuc_target_table",
                  "pnuc_simulate", "pnuc_simulate_host", "pnuc_simulate_host_noalloc", "pnuc_get_tuning",
                  "pnuc_set_tuning",
                  "pnuc_measure_peaks", "pnuc_autotune", "pnuc_save_tuning", "pnuc_load_tuning",
-                 "pnuc_graph_create", "pnuc_graph_update", "pnuc_graph_launch", "pnuc_graph_destroy"):
+                 "pnuc_graph_create", "pnuc_graph_update", "pnuc_graph_launch", "pnuc_graph_destroy",
+                 "pnuc_server_create", "pnuc_server_submit", "pnuc_server_wait", "pnuc_server_fetch",
+                 "pnuc_server_get_stats", "pnuc_server_reset_stats", "pnuc_server_destroy"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -330,6 +352,66 @@ class Graph:
     def close(self):
         if self.handle:
             self.ctx.lib.pnuc_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop (pnuc_server_*): continuous batching with memory-based admission."""
+
+    TIMEOUT = 5
+
+    def __init__(self, ctx: Context, precision: str = "fp32", **cfg):
+        self.ctx, self.lib, self.handle = ctx, ctx.lib, C.c_void_p()
+        c = pnuc_server_config()
+        self.lib.pnuc_server_default_config(C.byref(c))
+        c.precision = PRECISION[precision]
+        for k, v in cfg.items():
+            setattr(c, k, int(v))
+        ctx._check(self.lib.pnuc_server_create(ctx.handle, C.byref(c), C.byref(self.handle)))
+        self.n_events: dict[int, int] = {}
+
+    def submit(self, energies, target_ids, seed: int, first_event_id: int = 0) -> int:
+        """Queues a request; returns its ticket. Raises PnucError (status 3) when the queue is full."""
+        e = np.ascontiguousarray(energies, np.float64)
+        t = np.ascontiguousarray(target_ids, np.int32)
+        tk = C.c_uint64()
+        self.ctx._check(self.lib.pnuc_server_submit(self.handle, e.ctypes.data, t.ctypes.data, len(e), seed,
+                                                    first_event_id, C.byref(tk)))
+        self.n_events[tk.value] = len(e)
+        return tk.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Number of secondaries of the finished request, or None on timeout."""
+        n = C.c_uint64()
+        st = self.lib.pnuc_server_wait(self.handle, ticket, timeout_ms, C.byref(n))
+        if st == self.TIMEOUT:
+            return None
+        self.ctx._check(st)
+        return n.value
+
+    def fetch(self, ticket: int, n_secondaries: int):
+        sec = np.empty(max(n_secondaries, 1), SECONDARY_DTYPE)
+        res = np.empty(self.n_events.pop(ticket), RESIDUAL_DTYPE)
+        self.ctx._check(self.lib.pnuc_server_fetch(self.handle, ticket, sec.ctypes.data, len(sec), res.ctypes.data))
+        return sec[:n_secondaries], res
+
+    def stats(self) -> dict:
+        st = pnuc_server_stats()
+        self.ctx._check(self.lib.pnuc_server_get_stats(self.handle, C.byref(st)))
+        return {name: getattr(st, name) for name, _ in pnuc_server_stats._fields_}
+
+    def reset_stats(self):
+        self.ctx._check(self.lib.pnuc_server_reset_stats(self.handle))
+
+    def close(self):
+        if self.handle:
+            self.lib.pnuc_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

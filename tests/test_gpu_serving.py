@@ -1,0 +1,106 @@
+"""Serving loop (pnuc_server): continuous batching with memory-based admission. Every
+request's results equal those of the same events run alone; overflowing requests are re-run;
+admission respects the arena; queue limits, errors and timeouts are reported."""
+import numpy as np
+import pytest
+
+from paper_1309_7963_gb300 import driver, inputs, pnuc
+
+pytestmark = pytest.mark.gpu
+
+
+def serving_tids(ctx):
+    return np.array([ctx.create_target(*za) for za in inputs.SERVING_TARGETS], np.int32)
+
+
+def alone(ctx, req, tids, seed, precision="fp32"):
+    sec, res = ctx.simulate_host(req["energies"], tids[req["tidx"]], seed=seed, first_event_id=req["first_event_id"],
+                                 precision=precision, method="persistent")
+    return pnuc.sort_secondaries(sec), res
+
+
+def test_each_result_equals_its_events_run_alone(ctx):
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(24, rate_hz=1e6, seed=7, min_batch=500, max_batch=20_000)
+    srv = pnuc.Server(ctx, precision="fp32", streams=4, arena_bytes=256 << 20)
+    try:
+        tickets = [srv.submit(r["energies"], tids[r["tidx"]], 11, r["first_event_id"]) for r in reqs]
+        for tk, r in zip(tickets, reqs):
+            n = srv.wait(tk)
+            sec, res = srv.fetch(tk, n)
+            ref_sec, ref_res = alone(ctx, r, tids, 11)
+            assert np.array_equal(res, ref_res)
+            assert np.array_equal(pnuc.sort_secondaries(sec), ref_sec)
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["failed"] == 0
+        assert st["latency_p99_ms"] >= st["latency_p50_ms"] > 0
+    finally:
+        srv.close()
+
+
+def test_overflowing_requests_are_rerun_identically(ctx):
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(6, rate_hz=1e6, seed=8, min_batch=1000, max_batch=5000)
+    srv = pnuc.Server(ctx, precision="fp64", streams=2, arena_bytes=64 << 20, sec_per_event=1)
+    try:
+        tickets = [srv.submit(r["energies"], tids[r["tidx"]], 3, r["first_event_id"]) for r in reqs]
+        for tk, r in zip(tickets, reqs):
+            sec, res = srv.fetch(tk, srv.wait(tk))
+            ref_sec, ref_res = alone(ctx, r, tids, 3, precision="fp64")
+            assert np.array_equal(res, ref_res) and np.array_equal(pnuc.sort_secondaries(sec), ref_sec)
+        assert srv.stats()["reruns"] >= len(reqs)
+    finally:
+        srv.close()
+
+
+def test_admission_respects_the_arena(ctx):
+    tids = serving_tids(ctx)
+    arena = 8 << 20
+    srv = pnuc.Server(ctx, precision="fp32", streams=8, arena_bytes=arena, sec_per_event=12)
+    try:
+        reqs = inputs.serving_requests(10, rate_hz=1e6, seed=9, min_batch=9000, max_batch=9000)
+        tickets = [srv.submit(r["energies"], tids[r["tidx"]], 5, r["first_event_id"]) for r in reqs]
+        for tk in tickets:
+            srv.fetch(tk, srv.wait(tk))
+        st = srv.stats()
+        # one 9000-event request reserves ~3.9 MB: at most two fit the 8 MiB arena at once
+        assert st["completed"] == 10 and 0 < st["arena_peak_bytes"] <= arena
+        assert st["arena_peak_bytes"] <= 2 * 4_000_000
+    finally:
+        srv.close()
+
+
+def test_submit_errors_queue_limit_and_timeout(ctx):
+    tids = serving_tids(ctx)
+    srv = pnuc.Server(ctx, precision="fp32", streams=1, arena_bytes=64 << 20, max_pending=2)
+    try:
+        with pytest.raises(pnuc.PnucError):
+            srv.submit(np.zeros(0), np.zeros(0, np.int32), 0)
+        with pytest.raises(pnuc.PnucError):  # can never fit the 64 MiB arena
+            srv.submit(np.full(500_000, 100.0), np.full(500_000, tids[0], np.int32), 0)
+        big = srv.submit(np.full(150_000, 200.0), np.full(150_000, tids[2], np.int32), 0)
+        assert srv.wait(big, 0) is None  # still running: the wait times out
+        q1 = srv.submit(np.full(1000, 100.0), np.full(1000, tids[1], np.int32), 0, 1 << 32)
+        q2 = srv.submit(np.full(1000, 100.0), np.full(1000, tids[1], np.int32), 0, 2 << 32)
+        with pytest.raises(pnuc.PnucError) as e:
+            srv.submit(np.full(1000, 100.0), np.full(1000, tids[1], np.int32), 0, 3 << 32)
+        assert e.value.status == 3
+        for tk in (big, q1, q2):
+            srv.fetch(tk, srv.wait(tk))
+    finally:
+        srv.close()
+
+
+def test_driver_reports_latency_and_throughput(ctx):
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(60, rate_hz=300.0, seed=10)
+    srv = pnuc.Server(ctx, precision="fp32", streams=4, arena_bytes=1 << 30)
+    seen = []
+    try:
+        rep = driver.run(srv, reqs, tids, seed=1, keep=lambda req, sec, res: seen.append(len(res)))
+        assert rep["requests"] == 60 and sum(seen) == rep["events"] == sum(len(r["energies"]) for r in reqs)
+        assert 0 < rep["p50_ms"] <= rep["p99_ms"]
+        st = srv.stats()
+        assert st["completed"] == 60 and st["latency_p50_ms"] > 0
+    finally:
+        srv.close()
