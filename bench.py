@@ -69,10 +69,8 @@ def parse():
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    from paper_1309_7963_gb300 import dist
+    return dist.env()
 
 
 class ClockSampler:
@@ -215,7 +213,8 @@ def main():
     w = inputs.oxygen_calcium(n_each=args.n_each, energy=ENERGY)
     tids = np.array([ctx.create_target(*za) for za in w.targets], np.int32)
     n = w.n
-    first = rank * n  # weak scaling: each rank its own event-id range
+    from paper_1309_7963_gb300 import dist as pdist
+    first = pdist.shard_first_event_id(rank, n)  # weak scaling: each rank its own event-id range
     e_dev = torch.tensor(w.energies, dtype=torch.float64, device="cuda")
     t_dev = torch.tensor(tids[w.tidx], dtype=torch.int32, device="cuda")
     cap = 8 * n
@@ -252,10 +251,7 @@ def main():
     clocks.start()
     total_ms, kern_ms = timed("persistent", args.steps, args.warmup)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = pdist.max_over_ranks(total_ms, device="cuda")
     n_sec = out.n_secondaries()
     res = out.residuals_np()
     value = world * n * args.steps / (total_ms * 1e-3)
