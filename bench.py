@@ -49,6 +49,20 @@ FP64_OPS_PER_UNIT = {
 FP64_OPS_PER_EVENT = 15  # excitation energy from the energy balance
 
 
+def traffic_per_event():
+    """DRAM bytes per event of the persistent FP32 kernel from its last ncu capture
+    (profiles/persistent_kernel_traffic.txt), or None if the kernel sources changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "persistent_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = dict(line.split(": ", 1) for line in open(path) if ": " in line and not line.startswith("#"))
+    h = hashlib.sha1()
+    for f in ("pnuc_device.cuh", "pnuc_kernels.cuh", "kernel_fp32.cu", "pnuc_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1309_7963_gb300", "csrc", f), "rb").read())
+    return float(kv["bytes_per_event"]) if h.hexdigest() == kv.get("kernel_sha1", "").strip() else None
+
+
 def fp64_ops_per_event(counters: dict, n_events: int) -> float:
     tot = sum(counters[k] * v for k, v in FP64_OPS_PER_UNIT.items()) + FP64_OPS_PER_EVENT * n_events
     return tot / n_events
@@ -291,7 +305,9 @@ def main():
     peaks = ctx.measure_peaks()
     achieved = ops_ev * n / (launch_ms * 1e-3)
     roofline = {"bound": "alu", "pipe": "fp64", "achieved": achieved / 1e9, "peak": peaks["fp64_fma"] / 1e9,
-                "unit": "FP64 Gop/s", "frac": achieved / peaks["fp64_fma"], "traffic": None,
+                "unit": "FP64 Gop/s", "frac": achieved / peaks["fp64_fma"],
+                "traffic": (traffic_per_event() * n) if traffic_per_event() else None,
+                "traffic_note": "DRAM bytes per launch, scaled by events from an 8e5-event ncu capture",
                 "fp64_ops_per_event": ops_ev, "peak_source": "pnuc_measure_peaks (FP64 FMA lanes/s, this run)",
                 "peaks_lane_ops_per_s": peaks,
                 "work_per_event": {k: v / n for k, v in counters.items()}}
