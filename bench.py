@@ -310,7 +310,9 @@ def main():
                 "traffic_note": "DRAM bytes per launch, scaled by events from an 8e5-event ncu capture",
                 "fp64_ops_per_event": ops_ev, "peak_source": "pnuc_measure_peaks (FP64 FMA lanes/s, this run)",
                 "peaks_lane_ops_per_s": peaks,
-                "work_per_event": {k: v / n for k, v in counters.items()}}
+                "work_per_event": {k: v / n for k, v in counters.items() if not k.startswith("cycles")}}
+    cyc = {k[7:]: counters[k] for k in counters if k.startswith("cycles_")}
+    phase_split = {k: v / max(1, sum(cyc.values())) for k, v in cyc.items()}
     serving = None if (args.no_serving or world > 1) else serving_bench(ctx)
     if rank != 0:
         return
@@ -326,6 +328,7 @@ def main():
         "launch_ms": launch_ms, "secondaries_per_step": n_sec,
         "flags_nonzero_fraction": float(np.mean(res["flags"] != 0)),
         "plain": plain, "batched_vs_plain": (value / plain["value"]) if plain else None,
+        "phase_split": phase_split,
         "p50_ms": serving["runs"][-1]["p50_ms"] if serving else None,
         "p99_ms": serving["runs"][-1]["p99_ms"] if serving else None,
         "serving": serving,

@@ -50,7 +50,8 @@ typedef enum {
 
 typedef enum {
     PNUC_PLAIN = 0,     /* one event per thread, one launch of n threads */
-    PNUC_PERSISTENT = 1 /* resident warps that refill finished lanes from a device queue */
+    PNUC_PERSISTENT = 1 /* two launches of resident warps that refill finished lanes from device
+                           queues: the cascades, then the evaporations they leave pending */
 } pnuc_method;
 
 /* Secondary particle record, 32 bytes, 16-byte aligned array. */
@@ -94,7 +95,11 @@ typedef struct {
 enum {
     PNUC_C_STEPS = 0, PNUC_C_CANDIDATES, PNUC_C_KINEMATICS, PNUC_C_PAULI_BLOCKED, PNUC_C_COLLISIONS,
     PNUC_C_CROSSINGS, PNUC_C_REFLECTIONS, PNUC_C_ESCAPES, PNUC_C_CAPTURES, PNUC_C_ATTEMPTS,
-    PNUC_C_EVAP_STEPS, PNUC_C_EVAP_TRIALS, PNUC_C_DRAWS, PNUC_N_COUNTERS
+    PNUC_C_EVAP_STEPS, PNUC_C_EVAP_TRIALS, PNUC_C_DRAWS,
+    /* persistent method only: SM clock cycles its warps spent in each phase of the loop
+     * (summed over warps), the counterpart of the paper's kernel time split (§4.2) */
+    PNUC_C_CYCLES_TRANSPORT, PNUC_C_CYCLES_COLLISION, PNUC_C_CYCLES_EVAPORATION, PNUC_C_CYCLES_REFILL,
+    PNUC_N_COUNTERS
 };
 
 typedef struct {
@@ -134,7 +139,6 @@ typedef struct {
     int32_t refill_threshold; /* a warp refills when at least this many lanes are idle (1..32) */
     int32_t chunk;            /* events a warp takes from the queue per atomic (32 .. 2^20) */
     int32_t kin_batch;        /* accepted collisions a warp gathers before their FP64 kinematics (1..32) */
-    int32_t evap_batch;       /* lanes in evaporation a warp gathers before an evaporation step (1..32) */
 } pnuc_tuning;
 
 typedef struct pnuc_ctx pnuc_ctx;
@@ -219,7 +223,7 @@ pnuc_status pnuc_get_tuning(const pnuc_ctx *ctx, pnuc_precision precision, pnuc_
 pnuc_status pnuc_set_tuning(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_tuning *t);
 
 /* Autotuner of the persistent method: from the context's current tuning for `precision`,
- * a coordinate search over block_size, kin_batch, evap_batch,
+ * a coordinate search over block_size, kin_batch,
  * refill_threshold and chunk (two passes; each candidate timed with CUDA events over `reps`
  * launches after one warm-up, on the given batch and output buffers, whose contents it
  * overwrites). The fastest tuning is kept in the context and written to *best (and its

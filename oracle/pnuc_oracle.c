@@ -779,12 +779,14 @@ static void run_event(const orc_target *t, double T0, uint32_t ev, orc_stream *s
         res->flags |= F_BAD_RESIDUAL;
         return;
     }
-    double Estar = Er - orc_semf_mass(Z, A);
+    double Mc = orc_semf_mass(Z, A);
+    double Estar = Er - Mc;
     res->Estar_c = res->Estar_f = Estar;
     if (!(Estar > 0.0)) {
         res->flags |= F_NO_EXCITATION;
         return;
     }
+    Er = Mc + Estar; /* the excited residual at rest: its total energy is M + E* */
 
     /* -------- evaporation (section 2.4) */
     int step;

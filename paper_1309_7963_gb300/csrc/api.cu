@@ -44,8 +44,8 @@ pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t)
         return fail(ctx, PNUC_ERR_ARG, "refill_threshold %d not in [1,32]", t->refill_threshold);
     if (t->chunk < 32 || t->chunk > (1 << 20))
         return fail(ctx, PNUC_ERR_ARG, "chunk %d not in [32, 2^20]", t->chunk);
-    if (t->kin_batch < 1 || t->kin_batch > 32 || t->evap_batch < 1 || t->evap_batch > 32)
-        return fail(ctx, PNUC_ERR_ARG, "kin_batch %d / evap_batch %d not in [1,32]", t->kin_batch, t->evap_batch);
+    if (t->kin_batch < 1 || t->kin_batch > 32)
+        return fail(ctx, PNUC_ERR_ARG, "kin_batch %d not in [1,32]", t->kin_batch);
     return PNUC_OK;
 }
 
@@ -93,8 +93,9 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
     p.refill_threshold = t.refill_threshold;
     p.chunk = t.chunk;
     p.kin_batch = t.kin_batch;
-    p.evap_batch = t.evap_batch;
     p.queue_head = nullptr;
+    p.evap_head = nullptr;
+    p.split_evap = 0;
     const bool count = out->counters != nullptr;
     cudaError_t e;
     if (method == PNUC_PLAIN) {
@@ -106,10 +107,16 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
         unsigned long long grid = (unsigned long long)bps * ctx->sm_count;
         unsigned long long need = (batch->n + t.block_size - 1) / t.block_size;
         if (grid > need) grid = need;
+        // queue slot: [0] the cascade kernel's queue head, [1] the evaporation kernel's
         p.queue_head = queue_head ? queue_head : ctx->queue + (size_t)(ctx->queue_next++ % kQueueSlots) * kQueueStride;
-        CU(ctx, cudaMemsetAsync(p.queue_head, 0, sizeof(unsigned long long), s));
+        p.evap_head = p.queue_head + 1;
+        p.split_evap = 1;
+        CU(ctx, cudaMemsetAsync(p.queue_head, 0, 2 * sizeof(unsigned long long), s));
         e = precision == PNUC_FP64 ? launch_persistent_fp64(p, (int)grid, t.block_size, s)
                                    : launch_persistent_fp32(p, (int)grid, t.block_size, count, s);
+        if (e == cudaSuccess)
+            e = precision == PNUC_FP64 ? launch_evap_fp64(p, (int)grid, t.block_size, s)
+                                       : launch_evap_fp32(p, (int)grid, t.block_size, count, s);
     }
     if (e != cudaSuccess) return fail(ctx, PNUC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     return PNUC_OK;
@@ -189,7 +196,6 @@ pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
             t.block_size = 128;
             t.chunk = 256;
             t.kin_batch = 16;
-            t.evap_batch = 16;
             t.refill_threshold = 4;
             int occ = occupancy((pnuc_precision)p, t.block_size, false);
             t.blocks_per_sm = occ > 0 ? occ : 1;

@@ -1,7 +1,7 @@
 // Autotuner of the persistent method and its on-disk cache (host code).
 //
 // The persistent kernel's tuning (block size, refill threshold, queue chunk,
-// and the collision / evaporation batch sizes) changes only the order in which lanes do
+// and the collision batch size) changes only the order in which lanes do
 // their work, never an event's result, so it can be chosen by timing alone. The search is
 // a coordinate descent from the context's current tuning: each parameter in turn takes each
 // candidate value with the others fixed, and keeps the fastest; two passes.
@@ -22,8 +22,7 @@ int32_t *field(pnuc_tuning &t, int k)
     switch (k) {
     case 0: return &t.block_size;
     case 1: return &t.kin_batch;
-    case 2: return &t.evap_batch;
-    case 3: return &t.refill_threshold;
+    case 2: return &t.refill_threshold;
     default: return &t.chunk;
     }
 }
@@ -33,8 +32,7 @@ std::vector<int32_t> candidates(int k)
     switch (k) {
     case 0: return {64, 128, 256};
     case 1: return {1, 8, 16, 24, 32};
-    case 2: return {1, 8, 16, 24, 32};
-    case 3: return {1, 2, 4, 8, 16};
+    case 2: return {1, 2, 4, 8, 16};
     default: return {64, 256, 1024};
     }
 }
@@ -92,7 +90,7 @@ struct Json {
     }
 };
 
-const char *kKeys[6] = {"block_size", "blocks_per_sm", "refill_threshold", "chunk", "kin_batch", "evap_batch"};
+const char *kKeys[5] = {"block_size", "blocks_per_sm", "refill_threshold", "chunk", "kin_batch"};
 
 int32_t *by_name(pnuc_tuning &t, const std::string &k)
 {
@@ -101,7 +99,6 @@ int32_t *by_name(pnuc_tuning &t, const std::string &k)
     if (k == kKeys[2]) return &t.refill_threshold;
     if (k == kKeys[3]) return &t.chunk;
     if (k == kKeys[4]) return &t.kin_batch;
-    if (k == kKeys[5]) return &t.evap_batch;
     return nullptr;
 }
 
@@ -177,7 +174,7 @@ pnuc_status pnuc_autotune(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_ba
     cur.blocks_per_sm = 32;  // the launch clamps to the kernel's occupancy
     double cur_ms = time_tuning(ctx, precision, batch, out, cur, reps, s, e0, e1);
     for (int pass = 0; pass < 2 && cur_ms > 0; ++pass) {
-        for (int k = 0; k < 5; ++k) {
+        for (int k = 0; k < 4; ++k) {
             for (int32_t v : candidates(k)) {
                 pnuc_tuning t = cur;
                 *field(t, k) = v;
@@ -234,7 +231,7 @@ pnuc_status pnuc_save_tuning(pnuc_ctx *ctx, const char *path)
             if (!entries[i].has[p]) continue;
             pnuc_tuning &t = entries[i].t[p];
             fprintf(f, "%s\n    \"%s\": {", first ? "" : ",", p ? "fp64" : "fp32");
-            for (int k = 0; k < 6; ++k) fprintf(f, "%s\"%s\": %d", k ? ", " : "", kKeys[k], *by_name(t, kKeys[k]));
+            for (int k = 0; k < 5; ++k) fprintf(f, "%s\"%s\": %d", k ? ", " : "", kKeys[k], *by_name(t, kKeys[k]));
             fprintf(f, "}");
             first = false;
         }

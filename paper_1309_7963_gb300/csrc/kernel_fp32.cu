@@ -14,6 +14,10 @@ cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool
     return count ? dev::launch_persistent<float, true>(p, grid, block, s)
                  : dev::launch_persistent<float, false>(p, grid, block, s);
 }
+cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s)
+{
+    return count ? dev::launch_evap<float, true>(p, grid, block, s) : dev::launch_evap<float, false>(p, grid, block, s);
+}
 int occupancy_persistent_fp32(int block, bool count)
 {
     return count ? dev::occupancy_persistent<float, true>(block) : dev::occupancy_persistent<float, false>(block);

@@ -13,6 +13,10 @@ cudaError_t launch_persistent_fp64(const SimParams &p, int grid, int block, cuda
 {
     return dev::launch_persistent<double, true>(p, grid, block, s);
 }
+cudaError_t launch_evap_fp64(const SimParams &p, int grid, int block, cudaStream_t s)
+{
+    return dev::launch_evap<double, true>(p, grid, block, s);
+}
 int occupancy_persistent_fp64(int block) { return dev::occupancy_persistent<double, true>(block); }
 
 }  // namespace pnuc

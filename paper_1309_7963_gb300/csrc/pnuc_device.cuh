@@ -108,6 +108,17 @@ struct Stream {
             left += 4;
         }
     }
+    // positions the stream at draw d (the next draw returned is draw d)
+    __device__ void seek(uint64_t d)
+    {
+        block = (uint32_t)(d >> 2);
+        left = 0;
+        head = 0;
+        ensure(4);
+        head = (int)(d & 3);
+        left -= (int)(d & 3);
+    }
+    __device__ __forceinline__ uint32_t position() const { return 4u * block - (uint32_t)left; }
     __device__ __forceinline__ R next()
     {
         R u = buf[head * stride];
@@ -324,6 +335,7 @@ struct Lane {
     // event bookkeeping (FP64)
     int steps, attempts, n_coll, n_index, n_esc, n_p_esc, n_evap;
     uint32_t flags;
+    uint32_t pend;  // 1 + the draw index at which a pending evaporation resumes, else 0
     double Esum, Px, Py, Pz;
     // residual / evaporation
     int Z, A, Zc, Ac;
@@ -375,7 +387,7 @@ __device__ void write_residual(const SimParams &P, const Lane<R> &L)
     o.n_collisions = (uint16_t)min(L.n_coll, 65535);
     o.n_attempts = (uint16_t)min(L.attempts, 65535);
     o.flags = L.flags;
-    o.reserved = 0;
+    o.reserved = L.pend;
     o.Estar_cascade = L.Estar_c;
     o.Estar_final = L.Estar;
     o.P_cascade[0] = (float)L.Px;  // set by end_cascade; zero for events without a cascade
@@ -400,6 +412,7 @@ __device__ void begin_event(const SimParams &P, const TargetScalars *tabs, Lane<
     L.tgt = __ldg(&P.target_ids[ev]);
     L.steps = L.attempts = L.n_coll = L.n_index = L.n_esc = L.n_p_esc = L.n_evap = 0;
     L.flags = 0;
+    L.pend = 0;
     L.Esum = L.Px = L.Py = L.Pz = 0.0;
     L.Estar = L.Estar_c = 0.0;
     L.Er = L.Prx = L.Pry = L.Prz = 0.0;
@@ -473,13 +486,55 @@ __device__ void end_cascade(const SimParams &P, const TargetScalars &tab, Lane<R
         L.phase = kFinish;
         return;
     }
-    double Estar = Er - __ldg(&P.mass[Z * kMassA + A]);
+    const double Mc = __ldg(&P.mass[Z * kMassA + A]);
+    double Estar = Er - Mc;
     L.Estar = L.Estar_c = Estar;
     if (!(Estar > 0.0)) {
         L.flags |= PNUC_FLAG_NO_EXCITATION;
         L.phase = kFinish;
         return;
     }
+    L.Er = Mc + Estar;  // the excited residual at rest: its total energy is M + E*
+    if (P.split_evap) {
+        // the evaporation kernel resumes this event from its residual record
+        L.pend = L.rng.position() + 1u;
+        L.phase = kFinish;
+        return;
+    }
+    L.phase = kEvap;
+}
+
+// Resumes event ev's evaporation from the residual record the cascade kernel wrote (the
+// evaporation kernel of the persistent method). Leaves the lane idle if nothing is pending.
+template <typename R>
+__device__ void begin_evap(const SimParams &P, Lane<R> &L, uint32_t ev)
+{
+    const uint4 *src = reinterpret_cast<const uint4 *>(P.res + ev);
+    alignas(16) pnuc_residual o;
+    uint4 *dst = reinterpret_cast<uint4 *>(&o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dst[k] = src[k];
+    if (o.reserved == 0) {
+        L.phase = kIdle;
+        return;
+    }
+    L.ev = ev;
+    L.Z = L.Zc = o.Z_cascade;
+    L.A = L.Ac = o.A_cascade;
+    L.n_esc = L.n_index = o.n_cascade;
+    L.n_coll = o.n_collisions;
+    L.attempts = o.n_attempts;
+    L.n_evap = 0;
+    L.flags = o.flags;
+    L.pend = 0;
+    L.Estar = L.Estar_c = o.Estar_cascade;
+    L.Er = __ldg(&P.mass[L.Z * kMassA + L.A]) + L.Estar;
+    L.Px = o.P_cascade[0];
+    L.Py = o.P_cascade[1];
+    L.Pz = o.P_cascade[2];
+    L.Prx = L.Pry = L.Prz = 0.0;
+    L.rng.reset(P.seed, P.first_event_id + ev);
+    L.rng.seek(o.reserved - 1u);
     L.phase = kEvap;
 }
 

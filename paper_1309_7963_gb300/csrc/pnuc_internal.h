@@ -57,15 +57,19 @@ struct SimParams {
     int32_t n_targets;
     const double *mass;            // [kMassZ * kMassA] SEMF masses, MeV (0 where undefined)
     const double *cbrtA;           // [kMassA] A^(1/3)
-    unsigned long long *queue_head;  // persistent method: next unclaimed event
+    unsigned long long *queue_head;  // persistent method: next unclaimed event of the cascade kernel
+    unsigned long long *evap_head;   // persistent method: next unclaimed event of the evaporation kernel
+    int32_t split_evap;              // 1: the cascade leaves evaporation pending for evap_kernel
     int32_t max_steps, max_attempts, max_evap_steps, max_evap_trials;
     int32_t refill_threshold, chunk;
-    int32_t kin_batch, evap_batch;  // persistent kernel: lanes a warp gathers before FP64-heavy work
+    int32_t kin_batch;  // persistent kernel: accepted collisions a warp gathers before their kinematics
 };
 
 // Launchers, one per compiled variant (kernel_fp32.cu, kernel_fp64.cu).
 cudaError_t launch_plain_fp64(const SimParams &p, int block, cudaStream_t s);
 cudaError_t launch_persistent_fp64(const SimParams &p, int grid, int block, cudaStream_t s);
+cudaError_t launch_evap_fp64(const SimParams &p, int grid, int block, cudaStream_t s);
+cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s);
 cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, cudaStream_t s);
 cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s);
 // Resident blocks per SM of the persistent kernels at a block size.

@@ -95,10 +95,47 @@ __global__ void __launch_bounds__(512) plain_kernel(const SimParams P)
     flush_counters<kCount>(P, cnt);
 }
 
-// Persistent kernel: grid = resident blocks only. Each warp keeps a reservoir
-// [wnext, wend) of claimed event indices; when at least refill_threshold lanes are idle
-// (or no lane is busy) the idle lanes take events from it, and the warp claims a new chunk
-// with one atomicAdd on the queue head when it runs short.
+// Warp-level reservoir [next, end) of claimed queue indices (warp-uniform state). take()
+// gives every idle lane one index, or ~0 once the queue is exhausted, and claims a new chunk
+// of `chunk` indices with one atomicAdd on the queue head when the reservoir runs short.
+struct WarpQueue {
+    unsigned long long next = 0, end = 0;
+    bool drained = false;
+    __device__ __forceinline__ unsigned long long take(unsigned idle, unsigned lane, unsigned long long *head,
+                                                       unsigned long long n, unsigned long long chunk)
+    {
+        const unsigned FULL = 0xffffffffu;
+        const unsigned long long nidle = (unsigned long long)__popc(idle);
+        const unsigned rank = __popc(idle & ((1u << lane) - 1u));
+        const unsigned long long avail = end - next;
+        unsigned long long ev;
+        if (avail >= nidle || drained) {
+            ev = rank < avail ? next + rank : ~0ull;
+            next = avail >= nidle ? next + nidle : end;
+            return ev;
+        }
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(head, chunk);
+        got = __shfl_sync(FULL, got, 0);
+        unsigned long long gend = got + chunk < n ? got + chunk : n;
+        if (got >= n) {
+            drained = true;
+            gend = got;
+        }
+        ev = rank < avail ? next + rank : got + (rank - avail);
+        if (rank >= avail && ev >= gend) ev = ~0ull;
+        const unsigned long long used_new = nidle - avail;
+        next = got + used_new < gend ? got + used_new : gend;
+        end = gend;
+        return ev;
+    }
+};
+
+// Persistent cascade kernel: grid = resident blocks only. When at least refill_threshold lanes
+// of a warp are idle (or none is busy) they take events from the warp's queue reservoir.
+// Accepted collisions wait until kin_batch lanes of the warp need their FP64 kinematics (or
+// nothing else can progress). Events with E* > 0 leave their evaporation pending in the
+// residual record for evap_kernel.
 template <typename R, bool kCount>
 __device__ __forceinline__ void persistent_body(const SimParams &P)
 {
@@ -118,71 +155,121 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
     L.rng.buf = ring_base<R>(P, smem);
     L.rng.stride = blockDim.x;
     Particle<R> stack[kStackCap];
-    unsigned long long wnext = 0, wend = 0;  // warp-uniform
-    bool drained = false;                    // warp-uniform: the queue returned nothing
-    const unsigned long long chunk = (unsigned long long)P.chunk;
+    WarpQueue Q;
     while (true) {
+        const long long t_top = kCount ? clock64() : 0;
         if (L.phase == kFinish) {
             finish_event<R, kCount>(P, L, C);
             L.phase = kIdle;
         }
         const unsigned idle = __ballot_sync(FULL, L.phase == kIdle);
-        const unsigned busy = __ballot_sync(FULL, L.phase == kEntry || L.phase == kTransport || L.phase == kEvap ||
-                                                      L.phase == kKinWait);
+        const unsigned busy = __ballot_sync(FULL, L.phase == kEntry || L.phase == kTransport || L.phase == kKinWait);
         const int nidle = __popc(idle);
-        if (nidle && (nidle >= P.refill_threshold || busy == 0 || drained)) {
-            const unsigned rank = __popc(idle & ((1u << lane) - 1u));
-            unsigned long long avail = wend - wnext;
-            unsigned long long ev;
-            if (avail >= (unsigned long long)nidle || drained) {
-                ev = wnext + rank;
-                wnext = avail >= (unsigned long long)nidle ? wnext + nidle : wend;
-                if (rank >= avail) ev = ~0ull;
-            } else {
-                unsigned long long got = 0;
-                if (lane == 0) got = atomicAdd(P.queue_head, chunk);
-                got = __shfl_sync(FULL, got, 0);
-                unsigned long long gend = got + chunk < P.n ? got + chunk : P.n;
-                if (got >= P.n) {
-                    drained = true;
-                    gend = got;
-                }
-                ev = rank < avail ? wnext + rank : got + (rank - avail);
-                if (rank >= avail && ev >= gend) ev = ~0ull;
-                unsigned long long used_new = (unsigned long long)nidle - avail;
-                wnext = got + used_new < gend ? got + used_new : gend;
-                wend = gend;
-            }
+        if (nidle && (nidle >= P.refill_threshold || busy == 0 || Q.drained)) {
+            const unsigned long long ev = Q.take(idle, lane, P.queue_head, P.n, (unsigned long long)P.chunk);
             if (L.phase == kIdle) {
                 if (ev < P.n) begin_event<R>(P, ts, L, (uint32_t)ev);
                 else L.phase = kExhausted;
             }
         }
         if (__all_sync(FULL, L.phase == kExhausted)) break;
-        // FP64-heavy work (collision kinematics, evaporation steps) runs when enough lanes of
-        // the warp need it, or when nothing else can progress, so that it executes with many
-        // lanes active; the others keep transporting meanwhile.
         const unsigned run = __ballot_sync(FULL, L.phase == kEntry || L.phase == kTransport);
         const unsigned kin = __ballot_sync(FULL, L.phase == kKinWait);
-        const unsigned evp = __ballot_sync(FULL, L.phase == kEvap);
         const bool do_kin = kin && (__popc(kin) >= P.kin_batch || run == 0);
-        const bool do_evap = evp && (__popc(evp) >= P.evap_batch || (run == 0 && kin == 0));
-        // the iteration's draws: at most 6 in a transport step, 3 in a collision, 2 at an
-        // entry, 1 before the evaporation sampler (which ensures its own)
-        if ((L.phase == kKinWait && do_kin) || (L.phase == kEvap && do_evap) || L.phase == kTransport ||
-            L.phase == kEntry)
-            L.rng.ensure(8);
-        if (L.phase == kKinWait) {
-            if (do_kin) finish_collision<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
-        } else if (L.phase == kEvap) {
-            if (do_evap) step_evap<R, kCount>(P, L, C);
-        } else if (L.phase == kTransport) {
-            step_transport<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
-        } else if (L.phase == kEntry) {
-            step_entry<R, kCount>(P, sh[L.tgt], ts[L.tgt].R, L, C);
+        // the iteration's draws: at most 6 in a transport step, 3 in a collision, 2 at an entry
+        if ((L.phase == kKinWait && do_kin) || L.phase == kTransport || L.phase == kEntry) L.rng.ensure(8);
+        if (!kCount) {
+            if (L.phase == kKinWait) {
+                if (do_kin) finish_collision<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+            } else if (L.phase == kTransport) {
+                step_transport<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+            } else if (L.phase == kEntry) {
+                step_entry<R, kCount>(P, sh[L.tgt], ts[L.tgt].R, L, C);
+            }
+        } else {
+            // the counting variant times each phase block of the warp (one lane records)
+            const int ph = L.phase;
+            long long t0 = clock64();
+            if (ph == kKinWait && do_kin) finish_collision<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+            __syncwarp();
+            long long t1 = clock64();
+            if (ph == kTransport) step_transport<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+            else if (ph == kEntry) step_entry<R, kCount>(P, sh[L.tgt], ts[L.tgt].R, L, C);
+            __syncwarp();
+            long long t2 = clock64();
+            if (lane == 0) {
+                C.add(PNUC_C_CYCLES_COLLISION, (unsigned)(t1 - t0));
+                C.add(PNUC_C_CYCLES_TRANSPORT, (unsigned)(t2 - t1));
+                C.add(PNUC_C_CYCLES_REFILL, (unsigned)(t0 - t_top));
+            }
         }
     }
     flush_counters<kCount>(P, cnt);
+}
+
+// Persistent evaporation kernel (after the cascade kernel on the same stream): every lane
+// evaporates, so the FP64 width exponentials and the decays run with full warps. Lanes take
+// event indices from the evaporation queue and skip events with nothing pending.
+template <typename R, bool kCount>
+__device__ __forceinline__ void evap_body(const SimParams &P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long cnt[PNUC_N_COUNTERS];
+    if (kCount)
+        for (int k = threadIdx.x; k < PNUC_N_COUNTERS; k += blockDim.x) cnt[k] = 0;
+    __syncthreads();
+    Counters<kCount> C{cnt};
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lane = threadIdx.x & 31;
+    Lane<R> L;
+    L.phase = kIdle;
+    L.rng.buf = ring_base<R>(P, smem);
+    L.rng.stride = blockDim.x;
+    uint32_t d0 = 0;  // draw index at which the lane's evaporation resumed
+    WarpQueue Q;
+    while (true) {
+        const long long t_top = kCount ? clock64() : 0;
+        if (L.phase == kFinish) {
+            write_residual(P, L);
+            C.add(PNUC_C_DRAWS, L.rng.position() - d0);
+            L.phase = kIdle;
+        }
+        const unsigned idle = __ballot_sync(FULL, L.phase == kIdle);
+        const int nidle = __popc(idle);
+        const unsigned busy = __ballot_sync(FULL, L.phase == kEvap);
+        if (nidle && (nidle >= P.refill_threshold || busy == 0 || Q.drained)) {
+            const unsigned long long ev = Q.take(idle, lane, P.evap_head, P.n, (unsigned long long)P.chunk);
+            if (L.phase == kIdle) {
+                if (ev < P.n) {
+                    begin_evap<R>(P, L, (uint32_t)ev);
+                    if (L.phase == kEvap) d0 = L.rng.position();
+                } else {
+                    L.phase = kExhausted;
+                }
+            }
+        }
+        if (__all_sync(FULL, L.phase == kExhausted)) break;
+        const long long t1 = kCount ? clock64() : 0;
+        if (L.phase == kEvap) {
+            L.rng.ensure(8);
+            step_evap<R, kCount>(P, L, C);
+        }
+        if (kCount) {
+            __syncwarp();
+            if (lane == 0) {
+                C.add(PNUC_C_CYCLES_EVAPORATION, (unsigned)(clock64() - t1));
+                C.add(PNUC_C_CYCLES_REFILL, (unsigned)(t1 - t_top));
+            }
+        }
+    }
+    flush_counters<kCount>(P, cnt);
+}
+
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename R, bool kCount>
@@ -191,11 +278,21 @@ __global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
     persistent_body<R, kCount>(P);
 }
 
-template <typename K>
-cudaError_t allow_smem(K kernel, size_t bytes)
+template <typename R, bool kCount>
+__global__ void __launch_bounds__(512) evap_kernel(const SimParams P)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    evap_body<R, kCount>(P);
+}
+
+template <typename R, bool kCount>
+cudaError_t launch_evap(const SimParams &p, int grid, int block, cudaStream_t s)
+{
+    if (p.n == 0) return cudaSuccess;
+    size_t smem = smem_bytes<R>(p.n_targets, block);
+    cudaError_t e = allow_smem(evap_kernel<R, kCount>, smem);
+    if (e != cudaSuccess) return e;
+    evap_kernel<R, kCount><<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
 }
 
 template <typename R, bool kCount>

@@ -26,7 +26,8 @@ RESIDUAL_DTYPE = np.dtype([("Z_cascade", "<u2"), ("A_cascade", "<u2"), ("Z_final
 assert SECONDARY_DTYPE.itemsize == 32 and RESIDUAL_DTYPE.itemsize == 64
 
 COUNTER_NAMES = ("steps", "candidates", "kinematics", "pauli_blocked", "collisions", "crossings", "reflections",
-                 "escapes", "captures", "attempts", "evap_steps", "evap_trials", "draws")
+                 "escapes", "captures", "attempts", "evap_steps", "evap_trials", "draws", "cycles_transport",
+                 "cycles_collision", "cycles_evaporation", "cycles_refill")
 FLAGS = dict(bad_input=1, attempt_cap=2, step_cap=4, stack_overflow=8, bad_residual=16, no_excitation=32,
              evap_trial_cap=64, evap_step_cap=128, output_overflow=256)
 PRECISION = {"fp32": 0, "fp64": 1}
@@ -52,7 +53,7 @@ class pnuc_output(C.Structure):
 
 class pnuc_tuning(C.Structure):
     _fields_ = [("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_threshold", C.c_int32),
-                ("chunk", C.c_int32), ("kin_batch", C.c_int32), ("evap_batch", C.c_int32)]
+                ("chunk", C.c_int32), ("kin_batch", C.c_int32)]
 
 
 class pnuc_target_info(C.Structure):

@@ -32,9 +32,9 @@ def test_tuning_variants_give_identical_results(ctx):
     saved = ctx.get_tuning("fp32")
     try:
         ref = results(ctx.simulate(e, t, seed=21, precision="fp32", method="plain"))
-        for tun in [dict(block_size=256, kin_batch=1, evap_batch=1, refill_threshold=1, chunk=64),
-                    dict(block_size=128, kin_batch=32, evap_batch=32, refill_threshold=16, chunk=1024),
-                    dict(block_size=64, kin_batch=8, evap_batch=24, refill_threshold=4, chunk=256)]:
+        for tun in [dict(block_size=256, kin_batch=1, refill_threshold=1, chunk=64),
+                    dict(block_size=128, kin_batch=32, refill_threshold=16, chunk=1024),
+                    dict(block_size=64, kin_batch=8, refill_threshold=4, chunk=256)]:
             ctx.set_tuning("fp32", **tun)
             got = results(ctx.simulate(e, t, seed=21, precision="fp32", method="persistent"))
             torch.cuda.synchronize()
@@ -44,7 +44,7 @@ def test_tuning_variants_give_identical_results(ctx):
 
 
 def test_invalid_tuning_rejected(ctx):
-    for bad in [dict(block_size=96), dict(kin_batch=0), dict(evap_batch=33), dict(chunk=8),
+    for bad in [dict(block_size=96), dict(kin_batch=0), dict(kin_batch=33), dict(chunk=8),
                 dict(refill_threshold=40), dict(blocks_per_sm=0)]:
         with pytest.raises(pnuc.PnucError):
             ctx.set_tuning("fp32", **bad)
