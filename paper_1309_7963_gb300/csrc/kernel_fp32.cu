@@ -4,6 +4,13 @@
 #include "pnuc_kernels.cuh"
 
 namespace pnuc {
+namespace dev {
+namespace {
+// The FP32 cascade kernel capped at 96 registers: five resident 128-thread blocks per SM
+// instead of four (3.5% faster on GB300 than the 105 registers it uses unbounded).
+__global__ void __maxnreg__(96) persistent_kernel_f32(const SimParams P) { persistent_body<float, false>(P); }
+}  // namespace
+}  // namespace dev
 
 cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, cudaStream_t s)
 {
@@ -11,8 +18,8 @@ cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, cudaStr
 }
 cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s)
 {
-    return count ? dev::launch_persistent<float, true>(p, grid, block, s)
-                 : dev::launch_persistent<float, false>(p, grid, block, s);
+    if (count) return dev::launch_persistent<float, true>(p, grid, block, s);
+    return dev::launch_kernel(dev::persistent_kernel_f32, dev::smem_bytes<float>(p.n_targets, block), p, grid, block, s);
 }
 cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s)
 {
@@ -20,7 +27,8 @@ cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count
 }
 int occupancy_persistent_fp32(int block, bool count)
 {
-    return count ? dev::occupancy_persistent<float, true>(block) : dev::occupancy_persistent<float, false>(block);
+    if (count) return dev::occupancy_persistent<float, true>(block);
+    return dev::occupancy_of(dev::persistent_kernel_f32, dev::smem_bytes<float>(kMaxTargets, block), block);
 }
 
 }  // namespace pnuc

@@ -318,6 +318,25 @@ cudaError_t launch_persistent(const SimParams &p, int grid, int block, cudaStrea
     return cudaGetLastError();
 }
 
+template <typename K>
+cudaError_t launch_kernel(K kernel, size_t smem, const SimParams &p, int grid, int block, cudaStream_t s)
+{
+    if (p.n == 0) return cudaSuccess;
+    cudaError_t e = allow_smem(kernel, smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<grid, block, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename K>
+int occupancy_of(K kernel, size_t smem, int block)
+{
+    int nb = 0;
+    allow_smem(kernel, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem);
+    return nb;
+}
+
 template <typename R, bool kCount>
 int occupancy_persistent(int block)
 {
