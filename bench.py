@@ -39,33 +39,43 @@ WORKLOAD = "1e6 p-16O + 1e6 p-40Ca at 200 MeV, one batch of 2e6 events per step"
 # Algorithmic FP64 operations of the FP32-mode model per counted unit (see the design doc,
 # "Roofline"): adds, multiplies and FMAs count 1; a division or square root 8 and an
 # exponential 16 (the instruction counts of Newton-Raphson and Cody-Waite/Horner
-# implementations). The FP64 pipe is the binding ALU pipe of the event kernels.
-FP64_OPS_PER_UNIT = {
+# implementations). The FP64 pipe is the binding ALU pipe of the event kernels. Units of the
+# cascade kernel and of the evaporation kernel are listed apart.
+CASCADE_FP64_OPS = {
     "kinematics": 140,  # pair energies, CM boost in and out, product energies
-    "evap_steps": 480,  # six widths (FP64 exponentials, Q-values) + two-body decay + boost
     "escapes": 5,       # energy/momentum bookkeeping of an escaping nucleon
-    "attempts": 0,
 }
-FP64_OPS_PER_EVENT = 15  # excitation energy from the energy balance
+CASCADE_FP64_OPS_PER_EVENT = 15  # excitation energy from the energy balance
+EVAP_FP64_OPS = {
+    "evap_steps": 480,  # six widths (FP64 exponentials, Q-values) + two-body decay + boost
+}
+KERNEL_FILES = ("pnuc_device.cuh", "pnuc_kernels.cuh", "kernel_fp32.cu", "pnuc_internal.h")
 
 
-def traffic_per_event():
-    """DRAM bytes per event of the persistent FP32 kernel from its last ncu capture
-    (profiles/persistent_kernel_traffic.txt), or None if the kernel sources changed since."""
+def kernel_sha1() -> str:
     import hashlib
-    path = os.path.join(ROOT, "profiles", "persistent_kernel_traffic.txt")
-    if not os.path.exists(path):
-        return None
-    kv = dict(line.split(": ", 1) for line in open(path) if ": " in line and not line.startswith("#"))
     h = hashlib.sha1()
-    for f in ("pnuc_device.cuh", "pnuc_kernels.cuh", "kernel_fp32.cu", "pnuc_internal.h"):
+    for f in KERNEL_FILES:
         h.update(open(os.path.join(ROOT, "paper_1309_7963_gb300", "csrc", f), "rb").read())
-    return float(kv["bytes_per_event"]) if h.hexdigest() == kv.get("kernel_sha1", "").strip() else None
+    return h.hexdigest()
 
 
-def fp64_ops_per_event(counters: dict, n_events: int) -> float:
-    tot = sum(counters[k] * v for k, v in FP64_OPS_PER_UNIT.items()) + FP64_OPS_PER_EVENT * n_events
-    return tot / n_events
+def traffic_per_event() -> dict:
+    """DRAM bytes per event of the FP32 cascade and evaporation kernels from their last ncu
+    capture (profiles/persistent_kernels_traffic.txt); empty if the kernel sources changed since."""
+    path = os.path.join(ROOT, "profiles", "persistent_kernels_traffic.txt")
+    if not os.path.exists(path):
+        return {}
+    kv = dict(line.strip().split(": ", 1) for line in open(path) if ": " in line and not line.startswith("#"))
+    if kv.get("kernel_sha1", "") != kernel_sha1():
+        return {}
+    return {k: float(kv[k + "_bytes_per_event"]) for k in ("cascade", "evaporation") if k + "_bytes_per_event" in kv}
+
+
+def fp64_ops_per_event(counters: dict, n_events: int) -> dict:
+    cas = sum(counters[k] * v for k, v in CASCADE_FP64_OPS.items()) / n_events + CASCADE_FP64_OPS_PER_EVENT
+    eva = sum(counters[k] * v for k, v in EVAP_FP64_OPS.items()) / n_events
+    return {"cascade": cas, "evaporation": eva}
 
 
 def parse():
@@ -236,10 +246,11 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def timed(method, steps, warmup):
+    def timed(method, steps, warmup, per_kernel=False):
         for _ in range(warmup):
             ctx.simulate(e_dev, t_dev, seed=w.seed, first_event_id=first, precision="fp32", method=method, out=out)
         torch.cuda.synchronize()
+        ctx.kernel_timing(per_kernel)  # CUDA events around each kernel, on the launching stream
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
@@ -263,7 +274,9 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
-    total_ms, kern_ms = timed("persistent", args.steps, args.warmup)
+    total_ms, kern_ms = timed("persistent", args.steps, args.warmup, per_kernel=True)
+    ctx.kernel_timing(False)
+    ktimes = ctx.kernel_times()
     clk = clocks.stop()
     total_ms = pdist.max_over_ranks(total_ms, device="cuda")
     n_sec = out.n_secondaries()
@@ -303,13 +316,21 @@ def main():
     del cnt
     ops_ev = fp64_ops_per_event(counters, n)
     peaks = ctx.measure_peaks()
-    achieved = ops_ev * n / (launch_ms * 1e-3)
-    roofline = {"bound": "alu", "pipe": "fp64", "achieved": achieved / 1e9, "peak": peaks["fp64_fma"] / 1e9,
-                "unit": "FP64 Gop/s", "frac": achieved / peaks["fp64_fma"],
-                "traffic": (traffic_per_event() * n) if traffic_per_event() else None,
-                "traffic_note": "DRAM bytes per launch, scaled by events from an 8e5-event ncu capture",
-                "fp64_ops_per_event": ops_ev, "peak_source": "pnuc_measure_peaks (FP64 FMA lanes/s, this run)",
-                "peaks_lane_ops_per_s": peaks,
+    kernels = {}
+    traffic = traffic_per_event()
+    for name, ms_key in (("cascade", "cascade_ms"), ("evaporation", "evaporation_ms")):
+        ms = ktimes[ms_key] / max(1, ktimes["launches"])
+        achieved = ops_ev[name] * n / (ms * 1e-3)
+        kernels[name] = {"ms_per_launch": ms, "fp64_ops_per_event": ops_ev[name], "achieved": achieved / 1e9,
+                         "frac": achieved / peaks["fp64_fma"],
+                         "traffic": traffic[name] * n if name in traffic else None}
+    top = max(kernels, key=lambda k: kernels[k]["ms_per_launch"])
+    kt = kernels[top]
+    roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"{top} kernel (FP32 mode)", "achieved": kt["achieved"],
+                "peak": peaks["fp64_fma"] / 1e9, "unit": "FP64 Gop/s", "frac": kt["frac"], "traffic": kt["traffic"],
+                "traffic_note": "DRAM bytes per launch, scaled by events from an ncu capture of 8e5 events",
+                "peak_source": "pnuc_measure_peaks, FP64 FMA lane-ops/s measured in this run",
+                "timed_launches": ktimes["launches"], "kernels": kernels, "peaks_lane_ops_per_s": peaks,
                 "work_per_event": {k: v / n for k, v in counters.items() if not k.startswith("cycles")}}
     cyc = {k[7:]: counters[k] for k in counters if k.startswith("cycles_")}
     phase_split = {k: v / max(1, sum(cyc.values())) for k, v in cyc.items()}
@@ -332,7 +353,7 @@ def main():
         "p50_ms": serving["runs"][-1]["p50_ms"] if serving else None,
         "p99_ms": serving["runs"][-1]["p99_ms"] if serving else None,
         "serving": serving,
-        "e2e": e2e, "roofline": roofline, "cpu_baseline": cb, "clocks": clk, "gpu_launches": args.steps,
+        "e2e": e2e, "roofline": roofline, "cpu_baseline": cb, "clocks": clk, "gpu_launches": 2 * args.steps,
     }
     print(json.dumps(line))
 

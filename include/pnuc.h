@@ -310,6 +310,21 @@ pnuc_status pnuc_server_reset_stats(pnuc_server *server);
 /* Drops queued requests, waits for those in flight, frees everything. Safe on NULL. */
 pnuc_status pnuc_server_destroy(pnuc_server *server);
 
+/* Per-kernel timing of pnuc_simulate's launches (measurement support; the paper has no
+ * counterpart). pnuc_kernel_timing(ctx, 1) clears the record and makes later launches
+ * through pnuc_simulate and the entry points built on it record CUDA events on the
+ * launching stream: before the first kernel, between the cascade kernel and the evaporation
+ * kernel (persistent method), and after the last kernel. Launches made while the stream is
+ * being captured into a graph, and launches beyond the first 4096 since the clear, are not
+ * recorded. pnuc_kernel_timing(ctx, 0) stops recording and keeps the record.
+ * pnuc_kernel_times waits for the recorded events and returns, summed over the recorded
+ * launches, the milliseconds of the first kernel (the cascade kernel, or the plain kernel)
+ * and of the evaporation kernel (0 for the plain method), and the number of recorded
+ * launches. Any output pointer may be NULL. The record is not locked: enable it only while one
+ * host thread launches on the context (not while a pnuc_server runs on it). */
+pnuc_status pnuc_kernel_timing(pnuc_ctx *ctx, int32_t enable);
+pnuc_status pnuc_kernel_times(pnuc_ctx *ctx, double *cascade_ms, double *evaporation_ms, uint64_t *launches);
+
 /* Measured throughput of the pipes the event kernels use, in lane operations per second
  * (one fused multiply-add = one operation): FP32 FMA, FP64 FMA, special-function unit
  * (reciprocal square root) and 32-bit integer multiply-add. Independent FMA chains on 8

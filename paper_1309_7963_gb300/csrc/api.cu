@@ -65,6 +65,34 @@ pnuc_status check_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method met
     return PNUC_OK;
 }
 
+namespace {
+
+constexpr size_t kMaxTimedLaunches = 4096;
+
+// Three timing events for the next launch on s, or null when timing is off, the stream is
+// being captured or the record is full.
+cudaEvent_t *timing_slot(pnuc_ctx *ctx, cudaStream_t s)
+{
+    if (!ctx->timing) return nullptr;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    if (ctx->tev_used + 3 > ctx->tev.size()) {
+        if (ctx->tev.size() >= 3 * kMaxTimedLaunches) return nullptr;
+        for (int k = 0; k < 3; ++k) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ctx->tev.push_back(e);
+        }
+        ctx->tev_two.push_back(1);
+    }
+    ctx->tev_two[ctx->tev_used / 3] = 1;
+    cudaEvent_t *ev = ctx->tev.data() + ctx->tev_used;
+    ctx->tev_used += 3;
+    return ev;
+}
+
+}  // namespace
+
 pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
                          const pnuc_output *out, cudaStream_t s, const pnuc_tuning &t, unsigned long long *queue_head)
 {
@@ -97,10 +125,15 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
     p.evap_head = nullptr;
     p.split_evap = 0;
     const bool count = out->counters != nullptr;
-    cudaError_t e;
+    cudaEvent_t *ev = timing_slot(ctx, s);
+    cudaError_t e = ev ? cudaEventRecord(ev[0], s) : cudaSuccess;
+    if (e != cudaSuccess) ctx->tev_used -= 3;
+    CU(ctx, e);
     if (method == PNUC_PLAIN) {
         e = precision == PNUC_FP64 ? launch_plain_fp64(p, t.block_size, s)
                                    : launch_plain_fp32(p, t.block_size, count, s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+        if (ev) ctx->tev_two[ctx->tev_used / 3 - 1] = 0;
     } else {
         int occ = occupancy(precision, t.block_size, count);
         int bps = std::min(t.blocks_per_sm, std::max(occ, 1));
@@ -114,10 +147,18 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
         CU(ctx, cudaMemsetAsync(p.queue_head, 0, 2 * sizeof(unsigned long long), s));
         e = precision == PNUC_FP64 ? launch_persistent_fp64(p, (int)grid, t.block_size, s)
                                    : launch_persistent_fp32(p, (int)grid, t.block_size, count, s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+        // the evaporation kernel's own resident grid (it uses more registers)
+        int occ_e = precision == PNUC_FP64 ? occupancy_evap_fp64(t.block_size)
+                                           : occupancy_evap_fp32(t.block_size, count);
+        unsigned long long egrid = (unsigned long long)std::max(std::min(t.blocks_per_sm, occ_e), 1) * ctx->sm_count;
+        if (egrid > grid) egrid = grid;
         if (e == cudaSuccess)
-            e = precision == PNUC_FP64 ? launch_evap_fp64(p, (int)grid, t.block_size, s)
-                                       : launch_evap_fp32(p, (int)grid, t.block_size, count, s);
+            e = precision == PNUC_FP64 ? launch_evap_fp64(p, (int)egrid, t.block_size, s)
+                                       : launch_evap_fp32(p, (int)egrid, t.block_size, count, s);
     }
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
+    if (e != cudaSuccess && ev) ctx->tev_used -= 3;  // the slot is the last one taken
     if (e != cudaSuccess) return fail(ctx, PNUC_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
     return PNUC_OK;
 }
@@ -222,6 +263,7 @@ pnuc_status pnuc_destroy(pnuc_ctx *ctx)
     cudaFree(ctx->h_res);
     cudaFree(ctx->h_sec);
     cudaFree(ctx->h_count);
+    for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
     delete ctx;
     return PNUC_OK;
 }
@@ -447,6 +489,33 @@ pnuc_status pnuc_measure_peaks(pnuc_ctx *ctx, pnuc_peaks *out)
     out->fp64_fma = v[1];
     out->mufu = v[2];
     out->int32_mad = v[3];
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_kernel_timing(pnuc_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    if (enable) ctx->tev_used = 0;
+    ctx->timing = enable != 0;
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_kernel_times(pnuc_ctx *ctx, double *cascade_ms, double *evaporation_ms, uint64_t *launches)
+{
+    if (!ctx) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    CU(ctx, cudaSetDevice(ctx->cfg.device));
+    double c = 0.0, v = 0.0;
+    for (size_t i = 0; i + 2 < ctx->tev_used; i += 3) {
+        CU(ctx, cudaEventSynchronize(ctx->tev[i + 2]));
+        float a = 0.f, b = 0.f;
+        CU(ctx, cudaEventElapsedTime(&a, ctx->tev[i], ctx->tev[i + 1]));
+        if (ctx->tev_two[i / 3]) CU(ctx, cudaEventElapsedTime(&b, ctx->tev[i + 1], ctx->tev[i + 2]));
+        c += a;
+        v += b;
+    }
+    if (cascade_ms) *cascade_ms = c;
+    if (evaporation_ms) *evaporation_ms = v;
+    if (launches) *launches = ctx->tev_used / 3;
     return PNUC_OK;
 }
 

@@ -34,6 +34,11 @@ struct pnuc_ctx {
     pnuc_secondary *h_sec = nullptr;
     uint64_t h_sec_cap = 0;
     unsigned long long *h_count = nullptr;
+    // pnuc_kernel_timing: three events per recorded launch
+    bool timing = false;
+    std::vector<cudaEvent_t> tev;
+    std::vector<char> tev_two;  // per recorded launch: 1 if it ran two kernels
+    size_t tev_used = 0;
 };
 
 namespace pnuc {

@@ -25,6 +25,10 @@ cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count
 {
     return count ? dev::launch_evap<float, true>(p, grid, block, s) : dev::launch_evap<float, false>(p, grid, block, s);
 }
+int occupancy_evap_fp32(int block, bool count)
+{
+    return count ? dev::occupancy_evap<float, true>(block) : dev::occupancy_evap<float, false>(block);
+}
 int occupancy_persistent_fp32(int block, bool count)
 {
     if (count) return dev::occupancy_persistent<float, true>(block);

@@ -18,5 +18,6 @@ cudaError_t launch_evap_fp64(const SimParams &p, int grid, int block, cudaStream
     return dev::launch_evap<double, true>(p, grid, block, s);
 }
 int occupancy_persistent_fp64(int block) { return dev::occupancy_persistent<double, true>(block); }
+int occupancy_evap_fp64(int block) { return dev::occupancy_evap<double, true>(block); }
 
 }  // namespace pnuc

@@ -11,7 +11,9 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cstddef>
 
+#include "fpconv.h"
 #include "pnuc_internal.h"
 
 namespace pnuc {
@@ -27,6 +29,8 @@ constexpr double kTwoPi = 6.283185307179586;
 // ejectiles n, p, d, t, 3He, alpha (§2.4: He and lighter)
 __constant__ double cEjM[6] = {939.565, 938.272, 1875.613, 2808.921, 2808.391, 3727.379};
 __constant__ double cEjG[6] = {2.0, 2.0, 3.0, 2.0, 2.0, 1.0};
+__constant__ float cEjMf[6] = {939.565f, 938.272f, 1875.613f, 2808.921f, 2808.391f, 3727.379f};
+__constant__ float cEjGf[6] = {2.f, 2.f, 3.f, 2.f, 2.f, 1.f};
 __constant__ int cEjZ[6] = {0, 1, 1, 1, 2, 2};
 __constant__ int cEjA[6] = {1, 1, 2, 3, 3, 4};
 
@@ -133,6 +137,20 @@ template <typename R> __device__ __forceinline__ R dot3(const R *a, const R *b) 
 // kinetic energy from |p|^2 without cancellation
 template <typename R> __device__ __forceinline__ R kinetic(R p2, R m) { return p2 / (sqrt(p2 + m * m) + m); }
 __device__ __forceinline__ double nucleon_mass(int s) { return s ? kMp : kMn; }
+template <typename R> __device__ __forceinline__ R nucleon_mass_R(int s) { return s ? R(kMp) : R(kMn); }
+
+// Conversions: in FP32 mode on the integer pipes (fpconv.h), in FP64 mode plain casts.
+template <typename R> __device__ __forceinline__ R to_R(double x) { return (R)x; }
+template <> __device__ __forceinline__ float to_R<float>(double x) { return d2f(x); }
+template <typename R> __device__ __forceinline__ double to_d(R x) { return (double)x; }
+template <> __device__ __forceinline__ double to_d<float>(float x) { return f2d(x); }
+template <typename R> __device__ __forceinline__ float out_f(double x) { return (float)x; }
+template <> __device__ __forceinline__ float out_f<float>(double x) { return d2f(x); }
+// ejectile mass and spin factor of channel j in precision R
+template <typename R> __device__ __forceinline__ R ej_M(int j) { return cEjM[j]; }
+template <> __device__ __forceinline__ float ej_M<float>(int j) { return cEjMf[j]; }
+template <typename R> __device__ __forceinline__ R ej_G(int j) { return cEjG[j]; }
+template <> __device__ __forceinline__ float ej_G<float>(int j) { return cEjGf[j]; }
 
 // ------------------------------------------------------------------ NN cross sections (§2.3, Cugnon et al.)
 template <typename R> __device__ __forceinline__ R clamp_p(R p) { return p < R(0.1) ? R(0.1) : (p > R(2.0) ? R(2.0) : p); }
@@ -374,6 +392,30 @@ __device__ __forceinline__ void emit_secondary(const SimParams &P, uint32_t ev, 
     dst[1] = b;
 }
 
+// A residual record with a pending evaporation (persistent method, between its two kernels)
+// carries the escape sums at full precision: Esum in Estar_cascade, Pz in Estar_final, Px and
+// Py in the 16 bytes from P_cascade[0].
+static_assert(offsetof(pnuc_residual, P_cascade) == 40 && sizeof(pnuc_residual) == 64, "residual layout");
+
+__device__ __forceinline__ void write_pending_sums(pnuc_residual &o, double Esum, double Px, double Py, double Pz)
+{
+    o.Estar_cascade = Esum;
+    o.Estar_final = Pz;
+    unsigned char *b = reinterpret_cast<unsigned char *>(&o);
+    memcpy(b + 40, &Px, 8);
+    memcpy(b + 48, &Py, 8);
+}
+
+__device__ __forceinline__ void read_pending_sums(const pnuc_residual &o, double &Esum, double &Px, double &Py,
+                                                  double &Pz)
+{
+    Esum = o.Estar_cascade;
+    Pz = o.Estar_final;
+    const unsigned char *b = reinterpret_cast<const unsigned char *>(&o);
+    memcpy(&Px, b + 40, 8);
+    memcpy(&Py, b + 48, 8);
+}
+
 template <typename R>
 __device__ void write_residual(const SimParams &P, const Lane<R> &L)
 {
@@ -388,14 +430,19 @@ __device__ void write_residual(const SimParams &P, const Lane<R> &L)
     o.n_attempts = (uint16_t)min(L.attempts, 65535);
     o.flags = L.flags;
     o.reserved = L.pend;
-    o.Estar_cascade = L.Estar_c;
-    o.Estar_final = L.Estar;
-    o.P_cascade[0] = (float)L.Px;  // set by end_cascade; zero for events without a cascade
-    o.P_cascade[1] = (float)L.Py;
-    o.P_cascade[2] = (float)L.Pz;
-    o.P_final[0] = (float)L.Prx;
-    o.P_final[1] = (float)L.Pry;
-    o.P_final[2] = (float)L.Prz;
+    if (L.pend) {
+        write_pending_sums(o, L.Esum, L.Px, L.Py, L.Pz);
+        o.P_final[1] = o.P_final[2] = 0.f;
+    } else {
+        o.Estar_cascade = L.Estar_c;
+        o.Estar_final = L.Estar;
+        o.P_cascade[0] = out_f<R>(L.Px);  // set by settle_cascade; zero for events without a cascade
+        o.P_cascade[1] = out_f<R>(L.Py);
+        o.P_cascade[2] = out_f<R>(L.Pz);
+        o.P_final[0] = out_f<R>(L.Prx);
+        o.P_final[1] = out_f<R>(L.Pry);
+        o.P_final[2] = out_f<R>(L.Prz);
+    }
     const uint4 *src = reinterpret_cast<const uint4 *>(&o);
     uint4 *dst = reinterpret_cast<uint4 *>(P.res + L.ev);
 #pragma unroll
@@ -420,7 +467,7 @@ __device__ void begin_event(const SimParams &P, const TargetScalars *tabs, Lane<
     bool tgt_ok = L.tgt >= 0 && L.tgt < P.n_targets;
     L.Z = L.Zc = tgt_ok ? tabs[L.tgt].Z : 0;
     L.A = L.Ac = tgt_ok ? tabs[L.tgt].A : 0;
-    const R T0r = (R)L.T0;
+    const R T0r = to_R<R>(L.T0);
     if (!tgt_ok || !(T0r >= R(20) && T0r <= R(250))) {
         L.flags = PNUC_FLAG_BAD_INPUT;
         L.phase = kFinish;
@@ -440,7 +487,7 @@ __device__ void step_entry(const SimParams &P, const ShellTable<R> &t, double Ra
     }
     ++L.attempts;
     C.add(PNUC_C_ATTEMPTS);
-    R Rr = (R)Rad;
+    R Rr = to_R<R>(Rad);
     R b = Rr * sqrt(L.rng.next());
     R phi = R(kTwoPi) * L.rng.next();
     R sphi, cphi;
@@ -448,7 +495,7 @@ __device__ void step_entry(const SimParams &P, const ShellTable<R> &t, double Ra
     L.r[0] = b * cphi;
     L.r[1] = b * sphi;
     L.r[2] = -sqrt(Rr * Rr - b * b);
-    const R T0 = (R)L.T0;
+    const R T0 = to_R<R>(L.T0);
     L.p[0] = R(0);
     L.p[1] = R(0);
     L.p[2] = sqrt(T0 * T0 + R(2) * T0 * R(kMp));
@@ -461,24 +508,19 @@ __device__ void step_entry(const SimParams &P, const ShellTable<R> &t, double Ra
     L.phase = kTransport;
 }
 
-// The cascade of this attempt is over: retry if it was elastic (unless forced by the
-// step cap), else compute E* from the energy balance; the static mean field takes the
+// E* from the energy balance once the cascade is over: the static mean field takes the
 // momentum imbalance (kept in Px..Pz from here on) and the residual evaporates from rest.
+// Needs the cascade residual's Z, A in L.Z, L.A, the projectile energy in L.T0 and the
+// escape sums Esum, Px..Pz; Mt is the target's mass.
 template <typename R>
-__device__ void end_cascade(const SimParams &P, const TargetScalars &tab, Lane<R> &L, bool force)
+__device__ void settle_cascade(const SimParams &P, double Mt, Lane<R> &L)
 {
-    if (L.n_coll == 0 && !force) {
-        L.phase = kEntry;
-        return;
-    }
-    int Z = tab.Z + 1 - L.n_p_esc, A = tab.A + 1 - L.n_esc;
-    L.Z = L.Zc = Z;
-    L.A = L.Ac = A;
+    const int Z = L.Z, A = L.A;
     double p0 = sqrt(L.T0 * L.T0 + 2.0 * L.T0 * kMp);
     L.Px = -L.Px;
     L.Py = -L.Py;
     L.Pz = p0 - L.Pz;
-    double Er = L.T0 + kMp + tab.M - L.Esum;
+    double Er = L.T0 + kMp + Mt - L.Esum;
     L.Er = Er;
     L.Prx = L.Pry = L.Prz = 0.0;
     if (Z < 1 || A - Z < 1) {
@@ -495,17 +537,33 @@ __device__ void end_cascade(const SimParams &P, const TargetScalars &tab, Lane<R
         return;
     }
     L.Er = Mc + Estar;  // the excited residual at rest: its total energy is M + E*
+    L.phase = kEvap;
+}
+
+// The cascade of this attempt is over: retry if it was elastic (unless forced by the
+// step cap), else settle E*, here or (persistent method) in the evaporation kernel, whose
+// lanes do it together when they take the event.
+template <typename R>
+__device__ void end_cascade(const SimParams &P, const TargetScalars &tab, Lane<R> &L, bool force)
+{
+    if (L.n_coll == 0 && !force) {
+        L.phase = kEntry;
+        return;
+    }
+    L.Z = L.Zc = tab.Z + 1 - L.n_p_esc;
+    L.A = L.Ac = tab.A + 1 - L.n_esc;
     if (P.split_evap) {
-        // the evaporation kernel resumes this event from its residual record
+        // the residual record carries the raw escape sums and the draw position
         L.pend = L.rng.position() + 1u;
         L.phase = kFinish;
         return;
     }
-    L.phase = kEvap;
+    settle_cascade(P, tab.M, L);
 }
 
-// Resumes event ev's evaporation from the residual record the cascade kernel wrote (the
-// evaporation kernel of the persistent method). Leaves the lane idle if nothing is pending.
+// Resumes event ev from the residual record the cascade kernel wrote (the evaporation
+// kernel of the persistent method): settles E*, then evaporates. Leaves the lane idle if
+// nothing is pending.
 template <typename R>
 __device__ void begin_evap(const SimParams &P, Lane<R> &L, uint32_t ev)
 {
@@ -527,15 +585,18 @@ __device__ void begin_evap(const SimParams &P, Lane<R> &L, uint32_t ev)
     L.n_evap = 0;
     L.flags = o.flags;
     L.pend = 0;
-    L.Estar = L.Estar_c = o.Estar_cascade;
-    L.Er = __ldg(&P.mass[L.Z * kMassA + L.A]) + L.Estar;
-    L.Px = o.P_cascade[0];
-    L.Py = o.P_cascade[1];
-    L.Pz = o.P_cascade[2];
-    L.Prx = L.Pry = L.Prz = 0.0;
+    L.Estar = L.Estar_c = 0.0;
+    read_pending_sums(o, L.Esum, L.Px, L.Py, L.Pz);
+    L.T0 = __ldg(&P.energies[ev]);
+    const int tgt = __ldg(&P.target_ids[ev]);
     L.rng.reset(P.seed, P.first_event_id + ev);
     L.rng.seek(o.reserved - 1u);
-    L.phase = kEvap;
+    if (tgt < 0 || tgt >= P.n_targets) {  // cannot happen: the cascade checked it
+        L.flags |= PNUC_FLAG_BAD_INPUT;
+        L.phase = kFinish;
+        return;
+    }
+    settle_cascade(P, __ldg(&P.tables[tgt].M), L);
 }
 
 // Pops the next particle of the stack, or ends the attempt.
@@ -575,7 +636,7 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
     ++L.steps;
     C.add(PNUC_C_STEPS);
     const int s1 = L.s, i = L.shell;
-    const R m1 = (R)nucleon_mass(s1);
+    const R m1 = nucleon_mass_R<R>(s1);
     const R pp = dot3(L.p, L.p), pm = sqrt(pp);
     const R E1 = sqrt(pp + m1 * m1);
     R d[3] = {L.p[0] / pm, L.p[1] / pm, L.p[2] / pm};
@@ -590,7 +651,7 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
         for (int k = 0; k < 3; ++k) L.r[k] += s * d[k];
         C.add(PNUC_C_CANDIDATES);
         int s2 = (L.rng.next() < t.ZoverA) ? 1 : 0;
-        R m2 = (R)nucleon_mass(s2);
+        R m2 = nucleon_mass_R<R>(s2);
         R q = t.pF[s2][i] * cbrt(L.rng.next());
         R ct = R(2) * L.rng.next() - R(1);
         R sn = sqrt((R(1) - ct) * (R(1) + ct));
@@ -636,12 +697,13 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
     if (L.n_coll > 0) {
         C.add(PNUC_C_ESCAPES);
         R pn = sqrt(dot3(L.p, L.p));
-        emit_secondary(P, L.ev, s1, 0, L.n_index++, (double)Tout, (float)(L.p[0] / pn), (float)(L.p[1] / pn),
+        const double Toutd = to_d<R>(Tout);
+        emit_secondary(P, L.ev, s1, 0, L.n_index++, Toutd, (float)(L.p[0] / pn), (float)(L.p[1] / pn),
                        (float)(L.p[2] / pn), L.flags);
-        L.Esum += (double)Tout + nucleon_mass(s1);
-        L.Px += (double)L.p[0];
-        L.Py += (double)L.p[1];
-        L.Pz += (double)L.p[2];
+        L.Esum += Toutd + nucleon_mass(s1);
+        L.Px += to_d<R>(L.p[0]);
+        L.Py += to_d<R>(L.p[1]);
+        L.Pz += to_d<R>(L.p[2]);
         ++L.n_esc;
         if (s1 == 1) ++L.n_p_esc;
     }
@@ -671,15 +733,15 @@ __device__ void collide_mixed(int s1, const float *p1, int s2, const float *p2, 
                               float *q1, float *q2, double &T1n, double &T2n)
 {
     const double m1 = nucleon_mass(s1), m2 = nucleon_mass(s2);
-    const float m1f = (float)m1, m2f = (float)m2;
+    const float m1f = nucleon_mass_R<float>(s1), m2f = nucleon_mass_R<float>(s2);
     const bool like = s1 == s2;
     const float T1 = kinetic(dot3(p1, p1), m1f), T2 = kinetic(dot3(p2, p2), m2f);
     float Xf = T1 * T2 + T1 * m2f + T2 * m1f - dot3(p1, p2);  // four-product p1.p2 - m1 m2
     if (Xf < 0.f) Xf = 0.f;
     const float kf = sqrtf(Xf * (Xf + 2.f * m1f * m2f));        // sqrt(s) p* = m2 p_lab
-    const double P1[3] = {p1[0], p1[1], p1[2]};
-    const double P[3] = {P1[0] + (double)p2[0], P1[1] + (double)p2[1], P1[2] + (double)p2[2]};
-    const double E1 = m1 + (double)T1, Et = E1 + (m2 + (double)T2);
+    const double P1[3] = {f2d(p1[0]), f2d(p1[1]), f2d(p1[2])};
+    const double P[3] = {P1[0] + f2d(p2[0]), P1[1] + f2d(p2[1]), P1[2] + f2d(p2[2])};
+    const double E1 = m1 + f2d(T1), Et = E1 + (m2 + f2d(T2));
     const double s = Et * Et - dot3(P, P);
     const double irs = rsqrt(s);
     const double iEt = 1.0 / Et;
@@ -687,14 +749,14 @@ __device__ void collide_mixed(int s1, const float *p1, int s2, const float *p2, 
     const double gamma = Et * irs;
     const double g2 = gamma * gamma / (gamma + 1.0);
     const double f = g2 * dot3(beta, P1) - gamma * E1;
-    float n[3] = {(float)(P1[0] + beta[0] * f), (float)(P1[1] + beta[1] * f), (float)(P1[2] + beta[2] * f)};
+    float n[3] = {d2f(P1[0] + beta[0] * f), d2f(P1[1] + beta[1] * f), d2f(P1[2] + beta[2] * f)};
     const float rn = rsqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
     n[0] *= rn;
     n[1] *= rn;
     n[2] *= rn;
     const float plab = kf / m2f * 1e-3f;
-    const double pst = (double)kf * irs;
-    const float pg = (float)pst * 1e-3f;
+    const double pst = f2d(kf) * irs;
+    const float pg = d2f(pst) * 1e-3f;
     const float b = 4.f * slope_f(like, plab) * pg * pg;
     const float y = b > 0.f ? -log1pf(ut * expm1f(-b)) / b : ut;
     float ct = 1.f - 2.f * y;
@@ -717,15 +779,15 @@ __device__ void collide_mixed(int s1, const float *p1, int s2, const float *p2, 
         d[1] = st * sp;
         d[2] = (n[2] >= 0.f ? 1.f : -1.f) * ct;
     }
-    const double K[3] = {pst * d[0], pst * d[1], pst * d[2]};
+    const double K[3] = {pst * f2d(d[0]), pst * f2d(d[1]), pst * f2d(d[2])};
     const double hs = 0.5 * irs;
     const double e1 = (s + m1 * m1 - m2 * m2) * hs, e2 = (s + m2 * m2 - m1 * m1) * hs;  // CM energies
     const double bk = dot3(beta, K);
     const double f1 = g2 * bk + gamma * e1, f2 = -g2 * bk + gamma * e2;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        q1[c] = (float)(K[c] + beta[c] * f1);
-        q2[c] = (float)(-K[c] + beta[c] * f2);
+        q1[c] = d2f(K[c] + beta[c] * f1);
+        q2[c] = d2f(-K[c] + beta[c] * f2);
     }
     T1n = gamma * (e1 + bk) - m1;
     T2n = gamma * (e2 - bk) - m2;
@@ -761,14 +823,14 @@ __device__ void finish_collision(const SimParams &P, const ShellTable<R> &t, con
     double T1n, T2n;
     collide_lane<R>(s1, L.p, s2, L.jp, ut, uph, uf, q1, q2, T1n, T2n);
     L.phase = kTransport;
-    if (!(T1n > (double)t.EF[s1][i] && T2n > (double)t.EF[s2][i])) {
+    if (!(T1n > to_d<R>(t.EF[s1][i]) && T2n > to_d<R>(t.EF[s2][i]))) {
         C.add(PNUC_C_PAULI_BLOCKED);
         return;
     }
     C.add(PNUC_C_COLLISIONS);
     ++L.n_coll;
-    double cut2 = (double)t.V[s2][i] + (s2 == 1 ? (double)t.EC : 0.0);
-    double cut1 = (double)t.V[s1][i] + (s1 == 1 ? (double)t.EC : 0.0);
+    double cut2 = to_d<R>(t.V[s2][i]) + (s2 == 1 ? to_d<R>(t.EC) : 0.0);
+    double cut1 = to_d<R>(t.V[s1][i]) + (s1 == 1 ? to_d<R>(t.EC) : 0.0);
     if (T2n < cut2) {
         C.add(PNUC_C_CAPTURES);
     } else if (L.sp >= kStackCap) {
@@ -835,7 +897,7 @@ __device__ void channel_params(const SimParams &P, int Z, int A, double Mparent,
     if (Zd < 1 || Ad - Zd < 1 || Ad < 5) return;
     const double Md = __ldg(&P.mass[Zd * kMassA + Ad]);
     const double Q = Md + cEjM[j] - Mparent;
-    const R A3 = (R)__ldg(&P.cbrtA[Ad]);
+    const R A3 = to_R<R>(__ldg(&P.cbrtA[Ad]));
     R V, b, cj;
     if (cEjZ[j] == 0) {
         R alpha = R(0.76) + R(1.93) / A3;
@@ -844,11 +906,11 @@ __device__ void channel_params(const SimParams &P, int Z, int A, double Mparent,
         b = beta > R(0) ? beta : R(0);
         cj = alpha;
     } else {
-        V = R(kE2) * cEjZ[j] * Zd / (R(1.5) * ((R)__ldg(&P.cbrtA[cEjA[j]]) + A3));
+        V = R(kE2) * cEjZ[j] * Zd / (R(1.5) * (to_R<R>(__ldg(&P.cbrtA[cEjA[j]])) + A3));
         b = R(0);
         cj = R(1);
     }
-    const R X = (R)(Estar - Q);
+    const R X = to_R<R>(Estar - Q);
     const R Y = X - V;
     c.Q = Q;
     c.Md = Md;
@@ -857,7 +919,7 @@ __device__ void channel_params(const SimParams &P, int Z, int A, double Mparent,
     c.a = R(Ad) / R(8);
     if (!(Y > R(0))) return;
     c.x = R(2) * sqrt(c.a * Y);
-    c.w0 = (R)cEjG[j] * (R)cEjM[j] * cj * (A3 * A3);
+    c.w0 = ej_G<R>(j) * ej_M<R>(j) * cj * (A3 * A3);
     c.open = true;
 }
 
@@ -867,9 +929,9 @@ template <typename R>
 __device__ void width_FG_R(R x, double &F, double &G)
 {
     if (x >= R(1)) {
-        double ex = exp((double)x);
-        F = ex * (double)(x * x - R(3) * x + R(3)) + (double)(R(0.5) * x * x) - 3.0;
-        G = ex * (double)(x - R(1)) + 1.0;
+        double ex = exp(to_d<R>(x));
+        F = ex * to_d<R>(x * x - R(3) * x + R(3)) + to_d<R>(R(0.5) * x * x) - 3.0;
+        G = ex * to_d<R>(x - R(1)) + 1.0;
         return;
     }
     R term = x, f = R(0), g = R(0);  // term = x^n / n!
@@ -879,8 +941,8 @@ __device__ void width_FG_R(R x, double &F, double &G)
         g += R(n - 1) * term;
         if (n >= 4) f += R((n - 1) * (n - 3)) * term;
     }
-    F = (double)f;
-    G = (double)g;
+    F = to_d<R>(f);
+    G = to_d<R>(g);
 }
 
 template <typename R>
@@ -902,7 +964,7 @@ __device__ double channel_width<float>(const ChanP<float> &c)
     double F, G;
     width_FG_R<float>(c.x, F, G);
     const float ia = 1.f / c.a;
-    return (double)c.w0 * (F * (double)(0.25f * ia * ia) + G * (double)(0.5f * c.b * ia));
+    return f2d(c.w0) * (F * f2d(0.25f * ia * ia) + G * f2d(0.5f * c.b * ia));
 }
 
 // Two-body decay of the parent (invariant mass W) into an ejectile of mass m1 and a
@@ -943,15 +1005,15 @@ template <>
 __device__ void decay_to_lab<float>(double W, double m1, double m2, double eps, float ct, float ph,
                                     const Lane<float> &L, double *pl, double &el, double &Tl, float *u)
 {
-    const float ef = (float)eps, m1f = (float)m1, m2f = (float)m2, Wf = (float)W;
+    const float ef = d2f(eps), m1f = d2f(m1), m2f = d2f(m2), Wf = d2f(W);
     const float pd2 = ef * (2.f * (m1f + m2f) + ef) * (2.f * m2f + ef) * (2.f * m1f + ef) / (4.f * Wf * Wf);
     const float pd = sqrtf(pd2);
     const float tcm = pd2 / (sqrtf(pd2 + m1f * m1f) + m1f);  // rest-frame kinetic energy
     const float sn = sqrtf((1.f - ct) * (1.f + ct));
     float sph, cph;
     __sincosf(ph, &sph, &cph);
-    const double pv[3] = {(double)(pd * sn * cph), (double)(pd * sn * sph), (double)(pd * ct)};
-    const double e1 = m1 + (double)tcm;
+    const double pv[3] = {f2d(pd * sn * cph), f2d(pd * sn * sph), f2d(pd * ct)};
+    const double e1 = m1 + f2d(tcm);
     const double Pr[3] = {L.Prx, L.Pry, L.Prz};
     const double Er = L.Er;
     const double M2 = Er * Er - dot3(Pr, Pr);
@@ -964,40 +1026,31 @@ __device__ void decay_to_lab<float>(double W, double m1, double m2, double eps, 
     for (int k = 0; k < 3; ++k) pl[k] = pv[k] + beta[k] * f;
     el = gamma * (e1 + bp);
     Tl = el - m1;
-    const float plf[3] = {(float)pl[0], (float)pl[1], (float)pl[2]};
+    const float plf[3] = {d2f(pl[0]), d2f(pl[1]), d2f(pl[2])};
     const float r = rsqrtf(plf[0] * plf[0] + plf[1] * plf[1] + plf[2] * plf[2]);
     u[0] = plf[0] * r;
     u[1] = plf[1] * r;
     u[2] = plf[2] * r;
 }
 
-// One evaporation step (§2.4): widths of the six channels, the channel draw, the emission
-// energy, and the two-body decay isotropic in the parent's rest frame, boosted to the lab.
+// The second half of an evaporation step (§2.4), given the six channel widths G of the
+// parent (Z, A, E* in L): the channel draw, the emission energy, and the two-body decay
+// isotropic in the parent's rest frame, boosted to the lab.
 template <typename R, bool kCount>
-__device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
+__device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const ChanP<R> *chans, const double *G,
+                          Counters<kCount> &C)
 {
-    if (L.n_evap >= P.max_evap_steps) {
-        L.flags |= PNUC_FLAG_EVAP_STEP_CAP;
-        L.phase = kFinish;
-        return;
-    }
     const int Z = L.Z, A = L.A;
-    const double Mparent = __ldg(&P.mass[Z * kMassA + A]);
     const double Estar = L.Estar;
-    double G[6], S = 0.0;
-    ChanP<R> chans[6];  // kept for the chosen channel
-#pragma unroll 1
-    for (int j = 0; j < 6; ++j) {
-        channel_params<R>(P, Z, A, Mparent, Estar, j, chans[j]);
-        G[j] = channel_width<R>(chans[j]);
-        S += G[j];
-    }
+    double S = 0.0;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) S += G[j];
     if (!(S > 0.0)) {
         L.phase = kFinish;
         return;
     }
     C.add(PNUC_C_EVAP_STEPS);
-    double us = (double)L.rng.next() * S, cum = 0.0;
+    double us = to_d<R>(L.rng.next()) * S, cum = 0.0;
     int ch = -1;
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) {
@@ -1019,8 +1072,8 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
         L.phase = kFinish;
         return;
     }
-    const double xt = (double)c.x - (double)tt;
-    const double Ud = xt * xt / (4.0 * (double)c.a);
+    const double xt = to_d<R>(c.x) - to_d<R>(tt);
+    const double Ud = xt * xt / (4.0 * to_d<R>(c.a));
     const double eps = (Estar - c.Q) - Ud;
     const R ctr = R(2) * L.rng.next() - R(1);
     const R phr = R(kTwoPi) * L.rng.next();
@@ -1036,6 +1089,95 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     L.Z = Z - cEjZ[ch];
     L.A = A - cEjA[ch];
     L.Estar = Ud;
+}
+
+// One evaporation step of one lane (the plain kernel): widths of the six channels, then
+// evap_emit().
+template <typename R, bool kCount>
+__device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
+{
+    if (L.n_evap >= P.max_evap_steps) {
+        L.flags |= PNUC_FLAG_EVAP_STEP_CAP;
+        L.phase = kFinish;
+        return;
+    }
+    const double Mparent = __ldg(&P.mass[L.Z * kMassA + L.A]);
+    double G[6];
+    ChanP<R> chans[6];  // kept for the chosen channel
+#pragma unroll 1
+    for (int j = 0; j < 6; ++j) {
+        channel_params<R>(P, L.Z, L.A, Mparent, L.Estar, j, chans[j]);
+        G[j] = channel_width<R>(chans[j]);
+    }
+    evap_emit<R, kCount>(P, L, Mparent, chans, G, C);
+}
+
+// ------------------------------------------------------------------ warp-wide widths
+// One width evaluation: the parameters channel_width() reads.
+template <typename R>
+struct WidthJob {
+    R x, a, b, w0;
+};
+constexpr int kWidthSlots = 6 * 32;  // per warp: six channels of every lane
+
+template <typename R>
+__device__ __forceinline__ double job_width(const WidthJob<R> &jb)
+{
+    ChanP<R> c;
+    c.open = true;
+    c.x = jb.x;
+    c.a = jb.a;
+    c.b = jb.b;
+    c.w0 = jb.w0;
+    return channel_width<R>(c);
+}
+
+// One evaporation step of every lane of the warp with `active` set (the evaporation kernel).
+// The widths are evaluated by the whole warp: the (lane, channel) pairs of open channels
+// go to a job list in shared memory, those that need the FP64 exponential (x >= 1) from the
+// front and the series ones (x < 1) from the back, and the 32 lanes work through it. One
+// pass then serves up to 32 exponentials, where the per-lane loop issues one pass per channel
+// for whichever lanes have it open; each width is channel_width()'s arithmetic, bit for bit.
+// Called by all 32 lanes of the warp; jobs and wout are the warp's kWidthSlots entries.
+template <typename R, bool kCount>
+__device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, WidthJob<R> *jobs, double *wout,
+                               Counters<kCount> &C)
+{
+    if (active && L.n_evap >= P.max_evap_steps) {
+        L.flags |= PNUC_FLAG_EVAP_STEP_CAP;
+        L.phase = kFinish;
+        active = false;
+    }
+    const unsigned FULL = 0xffffffffu, lane = threadIdx.x & 31, below = (1u << lane) - 1u;
+    const double Mparent = active ? __ldg(&P.mass[L.Z * kMassA + L.A]) : 0.0;
+    ChanP<R> chans[6];
+    int slot[6];
+    int nexp = 0, nser = 0;
+#pragma unroll 1
+    for (int j = 0; j < 6; ++j) {
+        if (active) {
+            channel_params<R>(P, L.Z, L.A, Mparent, L.Estar, j, chans[j]);
+        } else {
+            chans[j].open = false;
+            chans[j].x = R(0);
+        }
+        const bool ex = chans[j].open && chans[j].x >= R(1);
+        const bool se = chans[j].open && !(chans[j].x >= R(1));
+        const unsigned me = __ballot_sync(FULL, ex), ms = __ballot_sync(FULL, se);
+        slot[j] = ex ? nexp + __popc(me & below) : kWidthSlots - 1 - (nser + __popc(ms & below));
+        if (ex || se) jobs[slot[j]] = WidthJob<R>{chans[j].x, chans[j].a, chans[j].b, chans[j].w0};
+        nexp += __popc(me);
+        nser += __popc(ms);
+    }
+    __syncwarp();
+    for (int k = lane; k < nexp; k += 32) wout[k] = job_width<R>(jobs[k]);
+    for (int k = kWidthSlots - 1 - (int)lane; k >= kWidthSlots - nser; k -= 32) wout[k] = job_width<R>(jobs[k]);
+    __syncwarp();
+    double G[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) G[j] = chans[j].open ? wout[slot[j]] : 0.0;
+    __syncwarp();  // the list is reused by the next step
+    if (active) evap_emit<R, kCount>(P, L, Mparent, chans, G, C);
 }
 
 // Advances lane L by one step of its current phase (no batching: the plain kernel).

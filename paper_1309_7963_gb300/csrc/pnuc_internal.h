@@ -75,6 +75,8 @@ cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool
 // Resident blocks per SM of the persistent kernels at a block size.
 int occupancy_persistent_fp64(int block);
 int occupancy_persistent_fp32(int block, bool count);
+int occupancy_evap_fp64(int block);
+int occupancy_evap_fp32(int block, bool count);
 
 // Pipe microbenchmarks (microbench.cu): FP32 FMA, FP64 FMA, MUFU, INT32 MAD lane ops/s.
 cudaError_t measure_peaks(int sm_count, double out[4]);

@@ -44,6 +44,13 @@ __host__ __device__ constexpr size_t smem_bytes(int n_targets, int block)
     return (table_smem_bytes<R>(n_targets) + 15) / 16 * 16 + (size_t)kRing * sizeof(R) * block;
 }
 
+// the evaporation kernel adds each warp's width-job list after the rings
+template <typename R>
+__host__ __device__ constexpr size_t evap_smem_bytes(int n_targets, int block)
+{
+    return smem_bytes<R>(n_targets, block) + (size_t)(block / 32) * kWidthSlots * (sizeof(WidthJob<R>) + sizeof(double));
+}
+
 template <typename R>
 __device__ __forceinline__ R *ring_base(const SimParams &P, unsigned char *smem)
 {
@@ -227,6 +234,10 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
     L.rng.stride = blockDim.x;
     uint32_t d0 = 0;  // draw index at which the lane's evaporation resumed
     WarpQueue Q;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    WidthJob<R> *jobs0 = reinterpret_cast<WidthJob<R> *>(smem + smem_bytes<R>(P.n_targets, blockDim.x));
+    WidthJob<R> *jobs = jobs0 + warp * kWidthSlots;
+    double *wout = reinterpret_cast<double *>(jobs0 + nwarps * kWidthSlots) + warp * kWidthSlots;
     while (true) {
         const long long t_top = kCount ? clock64() : 0;
         if (L.phase == kFinish) {
@@ -242,7 +253,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
             if (L.phase == kIdle) {
                 if (ev < P.n) {
                     begin_evap<R>(P, L, (uint32_t)ev);
-                    if (L.phase == kEvap) d0 = L.rng.position();
+                    d0 = L.rng.position();
                 } else {
                     L.phase = kExhausted;
                 }
@@ -250,10 +261,9 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
         }
         if (__all_sync(FULL, L.phase == kExhausted)) break;
         const long long t1 = kCount ? clock64() : 0;
-        if (L.phase == kEvap) {
-            L.rng.ensure(8);
-            step_evap<R, kCount>(P, L, C);
-        }
+        const bool stepping = L.phase == kEvap;
+        if (stepping) L.rng.ensure(8);
+        step_evap_warp<R, kCount>(P, L, stepping, jobs, wout, C);
         if (kCount) {
             __syncwarp();
             if (lane == 0) {
@@ -288,7 +298,7 @@ template <typename R, bool kCount>
 cudaError_t launch_evap(const SimParams &p, int grid, int block, cudaStream_t s)
 {
     if (p.n == 0) return cudaSuccess;
-    size_t smem = smem_bytes<R>(p.n_targets, block);
+    size_t smem = evap_smem_bytes<R>(p.n_targets, block);
     cudaError_t e = allow_smem(evap_kernel<R, kCount>, smem);
     if (e != cudaSuccess) return e;
     evap_kernel<R, kCount><<<grid, block, smem, s>>>(p);
@@ -335,6 +345,12 @@ int occupancy_of(K kernel, size_t smem, int block)
     allow_smem(kernel, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem);
     return nb;
+}
+
+template <typename R, bool kCount>
+int occupancy_evap(int block)
+{
+    return occupancy_of(evap_kernel<R, kCount>, evap_smem_bytes<R>(kMaxTargets, block), block);
 }
 
 template <typename R, bool kCount>

@@ -116,6 +116,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_get_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
     L.pnuc_set_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
     L.pnuc_measure_peaks.argtypes = [vp, C.POINTER(pnuc_peaks)]
+    L.pnuc_kernel_timing.argtypes = [vp, C.c_int32]
+    L.pnuc_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(u64)]
     L.pnuc_autotune.argtypes = [vp, C.c_int, C.POINTER(pnuc_batch), C.POINTER(pnuc_output), C.c_int32,
                                 C.POINTER(pnuc_tuning), C.POINTER(C.c_double), vp]
     L.pnuc_save_tuning.argtypes = [vp, C.c_char_p]
@@ -244,6 +246,17 @@ class Context:
         p = pnuc_peaks()
         self._check(self.lib.pnuc_measure_peaks(self.handle, C.byref(p)))
         return dict(fp32_fma=p.fp32_fma, fp64_fma=p.fp64_fma, mufu=p.mufu, int32_mad=p.int32_mad)
+
+    def kernel_timing(self, enable: bool) -> None:
+        """Start (clearing the record) or stop recording per-kernel CUDA-event times."""
+        self._check(self.lib.pnuc_kernel_timing(self.handle, 1 if enable else 0))
+
+    def kernel_times(self) -> dict:
+        """Summed milliseconds of the cascade (or plain) kernel and of the evaporation kernel
+        over the recorded launches, and their number."""
+        c, v, n = C.c_double(), C.c_double(), C.c_uint64()
+        self._check(self.lib.pnuc_kernel_times(self.handle, C.byref(c), C.byref(v), C.byref(n)))
+        return dict(cascade_ms=c.value, evaporation_ms=v.value, launches=n.value)
 
     def _structs(self, energies, target_ids, seed, first_event_id, out):
         b = pnuc_batch(_ptr(energies), _ptr(target_ids), int(energies.shape[0]), seed, first_event_id)

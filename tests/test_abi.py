@@ -44,6 +44,8 @@ def test_host_side_status_strings_without_gpu():
     # argument checks happen before any CUDA call
     assert lib.pnuc_simulate(None, 0, 0, None, None, None) == 1
     assert lib.pnuc_create(None, None) == 1
+    assert lib.pnuc_kernel_timing(None, 1) == 1
+    assert lib.pnuc_kernel_times(None, None, None, None) == 1
 
 
 def test_binding_refuses_without_gpu():

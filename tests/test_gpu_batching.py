@@ -102,3 +102,27 @@ def test_autotune_and_cache_roundtrip(ctx, tmp_path):
         assert ctx.get_tuning("fp32") == best
     finally:
         ctx.set_tuning("fp32", **saved)
+
+
+def test_kernel_timing_records_each_launch(ctx):
+    import torch
+    w = inputs.oxygen_calcium(n_each=20_000)
+    e, t = device_inputs(ctx, w)
+    out = ctx.alloc(w.n)
+    ctx.kernel_timing(True)
+    for _ in range(3):
+        ctx.simulate(e, t, seed=1, precision="fp32", method="persistent", out=out)
+    kt = ctx.kernel_times()
+    assert kt["launches"] == 3 and kt["cascade_ms"] > 0 and kt["evaporation_ms"] > 0
+    # a graph launch is not recorded; the plain method records one kernel
+    g = ctx.graph(e, t, seed=1, out=out)
+    g.launch()
+    torch.cuda.synchronize()
+    g.close()
+    assert ctx.kernel_times()["launches"] == 3
+    ctx.kernel_timing(True)
+    ctx.simulate(e, t, seed=1, precision="fp32", method="plain", out=out)
+    ctx.kernel_timing(False)
+    ctx.simulate(e, t, seed=1, precision="fp32", method="plain", out=out)
+    kt = ctx.kernel_times()
+    assert kt["launches"] == 1 and kt["cascade_ms"] > 0 and kt["evaporation_ms"] == 0.0
