@@ -36,18 +36,26 @@ ENERGY = 200.0
 PAPER_EVENTS_PER_S = 2 * 2.6e6 / (6.61 + 9.77)
 WORKLOAD = "1e6 p-16O + 1e6 p-40Ca at 200 MeV, one batch of 2e6 events per step"
 
-# Algorithmic FP64 operations of the FP32-mode model per counted unit (see the design doc,
-# "Roofline"): adds, multiplies and FMAs count 1; a division or square root 8 and an
-# exponential 16 (the instruction counts of Newton-Raphson and Cody-Waite/Horner
-# implementations). The FP64 pipe is the binding ALU pipe of the event kernels. Units of the
-# cascade kernel and of the evaporation kernel are listed apart.
+# Algorithmic FP64 operations of the FP32-mode model per counted unit, from the operations
+# the model performs in FP64 there (Lorentz boosts, energy/momentum bookkeeping, evaporation
+# widths): add, multiply, FMA and compare count 1; a division, square root or reciprocal
+# square root 8 and an exponential 16 (Newton-Raphson and Cody-Waite/Horner instruction
+# counts). Conversions between float and double are not arithmetic (the kernels do them on
+# the integer pipes). The units are the kernels' own counters.
 CASCADE_FP64_OPS = {
-    "kinematics": 140,  # pair energies, CM boost in and out, product energies
-    "escapes": 5,       # energy/momentum bookkeeping of an escaping nucleon
+    # pair sums and energies 6, s 4, 1/sqrt(s) 8, 1/E_t 8, beta and gamma 4, gamma^2/(gamma+1)
+    # 10, CM direction 8, p* 1, K 3, CM energies 8, back boost 10, q1 and q2 6, T1 and T2 6;
+    # the Pauli and cutoff tests 6
+    "kinematics": 86,
+    "escapes": 5,  # energy and momentum sums of an escaping nucleon
 }
-CASCADE_FP64_OPS_PER_EVENT = 15  # excitation energy from the energy balance
 EVAP_FP64_OPS = {
-    "evap_steps": 480,  # six widths (FP64 exponentials, Q-values) + two-body decay + boost
+    "settled": 18,      # E* from the energy balance (p0 with its square root, the sums)
+    "evap_passes": 18,  # six Q-values and excitations X = E* - Q
+    "evap_exps": 22,    # one open channel with x >= 1: exponential 16, F and G 3, width 3
+    "evap_series": 3,   # one open channel with x < 1: the width from F and G
+    # the channel draw 20, the emission energy and E_d 13, the decay boost 46, bookkeeping 6
+    "evap_steps": 85,
 }
 KERNEL_FILES = ("pnuc_device.cuh", "pnuc_kernels.cuh", "kernel_fp32.cu", "pnuc_internal.h")
 
@@ -73,7 +81,7 @@ def traffic_per_event() -> dict:
 
 
 def fp64_ops_per_event(counters: dict, n_events: int) -> dict:
-    cas = sum(counters[k] * v for k, v in CASCADE_FP64_OPS.items()) / n_events + CASCADE_FP64_OPS_PER_EVENT
+    cas = sum(counters[k] * v for k, v in CASCADE_FP64_OPS.items()) / n_events
     eva = sum(counters[k] * v for k, v in EVAP_FP64_OPS.items()) / n_events
     return {"cascade": cas, "evaporation": eva}
 

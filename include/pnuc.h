@@ -96,6 +96,9 @@ enum {
     PNUC_C_STEPS = 0, PNUC_C_CANDIDATES, PNUC_C_KINEMATICS, PNUC_C_PAULI_BLOCKED, PNUC_C_COLLISIONS,
     PNUC_C_CROSSINGS, PNUC_C_REFLECTIONS, PNUC_C_ESCAPES, PNUC_C_CAPTURES, PNUC_C_ATTEMPTS,
     PNUC_C_EVAP_STEPS, PNUC_C_EVAP_TRIALS, PNUC_C_DRAWS,
+    /* E* settlements (events whose cascade ended), six-channel width evaluations, and the
+     * open channels among them evaluated with the exponential (x >= 1) or the series (x < 1) */
+    PNUC_C_SETTLED, PNUC_C_EVAP_PASSES, PNUC_C_EVAP_EXPS, PNUC_C_EVAP_SERIES,
     /* persistent method only: SM clock cycles its warps spent in each phase of the loop
      * (summed over warps), the counterpart of the paper's kernel time split (§4.2) */
     PNUC_C_CYCLES_TRANSPORT, PNUC_C_CYCLES_COLLISION, PNUC_C_CYCLES_EVAPORATION, PNUC_C_CYCLES_REFILL,

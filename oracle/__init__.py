@@ -41,7 +41,8 @@ RESIDUAL_DTYPE = np.dtype([
     ("Ef", "<f8"),
 ])
 COUNTER_NAMES = ("steps", "candidates", "kinematics", "pauli_blocked", "collisions", "crossings",
-                 "reflections", "escapes", "captures", "attempts", "evap_steps", "evap_trials", "draws")
+                 "reflections", "escapes", "captures", "attempts", "evap_steps", "evap_trials", "draws",
+                 "settled", "evap_passes", "evap_exps", "evap_series")
 COUNTERS_DTYPE = np.dtype([(n, "<u8") for n in COUNTER_NAMES])
 LIMITS_DTYPE = np.dtype([("max_steps", "<i4"), ("max_attempts", "<i4"), ("stack_cap", "<i4"),
                          ("max_evap_steps", "<i4"), ("max_evap_trials", "<i4")])

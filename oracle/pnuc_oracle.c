@@ -71,6 +71,9 @@ typedef struct {
 typedef struct {
     uint64_t steps, candidates, kinematics, pauli_blocked, collisions, crossings,
         reflections, escapes, captures, attempts, evap_steps, evap_trials, draws;
+    /* E* settlements; six-channel width evaluations; open channels among them with
+     * x = 2 sqrt(aY) >= 1 and < 1 (work counts, no effect on the results) */
+    uint64_t settled, evap_passes, evap_exps, evap_series;
 } orc_counters;
 
 typedef struct {
@@ -767,6 +770,7 @@ static void run_event(const orc_target *t, double T0, uint32_t ev, orc_stream *s
      * but does no work, so E* is the energy balance in the target rest frame and the
      * residual starts the evaporation at rest. */
     int Z = t->Z + 1 - n_p_esc, A = t->A + 1 - n_esc;
+    c->settled++;
     res->Zc = res->Zf = Z;
     res->Ac = res->Af = A;
     double Er = T0 + M_P + t->M - Esum;
@@ -792,9 +796,14 @@ static void run_event(const orc_target *t, double T0, uint32_t ev, orc_stream *s
     int step;
     for (step = 0; step < L->max_evap_steps; step++) {
         double G[6], V[6], bj[6], Q[6], Md[6], a[6], x[6], S = 0.0;
+        c->evap_passes++;
         for (int j = 0; j < 6; j++) {
             G[j] = orc_channel(Z, A, Estar, j, &V[j], &bj[j], &Q[j], &Md[j], &a[j], &x[j]);
             S += G[j];
+            if (G[j] > 0.0) {
+                if (x[j] >= 1.0) c->evap_exps++;
+                else c->evap_series++;
+            }
         }
         if (!(S > 0.0)) break;
         c->evap_steps++;

@@ -71,7 +71,9 @@ template <> __device__ __forceinline__ double to_uniform<double>(uint64_t w)
 }
 template <> __device__ __forceinline__ float to_uniform<float>(uint64_t w)
 {
-    return ((float)(uint32_t)(w >> 41) + 0.5f) * 0x1p-23f;  // 23 bits + 1/2: exact, open interval
+    // (m + 1/2) 2^-23 for the top 23 bits m, built as (1 + m 2^-23) - (1 - 2^-24): both
+    // operands and the difference are exact floats, and no int->float conversion is needed
+    return __uint_as_float(0x3f800000u | (uint32_t)(w >> 41)) - 0x1.fffffep-1f;
 }
 
 // The event's draw stream: draw d is word d mod 4 of Philox((d div 4, event, 0, 0),
@@ -1101,6 +1103,7 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
         L.phase = kFinish;
         return;
     }
+    C.add(PNUC_C_EVAP_PASSES);
     const double Mparent = __ldg(&P.mass[L.Z * kMassA + L.A]);
     double G[6];
     ChanP<R> chans[6];  // kept for the chosen channel
@@ -1108,6 +1111,7 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     for (int j = 0; j < 6; ++j) {
         channel_params<R>(P, L.Z, L.A, Mparent, L.Estar, j, chans[j]);
         G[j] = channel_width<R>(chans[j]);
+        if (chans[j].open) C.add(chans[j].x >= R(1) ? PNUC_C_EVAP_EXPS : PNUC_C_EVAP_SERIES);
     }
     evap_emit<R, kCount>(P, L, Mparent, chans, G, C);
 }
@@ -1168,6 +1172,14 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
         if (ex || se) jobs[slot[j]] = WidthJob<R>{chans[j].x, chans[j].a, chans[j].b, chans[j].w0};
         nexp += __popc(me);
         nser += __popc(ms);
+    }
+    if (kCount) {
+        const unsigned act = __ballot_sync(FULL, active);
+        if (lane == 0) {
+            C.add(PNUC_C_EVAP_PASSES, __popc(act));
+            C.add(PNUC_C_EVAP_EXPS, nexp);
+            C.add(PNUC_C_EVAP_SERIES, nser);
+        }
     }
     __syncwarp();
     for (int k = lane; k < nexp; k += 32) wout[k] = job_width<R>(jobs[k]);

@@ -72,6 +72,8 @@ __device__ __forceinline__ void finish_event(const SimParams &P, Lane<R> &L, Cou
 {
     write_residual(P, L);
     C.add(PNUC_C_DRAWS, 4u * L.rng.block - (unsigned)L.rng.left);  // generated minus unused
+    // events whose E* was settled here (a pending one is settled by the evaporation kernel)
+    if (!L.pend && !(L.flags & (PNUC_FLAG_BAD_INPUT | PNUC_FLAG_ATTEMPT_CAP))) C.add(PNUC_C_SETTLED);
 }
 
 template <typename R, bool kCount>
@@ -183,8 +185,17 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
         const unsigned run = __ballot_sync(FULL, L.phase == kEntry || L.phase == kTransport);
         const unsigned kin = __ballot_sync(FULL, L.phase == kKinWait);
         const bool do_kin = kin && (__popc(kin) >= P.kin_batch || run == 0);
-        // the iteration's draws: at most 6 in a transport step, 3 in a collision, 2 at an entry
-        if ((L.phase == kKinWait && do_kin) || L.phase == kTransport || L.phase == kEntry) L.rng.ensure(8);
+        // the iteration's draws: at most 6 in a transport step, 3 in a collision, 2 at an entry.
+        // When a lane must generate, every other live lane with room for a block generates one
+        // too, so the warp runs the Philox code less often and with more lanes (the words are
+        // the same whenever they are made).
+        const bool draws = (L.phase == kKinWait && do_kin) || L.phase == kTransport || L.phase == kEntry;
+        if (__any_sync(FULL, draws && L.rng.left < 8)) {
+            const bool live = L.phase == kKinWait || L.phase == kTransport || L.phase == kEntry;
+            int k = draws ? 8 : 0;
+            if (live && L.rng.left < kRing - 3 && L.rng.left + 1 > k) k = L.rng.left + 1;
+            L.rng.ensure(k);
+        }
         if (!kCount) {
             if (L.phase == kKinWait) {
                 if (do_kin) finish_collision<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
@@ -254,6 +265,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
                 if (ev < P.n) {
                     begin_evap<R>(P, L, (uint32_t)ev);
                     d0 = L.rng.position();
+                    if (L.phase != kIdle) C.add(PNUC_C_SETTLED);
                 } else {
                     L.phase = kExhausted;
                 }

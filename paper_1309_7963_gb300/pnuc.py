@@ -26,8 +26,9 @@ RESIDUAL_DTYPE = np.dtype([("Z_cascade", "<u2"), ("A_cascade", "<u2"), ("Z_final
 assert SECONDARY_DTYPE.itemsize == 32 and RESIDUAL_DTYPE.itemsize == 64
 
 COUNTER_NAMES = ("steps", "candidates", "kinematics", "pauli_blocked", "collisions", "crossings", "reflections",
-                 "escapes", "captures", "attempts", "evap_steps", "evap_trials", "draws", "cycles_transport",
-                 "cycles_collision", "cycles_evaporation", "cycles_refill")
+                 "escapes", "captures", "attempts", "evap_steps", "evap_trials", "draws", "settled", "evap_passes",
+                 "evap_exps", "evap_series", "cycles_transport", "cycles_collision", "cycles_evaporation",
+                 "cycles_refill")
 FLAGS = dict(bad_input=1, attempt_cap=2, step_cap=4, stack_overflow=8, bad_residual=16, no_excitation=32,
              evap_trial_cap=64, evap_step_cap=128, output_overflow=256)
 PRECISION = {"fp32": 0, "fp64": 1}

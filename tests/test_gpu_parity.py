@@ -88,7 +88,8 @@ def test_gpu_counters_match_oracle_counters(ctx):
     r = run_gpu(ctx, w, "fp64", "persistent", counters=True)
     g = r.counters_dict()
     o = run_oracle(w)["counters"]
-    for k in ("steps", "candidates", "kinematics", "collisions", "attempts", "evap_steps", "draws"):
+    for k in ("steps", "candidates", "kinematics", "collisions", "attempts", "evap_steps", "draws", "settled",
+              "evap_passes", "evap_exps", "evap_series"):
         assert abs(g[k] - o[k]) <= 1e-3 * o[k] + 5, (k, g[k], o[k])
 
 
