@@ -165,7 +165,7 @@ def serving_bench(ctx, seconds: float = 1.5) -> dict:
 
     from paper_1309_7963_gb300 import driver, inputs, pnuc
     tids = np.array([ctx.create_target(*za) for za in inputs.SERVING_TARGETS], np.int32)
-    srv = pnuc.Server(ctx, precision="fp32", streams=4, arena_bytes=2 << 30)
+    srv = pnuc.Server(ctx, precision="fp32", streams=16, arena_bytes=2 << 30)
     try:
         burst = inputs.serving_requests(64, rate_hz=1e9, seed=101)
         rep = driver.run(srv, burst, tids, seed=7)
@@ -186,7 +186,7 @@ def serving_bench(ctx, seconds: float = 1.5) -> dict:
                          "reruns": st["reruns"]})
         return {"capacity_events_per_s": capacity, "mean_request_events": mean_events,
                 "config": "Poisson arrivals, 1e3-1e5 events log-uniform, 20-250 MeV, 12C/16O/40Ca/48Ti/56Fe, "
-                          "4 streams, 2 GiB arenas, FP32", "runs": runs}
+                          "16 streams, 2 GiB arenas, FP32", "runs": runs}
     finally:
         srv.close()
 

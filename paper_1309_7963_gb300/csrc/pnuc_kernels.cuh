@@ -161,6 +161,7 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
     const unsigned lane = threadIdx.x & 31;
     Lane<R> L;
     L.phase = kIdle;
+    L.rng.reset(0, 0);
     L.rng.buf = ring_base<R>(P, smem);
     L.rng.stride = blockDim.x;
     Particle<R> stack[kStackCap];
@@ -191,10 +192,12 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
         // the same whenever they are made).
         const bool draws = (L.phase == kKinWait && do_kin) || L.phase == kTransport || L.phase == kEntry;
         if (__any_sync(FULL, draws && L.rng.left < 8)) {
-            const bool live = L.phase == kKinWait || L.phase == kTransport || L.phase == kEntry;
-            int k = draws ? 8 : 0;
-            if (live && L.rng.left < kRing - 3 && L.rng.left + 1 > k) k = L.rng.left + 1;
-            L.rng.ensure(k);
+            // only lanes holding an event touch their stream
+            if (L.phase == kKinWait || L.phase == kTransport || L.phase == kEntry) {
+                int k = draws ? 8 : 0;
+                if (L.rng.left < kRing - 3 && L.rng.left + 1 > k) k = L.rng.left + 1;
+                L.rng.ensure(k);
+            }
         }
         if (!kCount) {
             if (L.phase == kKinWait) {
@@ -241,6 +244,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
     const unsigned lane = threadIdx.x & 31;
     Lane<R> L;
     L.phase = kIdle;
+    L.rng.reset(0, 0);
     L.rng.buf = ring_base<R>(P, smem);
     L.rng.stride = blockDim.x;
     uint32_t d0 = 0;  // draw index at which the lane's evaporation resumed

@@ -291,7 +291,7 @@ void pnuc_server_default_config(pnuc_server_config *cfg)
 {
     if (!cfg) return;
     cfg->precision = PNUC_FP32;
-    cfg->streams = 4;
+    cfg->streams = 8;
     cfg->arena_bytes = 1ull << 30;
     cfg->sec_per_event = 12;
     cfg->max_pending = 4096;

@@ -126,3 +126,21 @@ def test_kernel_timing_records_each_launch(ctx):
     ctx.simulate(e, t, seed=1, precision="fp32", method="plain", out=out)
     kt = ctx.kernel_times()
     assert kt["launches"] == 1 and kt["cascade_ms"] > 0 and kt["evaporation_ms"] == 0.0
+
+
+def test_small_batches_leave_idle_lanes_quiet(ctx):
+    """A batch much smaller than the resident grid leaves most lanes without an event; those
+    lanes must not touch their (unset) draw streams, and every launch ends promptly."""
+    import time
+
+    import torch
+    w = inputs.oxygen_calcium(n_each=3)
+    e, t = device_inputs(ctx, w)
+    out = ctx.alloc(w.n)
+    ref = results(ctx.simulate(e, t, seed=9, precision="fp32", method="plain"))
+    t0 = time.perf_counter()
+    for _ in range(50):
+        ctx.simulate(e, t, seed=9, precision="fp32", method="persistent", out=out)
+    torch.cuda.synchronize()
+    assert time.perf_counter() - t0 < 5.0
+    assert same(results(out), ref)
