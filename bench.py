@@ -68,16 +68,21 @@ def kernel_sha1() -> str:
     return h.hexdigest()
 
 
-def traffic_per_event() -> dict:
-    """DRAM bytes per event of the FP32 cascade and evaporation kernels from their last ncu
-    capture (profiles/persistent_kernels_traffic.txt); empty if the kernel sources changed since."""
+def profile_values() -> dict:
+    """The last ncu captures of the FP32 cascade and evaporation kernels
+    (profiles/persistent_kernels_traffic.txt): per kernel, DRAM bytes per event, issue-slot use,
+    active threads per instruction and FP64-pipe use; empty if the kernel sources changed since."""
     path = os.path.join(ROOT, "profiles", "persistent_kernels_traffic.txt")
     if not os.path.exists(path):
         return {}
     kv = dict(line.strip().split(": ", 1) for line in open(path) if ": " in line and not line.startswith("#"))
     if kv.get("kernel_sha1", "") != kernel_sha1():
         return {}
-    return {k: float(kv[k + "_bytes_per_event"]) for k in ("cascade", "evaporation") if k + "_bytes_per_event" in kv}
+    out = {}
+    for k in ("cascade", "evaporation"):
+        out[k] = {f: float(kv[f"{k}_{f}"]) for f in ("bytes_per_event", "issue_active_pct", "threads_per_inst",
+                                                     "fp64_pipe_pct") if f"{k}_{f}" in kv}
+    return out
 
 
 def fp64_ops_per_event(counters: dict, n_events: int) -> dict:
@@ -325,18 +330,21 @@ def main():
     ops_ev = fp64_ops_per_event(counters, n)
     peaks = ctx.measure_peaks()
     kernels = {}
-    traffic = traffic_per_event()
+    prof = profile_values()
     for name, ms_key in (("cascade", "cascade_ms"), ("evaporation", "evaporation_ms")):
         ms = ktimes[ms_key] / max(1, ktimes["launches"])
         achieved = ops_ev[name] * n / (ms * 1e-3)
+        pk = prof.get(name, {})
         kernels[name] = {"ms_per_launch": ms, "fp64_ops_per_event": ops_ev[name], "achieved": achieved / 1e9,
                          "frac": achieved / peaks["fp64_fma"],
-                         "traffic": traffic[name] * n if name in traffic else None}
+                         "traffic": pk["bytes_per_event"] * n if "bytes_per_event" in pk else None,
+                         "ncu": {k: v for k, v in pk.items() if k != "bytes_per_event"} or None}
     top = max(kernels, key=lambda k: kernels[k]["ms_per_launch"])
     kt = kernels[top]
     roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"{top} kernel (FP32 mode)", "achieved": kt["achieved"],
                 "peak": peaks["fp64_fma"] / 1e9, "unit": "FP64 Gop/s", "frac": kt["frac"], "traffic": kt["traffic"],
-                "traffic_note": "DRAM bytes per launch, scaled by events from an ncu capture of 8e5 events",
+                "traffic_note": "DRAM bytes per launch, scaled by events from an ncu capture of 8e5 events; "
+                                "ncu: issue-slot use and active threads per instruction of the same capture",
                 "peak_source": "pnuc_measure_peaks, FP64 FMA lane-ops/s measured in this run",
                 "timed_launches": ktimes["launches"], "kernels": kernels, "peaks_lane_ops_per_s": peaks,
                 "work_per_event": {k: v / n for k, v in counters.items() if not k.startswith("cycles")}}
@@ -345,7 +353,11 @@ def main():
     serving = None if (args.no_serving or world > 1) else serving_bench(ctx)
     if rank != 0:
         return
-    cb = None if args.no_cpu else cpu_baseline(500_000)
+    cb = None
+    if not args.no_cpu:
+        cb = cpu_baseline(500_000)
+        one = cpu_baseline(50_000, threads=1)
+        cb["one_core"] = {"value": one["value"], "unit": UNIT, "cores": 1, "sample": one["sample"]}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
