@@ -148,14 +148,21 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
         e = precision == PNUC_FP64 ? launch_persistent_fp64(p, (int)grid, t.block_size, s)
                                    : launch_persistent_fp32(p, (int)grid, t.block_size, count, s);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
-        // the evaporation kernel's own resident grid (it uses more registers)
-        int occ_e = precision == PNUC_FP64 ? occupancy_evap_fp64(t.block_size)
-                                           : occupancy_evap_fp32(t.block_size, count);
-        unsigned long long egrid = (unsigned long long)std::max(std::min(t.blocks_per_sm, occ_e), 1) * ctx->sm_count;
-        if (egrid > grid) egrid = grid;
+        // the evaporation kernel's own resident grid (it uses more registers, and its
+        // shared-memory job lists can make the block size too large: then it halves)
+        auto occ_evap = [&](int b) {
+            return precision == PNUC_FP64 ? occupancy_evap_fp64(b) : occupancy_evap_fp32(b, count);
+        };
+        int eblock = t.block_size, occ_e = occ_evap(eblock);
+        while (occ_e < 1 && eblock > 64) occ_e = occ_evap(eblock /= 2);
+        const long long want = (long long)t.blocks_per_sm * t.block_size / eblock;
+        unsigned long long egrid = (unsigned long long)std::max<long long>(std::min<long long>(want, occ_e), 1) *
+                                   ctx->sm_count;
+        const unsigned long long eneed = (batch->n + eblock - 1) / eblock;
+        if (egrid > eneed) egrid = eneed;
         if (e == cudaSuccess)
-            e = precision == PNUC_FP64 ? launch_evap_fp64(p, (int)egrid, t.block_size, s)
-                                       : launch_evap_fp32(p, (int)egrid, t.block_size, count, s);
+            e = precision == PNUC_FP64 ? launch_evap_fp64(p, (int)egrid, eblock, s)
+                                       : launch_evap_fp32(p, (int)egrid, eblock, count, s);
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     if (e != cudaSuccess && ev) ctx->tev_used -= 3;  // the slot is the last one taken
@@ -236,7 +243,7 @@ pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
             pnuc_tuning &t = ctx->tuning[p];
             t.block_size = 128;
             t.chunk = 256;
-            t.kin_batch = 16;
+            t.kin_batch = 20;
             t.refill_threshold = 4;
             int occ = occupancy((pnuc_precision)p, t.block_size, false);
             t.blocks_per_sm = occ > 0 ? occ : 1;

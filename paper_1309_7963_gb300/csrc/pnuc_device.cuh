@@ -77,11 +77,11 @@ template <> __device__ __forceinline__ float to_uniform<float>(uint64_t w)
 }
 
 // The event's draw stream: draw d is word d mod 4 of Philox((d div 4, event, 0, 0),
-// (seed, 0)). Converted words wait in a 16-slot ring in shared memory (slot k of thread t
+// (seed, 0)). Converted words wait in a 32-slot ring in shared memory (slot k of thread t
 // at buf[k * stride], stride = block size: conflict-free). Words are generated only by
 // ensure(k), which the kernels call once per loop iteration (and the evaporation sampler
 // once per trial), so lanes generate together and the Philox code exists twice.
-constexpr int kRing = 16;
+constexpr int kRing = 32;
 
 template <typename R>
 struct Stream {
@@ -543,9 +543,10 @@ __device__ void settle_cascade(const SimParams &P, double Mt, Lane<R> &L)
 }
 
 // The cascade of this attempt is over: retry if it was elastic (unless forced by the
-// step cap), else settle E*, here or (persistent method) in the evaporation kernel, whose
-// lanes do it together when they take the event.
-template <typename R>
+// step cap), else settle E*, here or (kSplit: the persistent method) in the evaporation
+// kernel, whose lanes do it together when they take the event. kSplit is a compile-time
+// choice so that the cascade kernel keeps no evaporation state in registers.
+template <typename R, bool kSplit>
 __device__ void end_cascade(const SimParams &P, const TargetScalars &tab, Lane<R> &L, bool force)
 {
     if (L.n_coll == 0 && !force) {
@@ -554,7 +555,7 @@ __device__ void end_cascade(const SimParams &P, const TargetScalars &tab, Lane<R
     }
     L.Z = L.Zc = tab.Z + 1 - L.n_p_esc;
     L.A = L.Ac = tab.A + 1 - L.n_esc;
-    if (P.split_evap) {
+    if (kSplit) {
         // the residual record carries the raw escape sums and the draw position
         L.pend = L.rng.position() + 1u;
         L.phase = kFinish;
@@ -602,7 +603,7 @@ __device__ void begin_evap(const SimParams &P, Lane<R> &L, uint32_t ev)
 }
 
 // Pops the next particle of the stack, or ends the attempt.
-template <typename R>
+template <typename R, bool kSplit>
 __device__ __forceinline__ void next_particle(const SimParams &P, const TargetScalars &tab, Lane<R> &L, Particle<R> *stack)
 {
     if (L.sp > 0) {
@@ -616,14 +617,14 @@ __device__ __forceinline__ void next_particle(const SimParams &P, const TargetSc
         L.s = q.s;
         L.shell = q.shell;
     } else {
-        end_cascade(P, tab, L, false);
+        end_cascade<R, kSplit>(P, tab, L, false);
     }
 }
 
 // One transport step of the particle in flight (§2.3): a path from the majorant rate,
 // then a candidate collision or a boundary crossing. An accepted candidate leaves the
 // lane in kKinWait with its partner stored; finish_collision() completes it.
-template <typename R, bool kCount>
+template <typename R, bool kCount, bool kSplit>
 __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const TargetScalars &tab, Lane<R> &L,
                                Particle<R> *stack, Counters<kCount> &C)
 {
@@ -632,7 +633,7 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
         // its excitation energy with what has escaped so far
         L.flags |= PNUC_FLAG_STEP_CAP;
         L.sp = 0;
-        end_cascade(P, tab, L, true);
+        end_cascade<R, kSplit>(P, tab, L, true);
         return;
     }
     ++L.steps;
@@ -709,7 +710,7 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
         ++L.n_esc;
         if (s1 == 1) ++L.n_p_esc;
     }
-    next_particle(P, tab, L, stack);
+    next_particle<R, kSplit>(P, tab, L, stack);
 }
 
 // ------------------------------------------------------------------ FP32-mode collision
@@ -815,7 +816,7 @@ __device__ void collide_lane<float>(int s1, const float *p1, int s2, const float
 
 // Completes the lane's accepted candidate (§2.3): elastic kinematics, Pauli blocking,
 // then the cutoff of each product; the struck nucleon goes on the stack.
-template <typename R, bool kCount>
+template <typename R, bool kCount, bool kSplit>
 __device__ void finish_collision(const SimParams &P, const ShellTable<R> &t, const TargetScalars &tab, Lane<R> &L,
                                  Particle<R> *stack, Counters<kCount> &C)
 {
@@ -854,7 +855,7 @@ __device__ void finish_collision(const SimParams &P, const ShellTable<R> &t, con
     L.p[2] = q1[2];
     if (T1n < cut1) {
         C.add(PNUC_C_CAPTURES);
-        next_particle(P, tab, L, stack);
+        next_particle<R, kSplit>(P, tab, L, stack);
     }
 }
 
@@ -1198,9 +1199,9 @@ __device__ __forceinline__ void step(const SimParams &P, const ShellTable<R> *sh
                                      Particle<R> *stack, Counters<kCount> &C)
 {
     if (L.phase == kTransport) {
-        step_transport<R, kCount>(P, sh[L.tgt], tabs[L.tgt], L, stack, C);
+        step_transport<R, kCount, false>(P, sh[L.tgt], tabs[L.tgt], L, stack, C);
     } else if (L.phase == kKinWait) {
-        finish_collision<R, kCount>(P, sh[L.tgt], tabs[L.tgt], L, stack, C);
+        finish_collision<R, kCount, false>(P, sh[L.tgt], tabs[L.tgt], L, stack, C);
     } else if (L.phase == kEntry) {
         step_entry<R, kCount>(P, sh[L.tgt], tabs[L.tgt].R, L, C);
     } else if (L.phase == kEvap) {

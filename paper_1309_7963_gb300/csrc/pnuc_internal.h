@@ -59,7 +59,7 @@ struct SimParams {
     const double *cbrtA;           // [kMassA] A^(1/3)
     unsigned long long *queue_head;  // persistent method: next unclaimed event of the cascade kernel
     unsigned long long *evap_head;   // persistent method: next unclaimed event of the evaporation kernel
-    int32_t split_evap;              // 1: the cascade leaves evaporation pending for evap_kernel
+    int32_t split_evap;              // 1: persistent method (the cascade kernel leaves evaporation to evap_kernel)
     int32_t max_steps, max_attempts, max_evap_steps, max_evap_trials;
     int32_t refill_threshold, chunk;
     int32_t kin_batch;  // persistent kernel: accepted collisions a warp gathers before their kinematics

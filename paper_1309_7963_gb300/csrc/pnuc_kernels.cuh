@@ -201,9 +201,9 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
         }
         if (!kCount) {
             if (L.phase == kKinWait) {
-                if (do_kin) finish_collision<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+                if (do_kin) finish_collision<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
             } else if (L.phase == kTransport) {
-                step_transport<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+                step_transport<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
             } else if (L.phase == kEntry) {
                 step_entry<R, kCount>(P, sh[L.tgt], ts[L.tgt].R, L, C);
             }
@@ -211,10 +211,10 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
             // the counting variant times each phase block of the warp (one lane records)
             const int ph = L.phase;
             long long t0 = clock64();
-            if (ph == kKinWait && do_kin) finish_collision<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+            if (ph == kKinWait && do_kin) finish_collision<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
             __syncwarp();
             long long t1 = clock64();
-            if (ph == kTransport) step_transport<R, kCount>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+            if (ph == kTransport) step_transport<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
             else if (ph == kEntry) step_entry<R, kCount>(P, sh[L.tgt], ts[L.tgt].R, L, C);
             __syncwarp();
             long long t2 = clock64();

@@ -4,8 +4,8 @@ For each workload: the fraction of events whose integer outcomes are identical, 
 multiplicity of every species (cascade and evaporation) with the difference in units of its
 standard error, binned kinetic-energy spectra and angular distributions (two-sample chi-square
 p-values), and the mean E* after the cascade. Bounds asserted: identical integers on >= 90%
-of events, multiplicities within 3 sigma, chi-square p > 0.01. The table is written to
-gpurun_out/fp32_observables.json when the directory exists.
+of events, multiplicities within 3 sigma, chi-square p > 0.01. The table is written as JSON to
+the path in the environment variable PNUC_OBSERVABLES_OUT when it is set.
 """
 import json
 import os
@@ -81,8 +81,8 @@ def test_fp32_observables_against_fp64_oracle(ctx, name, make):
                                  "oracle": float(ores["Estar_c"][ok].mean())}
     row["mean_A_final"] = {"fp32": float(gres["A_final"].mean()), "oracle": float(ores["Af"].mean())}
     assert c["frac_same"] >= 0.90, c["frac_same"]
-    if os.path.isdir("gpurun_out"):
-        path = os.path.join("gpurun_out", "fp32_observables.json")
+    path = os.environ.get("PNUC_OBSERVABLES_OUT")
+    if path:
         data = json.load(open(path)) if os.path.exists(path) else {}
         data[name] = row
         json.dump(data, open(path, "w"), indent=1)
