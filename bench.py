@@ -259,9 +259,9 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
-    def timed(method, steps, warmup, per_kernel=False):
+    def timed(method, steps, warmup, per_kernel=False, precision="fp32"):
         for _ in range(warmup):
-            ctx.simulate(e_dev, t_dev, seed=w.seed, first_event_id=first, precision="fp32", method=method, out=out)
+            ctx.simulate(e_dev, t_dev, seed=w.seed, first_event_id=first, precision=precision, method=method, out=out)
         torch.cuda.synchronize()
         ctx.kernel_timing(per_kernel)  # CUDA events around each kernel, on the launching stream
         if dist:
@@ -274,7 +274,7 @@ def main():
         for k in range(steps):
             flush.fill_(float(k))  # L2 flush between steps
             ev[k][0].record(stream)
-            ctx.simulate(e_dev, t_dev, seed=w.seed, first_event_id=first, precision="fp32", method=method, out=out)
+            ctx.simulate(e_dev, t_dev, seed=w.seed, first_event_id=first, precision=precision, method=method, out=out)
             ev[k][1].record(stream)
         t_end.record(stream)
         torch.cuda.synchronize()
@@ -302,6 +302,14 @@ def main():
         p_total, p_kern = timed("plain", max(2, args.steps // 2), 1)
         plain = {"value": world * n * max(2, args.steps // 2) / (p_total * 1e-3), "unit": UNIT,
                  "ms_per_step": p_total / max(2, args.steps // 2)}
+
+    # the FP64 deterministic mode (per-event oracle parity) on the same batch: batched vs plain
+    fp64 = None
+    if not args.no_plain:
+        f_pers, _ = timed("persistent", 2, 1, precision="fp64")
+        f_plain, _ = timed("plain", 2, 1, precision="fp64")
+        fp64 = {"persistent": world * n * 2 / (f_pers * 1e-3), "plain": world * n * 2 / (f_plain * 1e-3),
+                "unit": UNIT, "batched_vs_plain": f_plain / f_pers}
 
     e2e = None
     if not args.no_e2e:
@@ -368,7 +376,7 @@ def main():
                    "parallelism": f"{world} rank(s), event-id ranges, no collective"},
         "launch_ms": launch_ms, "secondaries_per_step": n_sec,
         "flags_nonzero_fraction": float(np.mean(res["flags"] != 0)),
-        "plain": plain, "batched_vs_plain": (value / plain["value"]) if plain else None,
+        "plain": plain, "batched_vs_plain": (value / plain["value"]) if plain else None, "fp64_mode": fp64,
         "phase_split": phase_split,
         "p50_ms": serving["runs"][-1]["p50_ms"] if serving else None,
         "p99_ms": serving["runs"][-1]["p99_ms"] if serving else None,

@@ -243,7 +243,7 @@ pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
             pnuc_tuning &t = ctx->tuning[p];
             t.block_size = 128;
             t.chunk = 256;
-            t.kin_batch = 20;
+            t.kin_batch = 16;
             t.refill_threshold = 4;
             int occ = occupancy((pnuc_precision)p, t.block_size, false);
             t.blocks_per_sm = occ > 0 ? occ : 1;
