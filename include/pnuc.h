@@ -308,6 +308,15 @@ pnuc_status pnuc_server_wait(pnuc_server *server, uint64_t ticket, int32_t timeo
  * Finished requests hold pinned host memory until fetched. */
 pnuc_status pnuc_server_fetch(pnuc_server *server, uint64_t ticket, pnuc_secondary *secondaries, uint64_t capacity,
                               pnuc_residual *residuals);
+/* Zero-copy alternative to pnuc_server_fetch: points *secondaries (*n_secondaries records)
+ * and *residuals (n records) at a finished request's results where they landed, in the
+ * server's pinned host arena. They stay valid, and the arena space stays taken, until
+ * pnuc_server_release(ticket) or pnuc_server_destroy(). PNUC_ERR_STATE if the request is not
+ * finished; a failed request returns its error and is released. */
+pnuc_status pnuc_server_view(pnuc_server *server, uint64_t ticket, const pnuc_secondary **secondaries,
+                             uint64_t *n_secondaries, const pnuc_residual **residuals);
+/* Releases a finished request without copying (after pnuc_server_view). */
+pnuc_status pnuc_server_release(pnuc_server *server, uint64_t ticket);
 pnuc_status pnuc_server_get_stats(pnuc_server *server, pnuc_server_stats *out);
 pnuc_status pnuc_server_reset_stats(pnuc_server *server);
 /* Drops queued requests, waits for those in flight, frees everything. Safe on NULL. */

@@ -432,6 +432,42 @@ pnuc_status pnuc_server_fetch(pnuc_server *S, uint64_t ticket, pnuc_secondary *s
     return PNUC_OK;
 }
 
+pnuc_status pnuc_server_view(pnuc_server *S, uint64_t ticket, const pnuc_secondary **secondaries,
+                             uint64_t *n_secondaries, const pnuc_residual **residuals)
+{
+    if (!S || !secondaries || !n_secondaries || !residuals) return PNUC_ERR_ARG;
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return PNUC_ERR_ARG;
+    Request *r = it->second.get();
+    if (r->state == kFailed) {
+        pnuc_status st = r->status;
+        S->reqs.erase(it);
+        return st;
+    }
+    if (r->state != kDone) return PNUC_ERR_STATE;
+    Layout L(r->n, r->cap);
+    const unsigned char *h = S->host + r->host_off;
+    *residuals = reinterpret_cast<const pnuc_residual *>(h + L.r);
+    *secondaries = reinterpret_cast<const pnuc_secondary *>(h + L.s);
+    *n_secondaries = r->count;
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_server_release(pnuc_server *S, uint64_t ticket)
+{
+    if (!S) return PNUC_ERR_ARG;
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return PNUC_ERR_ARG;
+    Request *r = it->second.get();
+    if (r->state != kDone && r->state != kFailed) return PNUC_ERR_STATE;
+    if (r->has_host) S->host_arena->release(r->host_off, r->bytes);
+    S->reqs.erase(it);
+    S->cv.notify_all();
+    return PNUC_OK;
+}
+
 pnuc_status pnuc_server_get_stats(pnuc_server *S, pnuc_server_stats *out)
 {
     if (!S || !out) return PNUC_ERR_ARG;

@@ -1,7 +1,8 @@
 """Synthetic proton-transport driver for the serving loop (pnuc_server): it submits
 interaction requests at Poisson arrival times (inputs.serving_requests: 1e3-1e5 events,
-log-uniform; 20-250 MeV; 12C, 16O, 40Ca, 48Ti, 56Fe), and a consumer thread waits for and
-fetches each result, as a transport code would before it continues its histories."""
+log-uniform; 20-250 MeV; 12C, 16O, 40Ca, 48Ti, 56Fe), and a consumer thread waits for each
+result, reads it in place (zero-copy views of the server's pinned arena) and releases it, as
+a transport code would before it continues its histories."""
 from __future__ import annotations
 
 import threading
@@ -16,7 +17,8 @@ from .pnuc import PnucError, Server
 def run(server: Server, requests: list, target_ids: np.ndarray, seed: int, keep=None, time_limit_s: float = 120.0):
     """Plays `requests` against `server` in real time. target_ids maps the workload's target
     index to the context's target id. keep(request, secondaries, residuals) is called for
-    each result if given. Returns client-side latencies (ms) and throughput."""
+    each result if given, with views valid only during the call (copy what you keep).
+    Returns client-side latencies (ms, submit to release) and throughput."""
     done = {}
     order = []
     lock = threading.Condition()
@@ -32,11 +34,12 @@ def run(server: Server, requests: list, target_ids: np.ndarray, seed: int, keep=
                     return
                 tk, req, t_sub = order[k]
             k += 1
-            nsec = server.wait(tk, -1)
-            sec, res = server.fetch(tk, nsec)
-            done[tk] = (t_sub, time.perf_counter(), req["energies"].shape[0])
+            server.wait(tk, -1)
+            sec, res = server.view(tk)  # zero-copy: the results where they landed
             if keep is not None:
                 keep(req, sec, res)
+            server.release(tk)
+            done[tk] = (t_sub, time.perf_counter(), req["energies"].shape[0])
 
     finished = [False]
     th = threading.Thread(target=consumer, daemon=True)

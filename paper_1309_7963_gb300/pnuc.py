@@ -133,6 +133,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_server_submit.argtypes = [vp, vp, vp, u64, u64, u64, C.POINTER(u64)]
     L.pnuc_server_wait.argtypes = [vp, u64, C.c_int32, C.POINTER(u64)]
     L.pnuc_server_fetch.argtypes = [vp, u64, vp, u64, vp]
+    L.pnuc_server_view.argtypes = [vp, u64, C.POINTER(vp), C.POINTER(u64), C.POINTER(vp)]
+    L.pnuc_server_release.argtypes = [vp, u64]
     L.pnuc_server_get_stats.argtypes = [vp, C.POINTER(pnuc_server_stats)]
     L.pnuc_server_reset_stats.argtypes = [vp]
     L.pnuc_server_destroy.argtypes = [vp]
@@ -415,6 +417,24 @@ class Server:
         res = np.empty(self.n_events.pop(ticket), RESIDUAL_DTYPE)
         self.ctx._check(self.lib.pnuc_server_fetch(self.handle, ticket, sec.ctypes.data, len(sec), res.ctypes.data))
         return sec[:n_secondaries], res
+
+    def view(self, ticket: int):
+        """Zero-copy results of a finished request: (secondaries, residuals) as numpy arrays
+        over the server's pinned host arena, valid until release(ticket)."""
+        sp, rp, n = C.c_void_p(), C.c_void_p(), C.c_uint64()
+        self.ctx._check(self.lib.pnuc_server_view(self.handle, ticket, C.byref(sp), C.byref(n), C.byref(rp)))
+        n_res = self.n_events[ticket]
+
+        def arr(ptr, count, dtype):
+            if count == 0:
+                return np.empty(0, dtype)
+            buf = (C.c_ubyte * (count * dtype.itemsize)).from_address(ptr.value)
+            return np.frombuffer(buf, dtype=dtype, count=count)
+        return arr(sp, n.value, SECONDARY_DTYPE), arr(rp, n_res, RESIDUAL_DTYPE)
+
+    def release(self, ticket: int):
+        self.ctx._check(self.lib.pnuc_server_release(self.handle, ticket))
+        self.n_events.pop(ticket, None)
 
     def stats(self) -> dict:
         st = pnuc_server_stats()

@@ -106,3 +106,29 @@ def test_driver_reports_latency_and_throughput(ctx):
         assert st["completed"] == 60 and st["latency_p50_ms"] > 0
     finally:
         srv.close()
+
+
+def test_zero_copy_view_and_release(ctx):
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(5, rate_hz=1e6, seed=12, min_batch=2000, max_batch=8000)
+    srv = pnuc.Server(ctx, precision="fp32", streams=2, arena_bytes=64 << 20)
+    try:
+        tickets = [srv.submit(r["energies"], tids[r["tidx"]], 13, r["first_event_id"]) for r in reqs]
+        for tk, r in zip(tickets, reqs):
+            srv.wait(tk)
+            sec, res = srv.view(tk)
+            ref_sec, ref_res = alone(ctx, r, tids, 13)
+            assert np.array_equal(res, ref_res)
+            assert np.array_equal(pnuc.sort_secondaries(sec.copy()), ref_sec)
+            srv.release(tk)
+            with pytest.raises(pnuc.PnucError):  # released: the ticket is gone
+                srv.release(tk)
+        big = srv.submit(np.full(100_000, 200.0), np.full(100_000, tids[2], np.int32), 13)
+        with pytest.raises(pnuc.PnucError) as e:  # still running
+            srv.view(big)
+        assert e.value.status == 6
+        srv.wait(big)
+        srv.release(big)
+        assert srv.stats()["completed"] == len(reqs) + 1
+    finally:
+        srv.close()
