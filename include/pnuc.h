@@ -274,7 +274,7 @@ pnuc_status pnuc_graph_destroy(pnuc_graph *graph);
  * pnuc_simulate call. Latency is measured from submit to results ready on the host. */
 typedef struct {
     int32_t precision;           /* pnuc_precision */
-    int32_t streams;             /* requests in flight at once, 1..16 (default 8) */
+    int32_t streams;             /* requests in flight at once, 1..64 (default 8) */
     uint64_t arena_bytes;        /* device arena and pinned host arena, each (default 1 GiB, >= 1 MiB) */
     uint32_t sec_per_event;      /* secondaries reserved per event at admission, 1..256 (default 12) */
     uint32_t max_pending;        /* queued requests before submit refuses (default 4096) */

@@ -70,7 +70,7 @@ class Arena {
     std::map<size_t, size_t> free_;
 };
 
-enum State { kPending, kRunning, kCopying, kDone, kFailed };
+enum State { kPending, kRunning, kDone, kFailed };
 
 struct Request {
     uint64_t ticket, n, seed, first;
@@ -190,8 +190,15 @@ bool admit(pnuc_server *S, Request &r)
         st = PNUC_ERR_CUDA;
     if (st == PNUC_OK) st = launch_batch(S->ctx, (pnuc_precision)S->cfg.precision, PNUC_PERSISTENT, &b, &o, s,
                                          S->ctx->tuning[S->cfg.precision], nullptr);
-    if (st == PNUC_OK && (cudaMemcpyAsync(h + L.count, d + L.count, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                          cudaEventRecord(S->events[si], s) != cudaSuccess))
+    // the count, the residuals and the whole reservation of secondaries come back in the same
+    // stream order, so one completion event covers them (a count above the reservation
+    // sends the request round again)
+    if (st == PNUC_OK &&
+        (cudaMemcpyAsync(h + L.count, d + L.count, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(h + L.r, d + L.r, sizeof(pnuc_residual) * r.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         (r.cap && cudaMemcpyAsync(h + L.s, d + L.s, sizeof(pnuc_secondary) * r.cap, cudaMemcpyDeviceToHost, s) !=
+                       cudaSuccess) ||
+         cudaEventRecord(S->events[si], s) != cudaSuccess))
         st = PNUC_ERR_CUDA;
     if (st != PNUC_OK) {
         finish(S, r, kFailed, st);
@@ -210,36 +217,24 @@ void poll(pnuc_server *S, Request &r)
         return;
     }
     Layout L(r.n, r.cap);
-    unsigned char *d = S->dev + r.dev_off, *h = S->host + r.host_off;
-    if (r.state == kRunning) {
-        r.count = *(volatile unsigned long long *)(h + L.count);
-        if (r.count > r.cap) {
-            // overflow: release and run again with room for exactly the count
-            S->dev_arena->release(r.dev_off, r.bytes);
-            S->host_arena->release(r.host_off, r.bytes);
-            r.has_dev = r.has_host = false;
-            S->stream_owner[r.stream] = 0;
-            r.stream = -1;
-            if (Layout(r.n, r.count).total > S->cfg.arena_bytes) {
-                finish(S, r, kFailed, PNUC_ERR_CAPACITY);
-                return;
-            }
-            r.cap = r.count;
-            r.reruns++;
-            S->reruns++;
-            r.state = kPending;
-            S->pending.push_front(r.ticket);
+    const unsigned char *h = S->host + r.host_off;
+    r.count = *(volatile const unsigned long long *)(h + L.count);
+    if (r.count > r.cap) {
+        // overflow: release and run again with room for exactly the count
+        S->dev_arena->release(r.dev_off, r.bytes);
+        S->host_arena->release(r.host_off, r.bytes);
+        r.has_dev = r.has_host = false;
+        S->stream_owner[r.stream] = 0;
+        r.stream = -1;
+        if (Layout(r.n, r.count).total > S->cfg.arena_bytes) {
+            finish(S, r, kFailed, PNUC_ERR_CAPACITY);
             return;
         }
-        cudaStream_t s = S->streams[r.stream];
-        if (cudaMemcpyAsync(h + L.r, d + L.r, sizeof(pnuc_residual) * r.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-            (r.count && cudaMemcpyAsync(h + L.s, d + L.s, sizeof(pnuc_secondary) * r.count, cudaMemcpyDeviceToHost,
-                                        s) != cudaSuccess) ||
-            cudaEventRecord(S->events[r.stream], s) != cudaSuccess) {
-            finish(S, r, kFailed, PNUC_ERR_CUDA);
-            return;
-        }
-        r.state = kCopying;
+        r.cap = r.count;
+        r.reruns++;
+        S->reruns++;
+        r.state = kPending;
+        S->pending.push_front(r.ticket);
         return;
     }
     finish(S, r, kDone, PNUC_OK);  // results are in the pinned host arena until fetched
@@ -327,7 +322,7 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg_in, 
     pnuc_server_config cfg;
     pnuc_server_default_config(&cfg);
     if (cfg_in) cfg = *cfg_in;
-    if ((cfg.precision != PNUC_FP32 && cfg.precision != PNUC_FP64) || cfg.streams < 1 || cfg.streams > 16 ||
+    if ((cfg.precision != PNUC_FP32 && cfg.precision != PNUC_FP64) || cfg.streams < 1 || cfg.streams > 64 ||
         cfg.arena_bytes < (1u << 20) || cfg.sec_per_event < 1 || cfg.sec_per_event > 256 || cfg.max_pending < 1 ||
         cfg.max_request_events < 1)
         return fail(ctx, PNUC_ERR_ARG, "bad server configuration");
