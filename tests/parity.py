@@ -79,3 +79,75 @@ def gpu_subset(res, sec, ids):
     s = sec[keep].copy()
     s["event"] = [pos[int(e)] for e in s["event"]]
     return res[ids], s
+
+
+SPECIES = ("n", "p", "d", "t", "3He", "alpha")
+FIG2_ANGLES = (7.5, 30.0, 60.0, 150.0)  # degrees: the paper's double-differential spectra (Fig. 2)
+
+
+def chi2_p(a, b, edges):
+    """Two-sample chi-square p-value of two binned samples of equal size (bins with > 10
+    entries in the pair); 1.0 when fewer than two such bins."""
+    from scipy import stats
+    ha, _ = np.histogram(a, edges)
+    hb, _ = np.histogram(b, edges)
+    keep = (ha + hb) > 10
+    if keep.sum() < 2:
+        return 1.0
+    chi2 = (((ha[keep] - hb[keep]) ** 2) / (ha[keep] + hb[keep])).sum()
+    return float(stats.chi2.sf(chi2, keep.sum() - 1))
+
+
+def observable_table(gres, gsec, ores, osec, n):
+    """Per-observable comparison of GPU results (FP32 mode) with the oracle on the same n
+    events: mean multiplicity per species and origin (difference in standard errors),
+    kinetic-energy spectra (2 MeV bins) and cos(theta) spectra (0.05 bins), the spectra in 1
+    degree windows at the angles of the paper's Fig. 2, the residual (Z, A) distribution after
+    evaporation, and the mean E* after the cascade. Returns the table row."""
+    row = {"events": int(n), "multiplicity": {}, "spectra_p": {}, "angle_p": {}, "fig2_p": {}}
+    for origin, label in ((0, "cascade"), (1, "evaporated")):
+        for sp, sname in enumerate(SPECIES):
+            gm_sel = (gsec["species"] == sp) & (gsec["origin"] == origin)
+            om_sel = (osec["species"] == sp) & (osec["origin"] == origin)
+            om = np.bincount(osec["event"][om_sel], minlength=n)
+            if om.sum() < 50:
+                continue
+            gm = np.bincount(gsec["event"][gm_sel], minlength=n)
+            se = np.sqrt(om.var() / n + gm.var() / n)
+            z = (gm.mean() - om.mean()) / se if se > 0 else 0.0
+            key = f"{label} {sname}"
+            row["multiplicity"][key] = {"fp32": float(gm.mean()), "oracle": float(om.mean()), "z": float(z)}
+            row["spectra_p"][key] = chi2_p(gsec["T"][gm_sel], osec["T"][om_sel], np.linspace(0, 250, 126))
+            row["angle_p"][key] = chi2_p(gsec["uz"][gm_sel], osec["uz"][om_sel], np.linspace(-1, 1, 41))
+            if origin == 0 or sp > 1:
+                continue
+            for ang in FIG2_ANGLES:  # evaporated n and p in 1-degree windows
+                lo, hi = np.cos(np.radians(ang + 0.5)), np.cos(np.radians(ang - 0.5))
+                gw = gm_sel & (gsec["uz"] >= lo) & (gsec["uz"] < hi)
+                ow = om_sel & (osec["uz"] >= lo) & (osec["uz"] < hi)
+                row["fig2_p"][f"{key} {ang:g} deg"] = chi2_p(gsec["T"][gw], osec["T"][ow], np.linspace(0, 60, 31))
+    # residual (Z, A) after evaporation: two-sample chi-square over the occupied cells
+    from scipy import stats
+    gk = gres["Z_final"].astype(np.int64) * 1000 + gres["A_final"].astype(np.int64)
+    ok = ores["Zf"].astype(np.int64) * 1000 + ores["Af"].astype(np.int64)
+    cells, inv = np.unique(np.concatenate([gk, ok]), return_inverse=True)
+    hg = np.bincount(inv[:n], minlength=len(cells))
+    ho = np.bincount(inv[n:], minlength=len(cells))
+    keep = (hg + ho) > 10
+    chi2 = (((hg[keep] - ho[keep]) ** 2) / (hg[keep] + ho[keep])).sum()
+    row["residual_ZA_p"] = float(stats.chi2.sf(chi2, max(keep.sum() - 1, 1))) if keep.sum() > 1 else 1.0
+    row["residual_ZA_identical"] = float(np.mean(gk == ok))
+    good = (ores["flags"] & 48) == 0
+    row["mean_Estar_cascade"] = {"fp32": float(gres["Estar_cascade"][good].mean()),
+                                 "oracle": float(ores["Estar_c"][good].mean())}
+    return row
+
+
+def assert_observables(row, name):
+    """The bounds: multiplicities within 3 standard errors, chi-square p > 0.01."""
+    for k, v in row["multiplicity"].items():
+        assert abs(v["z"]) < 3.0, (name, k, v)
+    for field in ("spectra_p", "angle_p", "fig2_p"):
+        for k, p in row[field].items():
+            assert p > 0.01, (name, field, k, p)
+    assert row["residual_ZA_p"] > 0.01, (name, row["residual_ZA_p"])

@@ -2,26 +2,26 @@
 
 For each workload: the fraction of events whose integer outcomes are identical, the mean
 multiplicity of every species (cascade and evaporation) with the difference in units of its
-standard error, binned kinetic-energy spectra and angular distributions (two-sample chi-square
-p-values), and the mean E* after the cascade. Bounds asserted: identical integers on >= 90%
-of events, multiplicities within 3 sigma, chi-square p > 0.01. The table is written as JSON to
-the path in the environment variable PNUC_OBSERVABLES_OUT when it is set.
+standard error, binned kinetic-energy spectra and angular distributions, the evaporated n and
+p spectra in 1-degree windows at the angles of the paper's Fig. 2, the residual (Z, A)
+distribution (two-sample chi-square p-values), and the mean E* after the cascade. Bounds
+asserted: identical integers on >= 90% of events, multiplicities within 3 sigma, chi-square
+p > 0.01. The table is written as JSON to the path in the environment variable
+PNUC_OBSERVABLES_OUT when it is set.
 """
 import json
 import os
 
 import numpy as np
 import pytest
-from scipy import stats
 
 import oracle
-from paper_1309_7963_gb300 import inputs, pnuc
+from paper_1309_7963_gb300 import inputs
 
-from .parity import compare
+from .parity import assert_observables, compare, observable_table
 
 pytestmark = pytest.mark.gpu
 
-SPECIES = ("n", "p", "d", "t", "3He", "alpha")
 WORKLOADS = [
     ("p-16O + p-40Ca 200 MeV", lambda: inputs.oxygen_calcium(n_each=25_000)),
     ("mixed tissue targets 20-250 MeV", lambda: inputs.mixed(40_000, seed=2)),
@@ -29,16 +29,6 @@ WORKLOADS = [
     ("p-56Fe 100-250 MeV", lambda: inputs.heavy(inputs.FE56, 10_000, seed=4)),
     ("p-208Pb 100-250 MeV", lambda: inputs.heavy(inputs.PB208, 6_000, seed=5)),
 ]
-
-
-def chi2_p(a, b, edges):
-    ha, _ = np.histogram(a, edges)
-    hb, _ = np.histogram(b, edges)
-    keep = (ha + hb) > 10
-    if keep.sum() < 2:
-        return 1.0
-    chi2 = (((ha[keep] - hb[keep]) ** 2) / (ha[keep] + hb[keep])).sum()
-    return float(stats.chi2.sf(chi2, keep.sum() - 1))
 
 
 @pytest.mark.parametrize("name,make", WORKLOADS, ids=[w[0] for w in WORKLOADS])
@@ -53,34 +43,15 @@ def test_fp32_observables_against_fp64_oracle(ctx, name, make):
     orc = oracle.simulate_parallel(w.targets, w.energies, w.tidx, seed=w.seed, first_event_id=w.first_event_id)
     ores, osec = orc["residuals"], orc["secondaries"]
     c = compare(gres, gsec, orc, w.n, rel_tol=1e-4)
-    row = {"workload": name, "events": w.n, "identical_integers": c["frac_same"],
-           "identical_within_1e-4": c["frac_match"], "multiplicity": {}, "spectra_p": {}, "angle_p": {}}
-    for origin, label in ((0, "cascade"), (1, "evaporated")):
-        for sp, sname in enumerate(SPECIES):
-            gm = np.bincount(gsec["event"][(gsec["species"] == sp) & (gsec["origin"] == origin)], minlength=w.n)
-            om = np.bincount(osec["event"][(osec["species"] == sp) & (osec["origin"] == origin)], minlength=w.n)
-            if om.sum() < 50:
-                continue
-            se = np.sqrt(om.var() / w.n + gm.var() / w.n)
-            z = (gm.mean() - om.mean()) / se if se > 0 else 0.0
-            row["multiplicity"][f"{label} {sname}"] = {"fp32": float(gm.mean()), "oracle": float(om.mean()),
-                                                       "z": float(z)}
-            assert abs(z) < 3.0, (name, label, sname, z)
-            gT = gsec["T"][(gsec["species"] == sp) & (gsec["origin"] == origin)]
-            oT = osec["T"][(osec["species"] == sp) & (osec["origin"] == origin)]
-            p = chi2_p(gT, oT, np.linspace(0, 250, 126))
-            row["spectra_p"][f"{label} {sname}"] = p
-            assert p > 0.01, (name, label, sname, p)
-            ga = gsec["uz"][(gsec["species"] == sp) & (gsec["origin"] == origin)]
-            oa = osec["uz"][(osec["species"] == sp) & (osec["origin"] == origin)]
-            pa = chi2_p(ga, oa, np.linspace(-1, 1, 41))
-            row["angle_p"][f"{label} {sname}"] = pa
-            assert pa > 0.01, (name, label, sname, pa)
-    ok = (ores["flags"] & 48) == 0
-    row["mean_Estar_cascade"] = {"fp32": float(gres["Estar_cascade"][ok].mean()),
-                                 "oracle": float(ores["Estar_c"][ok].mean())}
+    row = observable_table(gres, gsec, ores, osec, w.n)
+    row.update(workload=name, identical_integers=c["frac_same"], **{"identical_within_1e-4": c["frac_match"]})
     row["mean_A_final"] = {"fp32": float(gres["A_final"].mean()), "oracle": float(ores["Af"].mean())}
+    assert_observables(row, name)
     assert c["frac_same"] >= 0.90, c["frac_same"]
+    record(name, row)
+
+
+def record(name, row):
     path = os.environ.get("PNUC_OBSERVABLES_OUT")
     if path:
         data = json.load(open(path)) if os.path.exists(path) else {}

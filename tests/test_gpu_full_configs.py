@@ -1,14 +1,20 @@
-"""The remaining workloads at their full sizes, in the launch configurations they name:
-4e6 mixed-target events (one autotuned persistent launch replayed from a CUDA graph) and
-1e6 events on each heavy target. Checked on sampled events that the oracle computes one by
-one (FP32 mode against the FP64 oracle, integer outcomes per event) and, over every event,
-by properties that hold at any size: baryon number and charge conservation, flags."""
+"""The workloads at their full sizes, in the launch configurations they name: 2e6 p-16O +
+p-40Ca events with the plain FP32 kernel, 4e6 mixed-target events (one autotuned persistent
+launch replayed from a CUDA graph) and 1e6 events on each heavy target. Checked against the
+oracle on every event where it runs in seconds on the host cores (spectra, angles, the
+paper's Fig. 2 windows, residual (Z, A), multiplicities), else on sampled events it computes
+one by one; and, over every event, by properties that hold at any size: baryon number and
+charge conservation, flags."""
+import os
+
 import numpy as np
 import pytest
 
 from paper_1309_7963_gb300 import inputs, pnuc
 
-from .parity import compare, gpu_subset, oracle_at
+import oracle
+
+from .parity import assert_observables, compare, gpu_subset, observable_table, oracle_at
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +67,22 @@ def test_mixed_targets_4e6_graph_replay_autotuned(ctx):
     assert c["frac_same"] >= 0.97, c["frac_same"]
 
 
+def test_plain_fp32_o16_ca40_2e6_against_the_oracle(ctx):
+    import torch
+    w = inputs.oxygen_calcium(n_each=1_000_000)
+    tids = np.array([ctx.create_target(*za) for za in w.targets], np.int32)
+    r = ctx.simulate(torch.tensor(w.energies, device="cuda"), torch.tensor(tids[w.tidx], device="cuda"), seed=w.seed,
+                     precision="fp32", method="plain", capacity=8 * w.n)
+    torch.cuda.synchronize()
+    res, sec = r.residuals_np(), r.secondaries_np()
+    ok, good = conservation(w, res, sec)
+    assert ok.mean() > 0.995 and good[ok].all()
+    orc = oracle.simulate_parallel(w.targets, w.energies, w.tidx, seed=w.seed)
+    row = observable_table(res, sec, orc["residuals"], orc["secondaries"], w.n)
+    assert_observables(row, "plain fp32 2e6")
+    assert row["residual_ZA_identical"] > 0.99
+
+
 @pytest.mark.parametrize("target", [inputs.TI48, inputs.FE56, inputs.PB208], ids=["48Ti", "56Fe", "208Pb"])
 def test_heavy_targets_1e6(ctx, target):
     import torch
@@ -73,7 +95,17 @@ def test_heavy_targets_1e6(ctx, target):
     res, sec = r.residuals_np(), r.secondaries_np()
     ok, good = conservation(w, res, sec)
     assert ok.mean() > 0.995 and good[ok].all()
+    orc = oracle.simulate_parallel(w.targets, w.energies, w.tidx, seed=w.seed)
+    row = observable_table(res, sec, orc["residuals"], orc["secondaries"], w.n)
+    assert_observables(row, f"{target} 1e6")
+    assert row["residual_ZA_identical"] > 0.99
     ids = sample_ids(w.n, 500, 2)
     gres, gsec = gpu_subset(res, sec, ids)
     c = compare(gres, gsec, oracle_at(w, ids), len(ids))
     assert c["frac_same"] >= 0.97, c["frac_same"]
+    path = os.environ.get("PNUC_OBSERVABLES_OUT")
+    if path:
+        import json
+        data = json.load(open(path)) if os.path.exists(path) else {}
+        data[f"full size: p-{target} 100-250 MeV, 1e6 events"] = row
+        json.dump(data, open(path, "w"), indent=1)
