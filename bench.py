@@ -60,6 +60,14 @@ EVAP_FP64_OPS = {
 KERNEL_FILES = ("pnuc_device.cuh", "pnuc_kernels.cuh", "kernel_fp32.cu", "pnuc_internal.h")
 
 
+def measured_hbm_gbs():
+    """Copy bandwidth of this machine's GB300 (driver-measured), or None."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def kernel_sha1() -> str:
     import hashlib
     h = hashlib.sha1()
@@ -329,6 +337,30 @@ def main():
         e2e = {"value": world * n * steps_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": int(e_h.nbytes + t_h.nbytes),
                "d2h_bytes_per_step": int(res_h.nbytes + len(sec) * 32 + 8)}
 
+    # yield tallies of the last step's outputs (an HBM-streaming pass): L2 flushed before each
+    tally = None
+    if rank == 0:
+        hbm_peak = measured_hbm_gbs()
+        n_sec_out = min(out.n_secondaries(), cap)
+        hs = None
+        tms = []
+        for k in range(6):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            hs = ctx.tally(out, e_dev, n_T=125, n_cos=1, n_E=1, E_range=(199.0, 201.0), Z_max=30, A_max=64)
+            b.record(stream)
+            torch.cuda.synchronize()
+            tms.append(a.elapsed_time(b))
+        t_ms = float(np.median(tms[1:]))
+        tbytes = 32 * n_sec_out + (32 + 8) * n
+        tally = {"ms": t_ms, "algorithmic_bytes": tbytes, "GB_s": tbytes / (t_ms * 1e-3) / 1e9,
+                 "hbm_peak_GB_s": hbm_peak, "frac": (tbytes / (t_ms * 1e-3) / 1e9) / hbm_peak if hbm_peak else None,
+                 "spec": "secondaries 2 x 6 x 125 T bins (2 MeV, angle-integrated as in the paper's Fig. 1; "
+                         "shared-memory counters), residuals 1 x 31 x 65 (Z, A) (global atomics)",
+                 "secondaries": int(n_sec_out), "events": n}
+        del hs
+
     # algorithmic work per event from the kernel's own counters (one counting launch)
     cnt = ctx.simulate(e_dev, t_dev, seed=w.seed, first_event_id=first, precision="fp32", method="persistent",
                        counters=True, capacity=cap)
@@ -382,6 +414,7 @@ def main():
         "p99_ms": serving["runs"][-1]["p99_ms"] if serving else None,
         "serving": serving,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cb, "clocks": clk, "gpu_launches": 2 * args.steps,
+        "tally": tally,
     }
     print(json.dumps(line))
 

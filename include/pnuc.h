@@ -322,6 +322,34 @@ pnuc_status pnuc_server_reset_stats(pnuc_server *server);
 /* Drops queued requests, waits for those in flight, frees everything. Safe on NULL. */
 pnuc_status pnuc_server_destroy(pnuc_server *server);
 
+/* Yield tallies of a batch (paper §4.1, Figs. 1-2: secondary yields per energy and angle;
+ * §4.2: yields of positron emitters, i.e. of residual nuclei, per incident energy). One pass
+ * over the output records on the device, accumulated (+=) into caller-owned device
+ * histograms of unsigned 64-bit counts, so several batches can add up.
+ *
+ * Secondaries: bin (origin, species, cos theta, T) of each record with T in [T_min, T_max):
+ *   iT = floor((T - T_min) * sT) with sT = n_T / (T_max - T_min),
+ *   ic = min(floor((uz + 1) * (n_cos / 2)), n_cos - 1), histogram
+ *   [2 origins][6 species][n_cos][n_T]; records outside the T range are not counted.
+ * Residuals: events without PNUC_FLAG_BAD_INPUT or PNUC_FLAG_ATTEMPT_CAP, with incident
+ *   energy E in [E_min, E_max), Z_final <= Z_max (<= 255) and A_final <= A_max (<= 511):
+ *   iE = floor((E - E_min) * sE) with sE = n_E / (E_max - E_min), histogram
+ *   [n_E][Z_max + 1][A_max + 1].
+ * All bin arithmetic in FP64, each operation rounded to nearest in the order written. Either
+ * histogram may be NULL (that part is skipped). sec and
+ * res/energies are the device arrays of one batch (n_sec records, n events).
+ * PNUC_ERR_ARG for a bad spec (empty or inverted ranges, more than 2^28 cells). */
+typedef struct {
+    int32_t n_T, n_cos;
+    double T_min, T_max;
+    int32_t n_E, Z_max;
+    double E_min, E_max;
+    int32_t A_max, reserved;
+} pnuc_tally_spec;
+pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, const pnuc_secondary *secondaries,
+                       uint64_t n_secondaries, const pnuc_residual *residuals, const double *energies, uint64_t n,
+                       unsigned long long *secondary_hist, unsigned long long *residual_hist, void *stream);
+
 /* Per-kernel timing of pnuc_simulate's launches (measurement support; the paper has no
  * counterpart). pnuc_kernel_timing(ctx, 1) clears the record and makes later launches
  * through pnuc_simulate and the entry points built on it record CUDA events on the

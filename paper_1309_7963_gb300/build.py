@@ -1,7 +1,8 @@
 """Builds libpnuc.so in-tree (paper_1309_7963_gb300/_build/) with nvcc for sm_103a.
 
-Four translation units compiled in parallel: the host API, the table kernels, and the
-event kernels in FP64 (no FMA contraction) and FP32 (fast single-precision math).
+Translation units compiled in parallel: the host API, autotuner, graph plans, serving loop,
+table kernels, pipe microbenchmarks, yield tallies, and the event kernels in FP64 (no FMA
+contraction) and FP32 (fast single-precision math).
 """
 from __future__ import annotations
 
@@ -24,6 +25,7 @@ UNITS = {
     "server.cu": [],
     "tables.cu": [],
     "microbench.cu": [],
+    "tally.cu": [],
     "kernel_fp64.cu": ["--fmad=false"],
     "kernel_fp32.cu": ["--use_fast_math"],
 }

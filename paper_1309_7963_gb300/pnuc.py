@@ -68,6 +68,12 @@ class pnuc_peaks(C.Structure):
     _fields_ = [("fp32_fma", C.c_double), ("fp64_fma", C.c_double), ("mufu", C.c_double), ("int32_mad", C.c_double)]
 
 
+class pnuc_tally_spec(C.Structure):
+    _fields_ = [("n_T", C.c_int32), ("n_cos", C.c_int32), ("T_min", C.c_double), ("T_max", C.c_double),
+                ("n_E", C.c_int32), ("Z_max", C.c_int32), ("E_min", C.c_double), ("E_max", C.c_double),
+                ("A_max", C.c_int32), ("reserved", C.c_int32)]
+
+
 class pnuc_server_config(C.Structure):
     _fields_ = [("precision", C.c_int32), ("streams", C.c_int32), ("arena_bytes", C.c_uint64),
                 ("sec_per_event", C.c_uint32), ("max_pending", C.c_uint32), ("max_request_events", C.c_uint64)]
@@ -119,6 +125,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_measure_peaks.argtypes = [vp, C.POINTER(pnuc_peaks)]
     L.pnuc_kernel_timing.argtypes = [vp, C.c_int32]
     L.pnuc_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(u64)]
+    L.pnuc_tally.argtypes = [vp, C.POINTER(pnuc_tally_spec), vp, u64, vp, vp, u64, vp, vp, vp]
     L.pnuc_autotune.argtypes = [vp, C.c_int, C.POINTER(pnuc_batch), C.POINTER(pnuc_output), C.c_int32,
                                 C.POINTER(pnuc_tuning), C.POINTER(C.c_double), vp]
     L.pnuc_save_tuning.argtypes = [vp, C.c_char_p]
@@ -260,6 +267,25 @@ class Context:
         c, v, n = C.c_double(), C.c_double(), C.c_uint64()
         self._check(self.lib.pnuc_kernel_times(self.handle, C.byref(c), C.byref(v), C.byref(n)))
         return dict(cascade_ms=c.value, evaporation_ms=v.value, launches=n.value)
+
+    def tally(self, result: "Result", energies, T_range=(0.0, 250.0), n_T=125, n_cos=1, E_range=(20.0, 250.0),
+              n_E=1, Z_max=100, A_max=250, hists=None, stream=None):
+        """pnuc_tally: yield histograms of a batch's results (int64 tensors on the device,
+        accumulated into `hists` if given): secondaries [2 origins][6 species][n_cos][n_T] over
+        T_range (MeV), residual nuclei [n_E][Z_max + 1][A_max + 1] over incident E_range."""
+        torch = self._torch
+        dev = torch.device("cuda", self.device)
+        if hists is None:
+            hists = (torch.zeros((2, 6, n_cos, n_T), dtype=torch.int64, device=dev),
+                     torch.zeros((n_E, Z_max + 1, A_max + 1), dtype=torch.int64, device=dev))
+        spec = pnuc_tally_spec(n_T, n_cos, T_range[0], T_range[1], n_E, Z_max, E_range[0], E_range[1], A_max, 0)
+        n = int(energies.shape[0])
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        n_sec = min(result.n_secondaries(), int(result.secondaries.shape[0]))
+        self._check(self.lib.pnuc_tally(self.handle, C.byref(spec), _ptr(result.secondaries), n_sec,
+                                        _ptr(result.residuals), _ptr(energies), n, _ptr(hists[0]), _ptr(hists[1]),
+                                        C.c_void_p(s)))
+        return hists
 
     def _structs(self, energies, target_ids, seed, first_event_id, out):
         b = pnuc_batch(_ptr(energies), _ptr(target_ids), int(energies.shape[0]), seed, first_event_id)
