@@ -357,7 +357,7 @@ def main():
         tally = {"ms": t_ms, "algorithmic_bytes": tbytes, "GB_s": tbytes / (t_ms * 1e-3) / 1e9,
                  "hbm_peak_GB_s": hbm_peak, "frac": (tbytes / (t_ms * 1e-3) / 1e9) / hbm_peak if hbm_peak else None,
                  "spec": "secondaries 2 x 6 x 125 T bins (2 MeV, angle-integrated as in the paper's Fig. 1; "
-                         "shared-memory counters), residuals 1 x 31 x 65 (Z, A) (global atomics)",
+                         "shared-memory counters), residuals 1 x 31 x 65 (Z, A) (shared-memory counters)",
                  "secondaries": int(n_sec_out), "events": n}
         del hs
 

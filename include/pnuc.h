@@ -81,7 +81,7 @@ typedef struct {
     float P_final[3];      /* recoil momentum of the final residual from evaporation, MeV/c */
 } pnuc_residual;
 
-#define PNUC_FLAG_BAD_INPUT 1u         /* energy outside [20, 250] MeV or unknown target id */
+#define PNUC_FLAG_BAD_INPUT 1u         /* energy outside [20, 250] MeV, unknown target id or projectile */
 #define PNUC_FLAG_ATTEMPT_CAP 2u       /* no non-elastic entry within max_attempts */
 #define PNUC_FLAG_STEP_CAP 4u          /* max_steps transport steps; particles in flight captured */
 #define PNUC_FLAG_STACK_OVERFLOW 8u    /* particle stack full; the particle was captured */
@@ -113,13 +113,18 @@ typedef struct {
     int32_t max_evap_trials;   /* rejection trials per emission (default 10000) */
 } pnuc_config;
 
-/* One batch of incident protons. */
+/* One batch of incident nucleons. */
 typedef struct {
     const double *energies;    /* device, n entries: incident kinetic energy, MeV */
     const int32_t *target_ids; /* device, n entries: ids from pnuc_create_target */
     uint64_t n;                /* events; at most 2^32 - 1 */
     uint64_t seed;             /* Philox key word 0 */
     uint64_t first_event_id;   /* event i of the batch has id first_event_id + i */
+    const uint8_t *projectiles; /* device, n entries: incident nucleon, 1 proton, 0 neutron
+                                  (other values: PNUC_FLAG_BAD_INPUT); NULL = all protons.
+                                  Neutron-induced events take the neutron's mass and the
+                                  neutron well at entry, and the residual keeps the target's
+                                  charge (an extension of the paper's proton-induced model) */
 } pnuc_batch;
 
 /* Where a batch's results go. */
@@ -191,7 +196,8 @@ pnuc_status pnuc_simulate(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method m
  * residuals (host, n entries), up to sec_capacity secondaries (host) and the produced
  * count (host) are copied back. Synchronous: returns after the results are on the host.
  * Returns PNUC_ERR_CAPACITY if *sec_count > sec_capacity (the first sec_capacity
- * records are still written). */
+ * records are still written). Incident protons (neutron-induced events go through
+ * pnuc_simulate with pnuc_batch.projectiles). */
 pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method,
                                const double *energies, const int32_t *target_ids, uint64_t n,
                                uint64_t seed, uint64_t first_event_id, pnuc_secondary *secondaries,

@@ -111,7 +111,7 @@ def lib() -> C.CDLL:
             L.orc_sample_U.argtypes = [d, d, d, u64, u64, i64, vp]
             L.orc_sample_U.restype = i64
             L.orc_sample_fermi.argtypes = [d, u64, u64, i64, vp]
-            L.orc_simulate.argtypes = [vp, i32, vp, vp, u64, u64, u64, vp, u64, vp, vp, vp, vp, i64,
+            L.orc_simulate.argtypes = [vp, i32, vp, vp, vp, u64, u64, u64, vp, u64, vp, vp, vp, vp, i64,
                                        vp, u64, vp]
             L.orc_simulate.restype = u64
             L.orc_sizeof.argtypes = [C.c_int]
@@ -233,10 +233,12 @@ def make_targets(za_list):
 
 
 def simulate(targets, energies, tidx, seed: int, first_event_id: int = 0, limits=None,
-             inject=None, trace: bool = False, trace_cap: int = 1 << 20, sec_per_event: int = 40):
+             inject=None, trace: bool = False, trace_cap: int = 1 << 20, sec_per_event: int = 40,
+             projectiles=None):
     """Runs events first_event_id + k on targets[tidx[k]] at energies[k] MeV, serially.
 
-    targets: TARGET_DTYPE array (see make_targets) or list of (Z, A).
+    targets: TARGET_DTYPE array (see make_targets) or list of (Z, A). projectiles: the
+    incident nucleon of each event (1 proton, 0 neutron); None = all protons.
     Returns dict(secondaries, residuals, counters[, trace]). Secondaries are in event
     order, each event's in emission order.
     """
@@ -248,6 +250,8 @@ def simulate(targets, energies, tidx, seed: int, first_event_id: int = 0, limits
     ti = np.ascontiguousarray(tidx, np.int32)
     n = int(e.shape[0])
     assert ti.shape[0] == n
+    pj = None if projectiles is None else np.ascontiguousarray(projectiles, np.int32)
+    assert pj is None or pj.shape[0] == n
     lim = np.zeros(1, LIMITS_DTYPE)
     for k, v in {**DEFAULT_LIMITS, **(limits or {})}.items():
         lim[k] = v
@@ -259,7 +263,8 @@ def simulate(targets, energies, tidx, seed: int, first_event_id: int = 0, limits
         sec = np.zeros(cap, SECONDARY_DTYPE)
         tr = np.zeros(trace_cap if trace else 0, TRACE_DTYPE)
         trc = np.zeros(1, np.uint64)
-        got = L.orc_simulate(_p(targets), len(targets), _p(e), _p(ti), n, seed, first_event_id,
+        got = L.orc_simulate(_p(targets), len(targets), _p(e), _p(ti), None if pj is None else _p(pj), n, seed,
+                             first_event_id,
                              _p(sec), cap, _p(res), _p(cnt), _p(lim),
                              None if inj is None else _p(inj), 0 if inj is None else len(inj),
                              _p(tr) if trace else None, trace_cap if trace else 0, _p(trc))
@@ -275,7 +280,8 @@ def simulate(targets, energies, tidx, seed: int, first_event_id: int = 0, limits
 
 
 def simulate_parallel(targets, energies, tidx, seed: int, first_event_id: int = 0,
-                      threads: int | None = None, chunk: int = 2048, limits=None, keep: bool = True):
+                      threads: int | None = None, chunk: int = 2048, limits=None, keep: bool = True,
+                      projectiles=None):
     """simulate() over event chunks on a thread pool (the C call releases the GIL).
 
     Results are identical to simulate(): every event depends only on (seed, event id).
@@ -286,13 +292,14 @@ def simulate_parallel(targets, energies, tidx, seed: int, first_event_id: int = 
         targets = make_targets(targets)
     e = np.ascontiguousarray(energies, np.float64)
     ti = np.ascontiguousarray(tidx, np.int32)
+    pj = None if projectiles is None else np.ascontiguousarray(projectiles, np.int32)
     n = e.shape[0]
     threads = threads or os.cpu_count() or 1
     starts = list(range(0, n, chunk))
 
     def run(s0):
         r = simulate(targets, e[s0:s0 + chunk], ti[s0:s0 + chunk], seed, first_event_id + s0,
-                     limits=limits)
+                     limits=limits, projectiles=None if pj is None else pj[s0:s0 + chunk])
         r["secondaries"]["event"] += s0
         if not keep:
             r = dict(n_secondaries=len(r["secondaries"]), counters=r["counters"])

@@ -594,7 +594,9 @@ static int emit(sink *o, uint32_t ev, int species, int origin, int index, double
     return 0;
 }
 
-static void run_event(const orc_target *t, double T0, uint32_t ev, orc_stream *st, const orc_limits *L,
+/* One event: a nucleon of species proj (1 proton, 0 neutron: the incident particle of a
+ * proton- or neutron-induced interaction) at kinetic energy T0 on target t. */
+static void run_event(const orc_target *t, int proj, double T0, uint32_t ev, orc_stream *st, const orc_limits *L,
                       sink *o, orc_residual *res, orc_counters *c)
 {
     memset(res, 0, sizeof *res);
@@ -604,7 +606,8 @@ static void run_event(const orc_target *t, double T0, uint32_t ev, orc_stream *s
         res->flags |= F_BAD_INPUT;
         return;
     }
-    const double p0 = sqrt(T0 * T0 + 2.0 * T0 * M_P);
+    const double mproj = mass_of(proj);
+    const double p0 = sqrt(T0 * T0 + 2.0 * T0 * mproj);
     int n_index = 0, n_coll = 0, n_p_esc = 0, n_esc = 0;
     double Esum = 0.0, Psum[3] = {0, 0, 0};
     particle stack[256];
@@ -625,7 +628,7 @@ static void run_event(const orc_target *t, double T0, uint32_t ev, orc_stream *s
         double b = t->R * sqrt(U(st));
         double phi = TWO_PI * U(st);
         particle cur;
-        cur.s = 1;
+        cur.s = proj;
         cur.shell = NSHELL - 1;
         cur.r[0] = b * cos(phi);
         cur.r[1] = b * sin(phi);
@@ -636,9 +639,9 @@ static void run_event(const orc_target *t, double T0, uint32_t ev, orc_stream *s
         {
             double rr = sqrt(dot3(cur.r, cur.r));
             double n[3] = {cur.r[0] / rr, cur.r[1] / rr, cur.r[2] / rr};
-            orc_refract(n, cur.p, M_P, t->V[1][NSHELL - 1]);
+            orc_refract(n, cur.p, mproj, t->V[proj][NSHELL - 1]);
         }
-        trace_put(o, ev, TR_ENTRY, 1, cur.shell, kinetic(dot3(cur.p, cur.p), M_P), cur.r);
+        trace_put(o, ev, TR_ENTRY, proj, cur.shell, kinetic(dot3(cur.p, cur.p), mproj), cur.r);
         int sp = 0;      /* stack depth */
         int alive = 1;   /* cur holds a particle */
         while (alive) {
@@ -769,11 +772,11 @@ static void run_event(const orc_target *t, double T0, uint32_t ev, orc_stream *s
      * Metropolis et al.): the static mean field absorbs the cascade's momentum imbalance
      * but does no work, so E* is the energy balance in the target rest frame and the
      * residual starts the evaporation at rest. */
-    int Z = t->Z + 1 - n_p_esc, A = t->A + 1 - n_esc;
+    int Z = t->Z + proj - n_p_esc, A = t->A + 1 - n_esc;
     c->settled++;
     res->Zc = res->Zf = Z;
     res->Ac = res->Af = A;
-    double Er = T0 + M_P + t->M - Esum;
+    double Er = T0 + mproj + t->M - Esum;
     double Pr[3] = {0.0, 0.0, 0.0};
     res->Pcas[0] = -Psum[0];
     res->Pcas[1] = -Psum[1];
@@ -868,12 +871,14 @@ static void run_event(const orc_target *t, double T0, uint32_t ev, orc_stream *s
 }
 
 /* ------------------------------------------------------------------ batch entry point
- * Simulates events first_event_id + k (k < n): energies[k] in MeV on targets[tidx[k]].
+ * Simulates events first_event_id + k (k < n): a nucleon of species projectiles[k] (1 proton,
+ * 0 neutron; all protons if projectiles is NULL) at energies[k] MeV on targets[tidx[k]].
  * Secondaries are written in event order (at most sec_cap); the return value is the
  * number produced. inject/n_inject, if given, replace the first draws of every event.
  * trace/trace_cap, if given, receive one entry per model decision. */
 uint64_t orc_simulate(const orc_target *targets, int32_t n_targets, const double *energies,
-                      const int32_t *tidx, uint64_t n, uint64_t seed, uint64_t first_event_id,
+                      const int32_t *tidx, const int32_t *projectiles, uint64_t n, uint64_t seed,
+                      uint64_t first_event_id,
                       orc_secondary *sec, uint64_t sec_cap, orc_residual *res, orc_counters *cnt,
                       const orc_limits *lim, const double *inject, int64_t n_inject, orc_trace *trace,
                       uint64_t trace_cap, uint64_t *trace_count)
@@ -886,15 +891,16 @@ uint64_t orc_simulate(const orc_target *targets, int32_t n_targets, const double
     }
     for (uint64_t k = 0; k < n; k++) {
         int32_t ti = tidx[k];
+        const int proj = projectiles ? projectiles[k] : 1;
         uint64_t before = o.count;
-        if (ti < 0 || ti >= n_targets) {
+        if (ti < 0 || ti >= n_targets || (proj != 0 && proj != 1)) {
             memset(&res[k], 0, sizeof res[k]);
             res[k].flags = F_BAD_INPUT;
             continue;
         }
         orc_stream st;
         stream_init(&st, seed, first_event_id + k, inject, n_inject, cnt);
-        run_event(&targets[ti], energies[k], (uint32_t)k, &st, lim, &o, &res[k], cnt);
+        run_event(&targets[ti], proj, energies[k], (uint32_t)k, &st, lim, &o, &res[k], cnt);
         if (o.count > sec_cap && before < o.count) res[k].flags |= F_OUTPUT_OVERFLOW;
     }
     if (trace_count) *trace_count = o.trace_count;

@@ -102,6 +102,7 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
     SimParams p;
     p.energies = batch->energies;
     p.target_ids = batch->target_ids;
+    p.projectiles = batch->projectiles;
     p.n = batch->n;
     p.seed = batch->seed;
     p.first_event_id = batch->first_event_id;

@@ -346,6 +346,7 @@ struct Lane {
     int tgt;
     int phase;
     double T0;
+    int proj;  // incident nucleon: 1 proton, 0 neutron
     // particle in flight
     R r[3], p[3];
     int s, shell, sp;
@@ -459,6 +460,7 @@ __device__ void begin_event(const SimParams &P, const TargetScalars *tabs, Lane<
     L.rng.reset(P.seed, P.first_event_id + ev);
     L.T0 = __ldg(&P.energies[ev]);
     L.tgt = __ldg(&P.target_ids[ev]);
+    L.proj = P.projectiles ? (int)__ldg(&P.projectiles[ev]) : 1;
     L.steps = L.attempts = L.n_coll = L.n_index = L.n_esc = L.n_p_esc = L.n_evap = 0;
     L.flags = 0;
     L.pend = 0;
@@ -470,7 +472,7 @@ __device__ void begin_event(const SimParams &P, const TargetScalars *tabs, Lane<
     L.Z = L.Zc = tgt_ok ? tabs[L.tgt].Z : 0;
     L.A = L.Ac = tgt_ok ? tabs[L.tgt].A : 0;
     const R T0r = to_R<R>(L.T0);
-    if (!tgt_ok || !(T0r >= R(20) && T0r <= R(250))) {
+    if (!tgt_ok || !(T0r >= R(20) && T0r <= R(250)) || (L.proj != 0 && L.proj != 1)) {
         L.flags = PNUC_FLAG_BAD_INPUT;
         L.phase = kFinish;
         return;
@@ -500,11 +502,12 @@ __device__ void step_entry(const SimParams &P, const ShellTable<R> &t, double Ra
     const R T0 = to_R<R>(L.T0);
     L.p[0] = R(0);
     L.p[1] = R(0);
-    L.p[2] = sqrt(T0 * T0 + R(2) * T0 * R(kMp));
+    const R mproj = nucleon_mass_R<R>(L.proj);
+    L.p[2] = sqrt(T0 * T0 + R(2) * T0 * mproj);
     R rr = sqrt(dot3(L.r, L.r));
     R n[3] = {L.r[0] / rr, L.r[1] / rr, L.r[2] / rr};
-    refract(n, L.p, (R)kMp, t.V[1][kShells - 1]);
-    L.s = 1;
+    refract(n, L.p, mproj, t.V[L.proj][kShells - 1]);
+    L.s = L.proj;
     L.shell = kShells - 1;
     L.sp = 0;
     L.phase = kTransport;
@@ -518,11 +521,12 @@ template <typename R>
 __device__ void settle_cascade(const SimParams &P, double Mt, Lane<R> &L)
 {
     const int Z = L.Z, A = L.A;
-    double p0 = sqrt(L.T0 * L.T0 + 2.0 * L.T0 * kMp);
+    const double mproj = nucleon_mass(L.proj);
+    double p0 = sqrt(L.T0 * L.T0 + 2.0 * L.T0 * mproj);
     L.Px = -L.Px;
     L.Py = -L.Py;
     L.Pz = p0 - L.Pz;
-    double Er = L.T0 + kMp + Mt - L.Esum;
+    double Er = L.T0 + mproj + Mt - L.Esum;
     L.Er = Er;
     L.Prx = L.Pry = L.Prz = 0.0;
     if (Z < 1 || A - Z < 1) {
@@ -553,7 +557,7 @@ __device__ void end_cascade(const SimParams &P, const TargetScalars &tab, Lane<R
         L.phase = kEntry;
         return;
     }
-    L.Z = L.Zc = tab.Z + 1 - L.n_p_esc;
+    L.Z = L.Zc = tab.Z + L.proj - L.n_p_esc;
     L.A = L.Ac = tab.A + 1 - L.n_esc;
     if (kSplit) {
         // the residual record carries the raw escape sums and the draw position
@@ -592,6 +596,7 @@ __device__ void begin_evap(const SimParams &P, Lane<R> &L, uint32_t ev)
     read_pending_sums(o, L.Esum, L.Px, L.Py, L.Pz);
     L.T0 = __ldg(&P.energies[ev]);
     const int tgt = __ldg(&P.target_ids[ev]);
+    L.proj = P.projectiles ? (int)__ldg(&P.projectiles[ev]) : 1;
     L.rng.reset(P.seed, P.first_event_id + ev);
     L.rng.seek(o.reserved - 1u);
     if (tgt < 0 || tgt >= P.n_targets) {  // cannot happen: the cascade checked it

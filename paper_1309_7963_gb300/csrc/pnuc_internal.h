@@ -45,6 +45,7 @@ struct TargetTable {
 struct SimParams {
     const double *energies;
     const int32_t *target_ids;
+    const uint8_t *projectiles;      // per event 1 proton, 0 neutron; null = all protons
     uint64_t n;
     uint64_t seed;
     uint64_t first_event_id;

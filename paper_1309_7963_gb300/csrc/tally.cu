@@ -57,8 +57,14 @@ __global__ void __launch_bounds__(kTallyBlock)
 
 __global__ void __launch_bounds__(kTallyBlock)
     residual_tally_kernel(const uint4 *__restrict__ res, const double *__restrict__ energies, uint64_t n,
-                          double E_min, double sE, int nE, int Zmax, int Amax, unsigned long long *hist)
+                          double E_min, double sE, int nE, int Zmax, int Amax, unsigned long long *hist, int nbins)
 {
+    extern __shared__ unsigned int cells[];
+    const bool priv = nbins <= kSmemBins;
+    if (priv) {
+        for (int i = threadIdx.x; i < nbins; i += blockDim.x) cells[i] = 0u;
+        __syncthreads();
+    }
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint4 a = __ldcs(res + 4 * i), b = __ldcs(res + 4 * i + 1);  // Z/A fields, then flags
@@ -66,7 +72,14 @@ __global__ void __launch_bounds__(kTallyBlock)
         const double e = __dmul_rn(__dsub_rn(__ldcs(energies + i), E_min), sE);
         const int Z = (int)(a.y & 0xffffu), A = (int)(a.y >> 16);
         if (!(e >= 0.0 && e < (double)nE) || Z > Zmax || A > Amax) continue;
-        add_cell(hist, ((int)e * (Zmax + 1) + Z) * (Amax + 1) + A);
+        const int idx = ((int)e * (Zmax + 1) + Z) * (Amax + 1) + A;
+        if (priv) atomicAdd(&cells[idx], 1u);
+        else add_cell(hist, idx);
+    }
+    if (priv) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < nbins; i += blockDim.x)
+            if (cells[i]) atomicAdd(&hist[i], (unsigned long long)cells[i]);
     }
 }
 
@@ -114,9 +127,10 @@ extern "C" pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, co
         if (n > 0 && (!residuals || !energies)) return fail(ctx, PNUC_ERR_ARG, "null residuals or energies");
         if (n > 0) {
             const double sE = (double)s.n_E / (s.E_max - s.E_min);
-            residual_tally_kernel<<<tally_grid(n, ctx->sm_count), kTallyBlock, 0, st>>>(
+            const size_t smem = cells <= (uint64_t)kSmemBins ? cells * sizeof(unsigned int) : 0;
+            residual_tally_kernel<<<tally_grid(n, ctx->sm_count), kTallyBlock, smem, st>>>(
                 reinterpret_cast<const uint4 *>(residuals), energies, n, s.E_min, sE, s.n_E, s.Z_max, s.A_max,
-                residual_hist);
+                residual_hist, (int)cells);
             CU(ctx, cudaGetLastError());
         }
     }

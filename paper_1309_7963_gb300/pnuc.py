@@ -44,7 +44,7 @@ class pnuc_config(C.Structure):
 
 class pnuc_batch(C.Structure):
     _fields_ = [("energies", C.c_void_p), ("target_ids", C.c_void_p), ("n", C.c_uint64), ("seed", C.c_uint64),
-                ("first_event_id", C.c_uint64)]
+                ("first_event_id", C.c_uint64), ("projectiles", C.c_void_p)]
 
 
 class pnuc_output(C.Structure):
@@ -327,9 +327,10 @@ class Context:
 
     def simulate(self, energies, target_ids, seed: int, first_event_id: int = 0, precision: str = "fp32",
                  method: str = "persistent", out: Result | None = None, capacity: int | None = None,
-                 counters: bool = False, stream=None) -> Result:
-        """Launches pnuc_simulate on device tensors (energies float64, target_ids int32).
-        Asynchronous on `stream` (default: torch's current stream)."""
+                 counters: bool = False, stream=None, projectiles=None) -> Result:
+        """Launches pnuc_simulate on device tensors (energies float64, target_ids int32,
+        optional projectiles uint8: 1 proton, 0 neutron; None = protons). Asynchronous on
+        `stream` (default: torch's current stream)."""
         torch = self._torch
         n = int(energies.shape[0])
         if energies.dtype != torch.float64 or target_ids.dtype != torch.int32:
@@ -340,7 +341,12 @@ class Context:
         target_ids = target_ids.contiguous()
         if out is None:
             out = self.alloc(n, capacity, counters)
-        b = pnuc_batch(_ptr(energies), _ptr(target_ids), n, seed, first_event_id)
+        pj = None
+        if projectiles is not None:
+            if projectiles.dtype != torch.uint8 or not projectiles.is_cuda or projectiles.shape[0] != n:
+                raise ValueError("projectiles must be a uint8 CUDA tensor of the batch's length")
+            pj = projectiles.contiguous()
+        b = pnuc_batch(_ptr(energies), _ptr(target_ids), n, seed, first_event_id, _ptr(pj) if pj is not None else None)
         o = pnuc_output(_ptr(out.secondaries), out.secondaries.shape[0], _ptr(out.count), _ptr(out.residuals),
                         _ptr(out.counters))
         s = (stream or torch.cuda.current_stream(self.device)).cuda_stream

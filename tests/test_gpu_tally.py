@@ -21,20 +21,20 @@ def run(ctx, w, precision):
     return e, r
 
 
-@pytest.mark.parametrize("n_cos,n_T", [(1, 125), (40, 125)])
-def test_tally_equals_reference_on_the_same_records(ctx, n_cos, n_T):
+@pytest.mark.parametrize("n_cos,n_T,n_E", [(1, 125, 2), (40, 125, 23)])  # shared-memory, then global cells
+def test_tally_equals_reference_on_the_same_records(ctx, n_cos, n_T, n_E):
     import torch
     w = inputs.mixed(60_000, seed=8)
     e, r = run(ctx, w, "fp32")
-    sh, rh = ctx.tally(r, e, n_T=n_T, n_cos=n_cos, n_E=23, Z_max=30, A_max=64)
+    sh, rh = ctx.tally(r, e, n_T=n_T, n_cos=n_cos, n_E=n_E, Z_max=30, A_max=64)
     torch.cuda.synchronize()
     sec, res = r.secondaries_np(), r.residuals_np()
     assert np.array_equal(sh.cpu().numpy(), ref.secondary_hist(sec["T"], sec["uz"], sec["species"], sec["origin"],
                                                                 (0.0, 250.0), n_T, n_cos))
     assert np.array_equal(rh.cpu().numpy(), ref.residual_hist(res["Z_final"], res["A_final"], res["flags"], w.energies,
-                                                               (20.0, 250.0), 23, 30, 64))
+                                                               (20.0, 250.0), n_E, 30, 64))
     # accumulation: a second call adds the same counts
-    ctx.tally(r, e, n_T=n_T, n_cos=n_cos, n_E=23, Z_max=30, A_max=64, hists=(sh, rh))
+    ctx.tally(r, e, n_T=n_T, n_cos=n_cos, n_E=n_E, Z_max=30, A_max=64, hists=(sh, rh))
     assert np.array_equal(sh.cpu().numpy(), 2 * ref.secondary_hist(sec["T"], sec["uz"], sec["species"], sec["origin"],
                                                                     (0.0, 250.0), n_T, n_cos))
 

@@ -18,22 +18,26 @@ def _run(za, energy, n, seed=0, **kw):
     return oracle.simulate([za], energy, np.zeros(n, np.int32), seed=seed, **kw)
 
 
+@pytest.mark.parametrize("proj", [1, 0], ids=["proton", "neutron"])
 @pytest.mark.parametrize("za,energy", [((8, 16), 200.0), ((20, 40), 70.0), ((82, 208), 150.0), ((6, 12), 25.0)])
-def test_conservation_per_event(za, energy):
+def test_conservation_per_event(za, energy, proj):
+    """Per event, for proton- and neutron-induced events: baryon number and charge, energy,
+    the cascade's momentum against the static field, evaporation momentum, mass shell."""
     Z, A = za
-    r = _run(za, energy, 1500)
+    m_proj = oracle.M_P if proj else oracle.M_N
+    r = _run(za, energy, 1500, projectiles=np.full(1500, proj))
     sec, res = r["secondaries"], r["residuals"]
     ok = (res["flags"] & ~np.uint32(32 | 16)) == 0
     ev = sec["event"]
     sa = np.bincount(ev, weights=ZA_EJ[sec["species"], 1], minlength=len(res))
     sz = np.bincount(ev, weights=ZA_EJ[sec["species"], 0], minlength=len(res))
     assert np.all(sa[ok] + res["Af"][ok] == A + 1)
-    assert np.all(sz[ok] + res["Zf"][ok] == Z + 1)
-    Ein = energy + oracle.M_P + oracle.semf_mass(Z, A)
+    assert np.all(sz[ok] + res["Zf"][ok] == Z + proj)
+    Ein = energy + m_proj + oracle.semf_mass(Z, A)
     Eout = np.bincount(ev, weights=sec["T"] + M_EJ[sec["species"]], minlength=len(res)) + res["Ef"]
     assert np.allclose(Eout[ok], Ein, rtol=1e-12, atol=0)
     # momentum: the cascade's imbalance goes to the static field, the evaporation conserves it
-    p0 = np.sqrt(energy ** 2 + 2 * energy * oracle.M_P)
+    p0 = np.sqrt(energy ** 2 + 2 * energy * m_proj)
     casc = sec["origin"] == 0
     for k, comp in enumerate(("px", "py", "pz")):
         pc = np.bincount(ev[casc], weights=sec[comp][casc], minlength=len(res))
@@ -132,3 +136,24 @@ def test_secondary_order_and_bad_inputs():
     assert list(s0["index"]) == list(range(len(s0)))
     assert np.all(np.diff(s0["origin"]) >= 0)
     assert res["n_casc"][0] + res["n_evap"][0] == len(s0)
+
+
+def test_neutron_entry_and_residual_charge_from_trace():
+    """A neutron enters through the neutron well of the surface shell: its entry record is
+    species 0 with kinetic energy T0 + V_n (refraction into the well at fixed tangential
+    momentum), and the residual charge after the cascade counts only escaped protons."""
+    za = (8, 16)
+    t = oracle.target(*za)
+    n = 300
+    r = _run(za, 60.0, n, trace=True, projectiles=np.zeros(n, np.int32))
+    tr = r["trace"]
+    ent = tr[tr["kind"] == K["entry"]]
+    assert len(ent) >= n and np.all(ent["species"] == 0)
+    assert np.allclose(ent["T"], 60.0 + t["V"][0][14], rtol=1e-12)
+    res, sec = r["residuals"], r["secondaries"]
+    ok = (res["flags"] & ~np.uint32(32 | 16)) == 0
+    nps = np.bincount(sec["event"][(sec["species"] == 1) & (sec["origin"] == 0)], minlength=n)
+    assert np.all((res["Zc"] == 8 - nps)[ok])
+    # the same events as protons differ: the projectile species enters the stream of decisions
+    rp = _run(za, 60.0, n, projectiles=np.ones(n, np.int32))
+    assert not np.array_equal(rp["residuals"]["Zc"], res["Zc"])
