@@ -50,8 +50,13 @@ typedef enum {
 
 typedef enum {
     PNUC_PLAIN = 0,     /* one event per thread, one launch of n threads */
-    PNUC_PERSISTENT = 1 /* two launches of resident warps that refill finished lanes from device
-                           queues: the cascades, then the evaporations they leave pending */
+    PNUC_PERSISTENT = 1, /* two launches of resident warps that refill finished lanes from device
+                            queues: the cascades, then the evaporations they leave pending */
+    PNUC_SORTED = 2      /* as PNUC_PERSISTENT, but the cascade kernel keeps its blocks' events in
+                            shared memory and regroups them by next action every iteration (each
+                            warp runs one action with all its lanes); needs a context buffer for
+                            the events' particle stacks, allocated at the first sorted launch
+                            (which must not be inside a stream capture) */
 } pnuc_method;
 
 /* Secondary particle record, 32 bytes, 16-byte aligned array. */

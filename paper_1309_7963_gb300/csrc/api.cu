@@ -54,7 +54,8 @@ pnuc_status check_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method met
 {
     if (!ctx || !batch || !out) return fail(ctx, PNUC_ERR_ARG, "null argument");
     if (precision != PNUC_FP32 && precision != PNUC_FP64) return fail(ctx, PNUC_ERR_ARG, "bad precision %d", precision);
-    if (method != PNUC_PLAIN && method != PNUC_PERSISTENT) return fail(ctx, PNUC_ERR_ARG, "bad method %d", method);
+    if (method != PNUC_PLAIN && method != PNUC_PERSISTENT && method != PNUC_SORTED)
+        return fail(ctx, PNUC_ERR_ARG, "bad method %d", method);
     if (batch->n > 0xFFFFFFFFull) return fail(ctx, PNUC_ERR_ARG, "n = %llu exceeds 2^32-1", (unsigned long long)batch->n);
     if (!out->count) return fail(ctx, PNUC_ERR_ARG, "out->count is null");
     if (batch->n > 0 && (!batch->energies || !batch->target_ids || !out->residuals))
@@ -92,6 +93,26 @@ cudaEvent_t *timing_slot(pnuc_ctx *ctx, cudaStream_t s)
 }
 
 }  // namespace
+
+// The evaporation kernel after a cascade kernel of the persistent or sorted method, on its
+// own resident grid (it uses more registers, and its shared-memory job lists can make the
+// block size too large: then it halves).
+cudaError_t launch_evap_for(pnuc_ctx *ctx, pnuc_precision precision, const SimParams &p, const pnuc_tuning &t,
+                            bool count, uint64_t n, cudaStream_t s)
+{
+    auto occ_evap = [&](int b) {
+        return precision == PNUC_FP64 ? occupancy_evap_fp64(b) : occupancy_evap_fp32(b, count);
+    };
+    int eblock = t.block_size, occ_e = occ_evap(eblock);
+    while (occ_e < 1 && eblock > 64) occ_e = occ_evap(eblock /= 2);
+    const long long want = (long long)t.blocks_per_sm * t.block_size / eblock;
+    unsigned long long egrid =
+        (unsigned long long)std::max<long long>(std::min<long long>(want, occ_e), 1) * ctx->sm_count;
+    const unsigned long long eneed = (n + eblock - 1) / eblock;
+    if (egrid > eneed) egrid = eneed;
+    return precision == PNUC_FP64 ? launch_evap_fp64(p, (int)egrid, eblock, s)
+                                  : launch_evap_fp32(p, (int)egrid, eblock, count, s);
+}
 
 pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
                          const pnuc_output *out, cudaStream_t s, const pnuc_tuning &t, unsigned long long *queue_head)
@@ -135,6 +156,36 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
                                    : launch_plain_fp32(p, t.block_size, count, s);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
         if (ev) ctx->tev_two[ctx->tev_used / 3 - 1] = 0;
+    } else if (method == PNUC_SORTED) {
+        int occ = precision == PNUC_FP64 ? occupancy_sorted_fp64(t.block_size)
+                                         : occupancy_sorted_fp32(t.block_size, count);
+        if (occ < 1) return fail(ctx, PNUC_ERR_ARG, "sorted method: block size %d does not fit an SM", t.block_size);
+        int bps = std::min(t.blocks_per_sm, occ);
+        unsigned long long grid = (unsigned long long)bps * ctx->sm_count;
+        unsigned long long need = (batch->n + t.block_size - 1) / t.block_size;
+        if (grid > need) grid = need;
+        const size_t per_slot = precision == PNUC_FP64 ? sorted_stack_bytes_fp64() : sorted_stack_bytes_fp32();
+        const size_t bytes = (size_t)grid * t.block_size * per_slot;
+        if (bytes > ctx->sorted_stacks_bytes) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+                return fail(ctx, PNUC_ERR_STATE, "sorted method: run one launch of this size before capturing it");
+            const size_t want = (size_t)std::max(occ, t.blocks_per_sm) * ctx->sm_count * t.block_size * per_slot;
+            CU(ctx, cudaStreamSynchronize(s));
+            cudaFree(ctx->sorted_stacks);
+            ctx->sorted_stacks = nullptr;
+            ctx->sorted_stacks_bytes = 0;
+            CU(ctx, cudaMalloc(&ctx->sorted_stacks, std::max(want, bytes)));
+            ctx->sorted_stacks_bytes = std::max(want, bytes);
+        }
+        p.queue_head = queue_head ? queue_head : ctx->queue + (size_t)(ctx->queue_next++ % kQueueSlots) * kQueueStride;
+        p.evap_head = p.queue_head + 1;
+        p.split_evap = 1;
+        CU(ctx, cudaMemsetAsync(p.queue_head, 0, 2 * sizeof(unsigned long long), s));
+        e = precision == PNUC_FP64 ? launch_sorted_fp64(p, ctx->sorted_stacks, (int)grid, t.block_size, s)
+                                   : launch_sorted_fp32(p, ctx->sorted_stacks, (int)grid, t.block_size, count, s);
+        if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+        e = e == cudaSuccess ? launch_evap_for(ctx, precision, p, t, count, batch->n, s) : e;
     } else {
         int occ = occupancy(precision, t.block_size, count);
         int bps = std::min(t.blocks_per_sm, std::max(occ, 1));
@@ -149,21 +200,7 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
         e = precision == PNUC_FP64 ? launch_persistent_fp64(p, (int)grid, t.block_size, s)
                                    : launch_persistent_fp32(p, (int)grid, t.block_size, count, s);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
-        // the evaporation kernel's own resident grid (it uses more registers, and its
-        // shared-memory job lists can make the block size too large: then it halves)
-        auto occ_evap = [&](int b) {
-            return precision == PNUC_FP64 ? occupancy_evap_fp64(b) : occupancy_evap_fp32(b, count);
-        };
-        int eblock = t.block_size, occ_e = occ_evap(eblock);
-        while (occ_e < 1 && eblock > 64) occ_e = occ_evap(eblock /= 2);
-        const long long want = (long long)t.blocks_per_sm * t.block_size / eblock;
-        unsigned long long egrid = (unsigned long long)std::max<long long>(std::min<long long>(want, occ_e), 1) *
-                                   ctx->sm_count;
-        const unsigned long long eneed = (batch->n + eblock - 1) / eblock;
-        if (egrid > eneed) egrid = eneed;
-        if (e == cudaSuccess)
-            e = precision == PNUC_FP64 ? launch_evap_fp64(p, (int)egrid, eblock, s)
-                                       : launch_evap_fp32(p, (int)egrid, eblock, count, s);
+        e = e == cudaSuccess ? launch_evap_for(ctx, precision, p, t, count, batch->n, s) : e;
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     if (e != cudaSuccess && ev) ctx->tev_used -= 3;  // the slot is the last one taken
@@ -272,6 +309,7 @@ pnuc_status pnuc_destroy(pnuc_ctx *ctx)
     cudaFree(ctx->h_sec);
     cudaFree(ctx->h_count);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
+    cudaFree(ctx->sorted_stacks);
     delete ctx;
     return PNUC_OK;
 }
@@ -424,6 +462,7 @@ pnuc_status pnuc_simulate_host_noalloc(pnuc_ctx *ctx, pnuc_precision precision, 
     if (!ctx || !sec_count) return fail(ctx, PNUC_ERR_ARG, "null argument");
     if (n > 0 && (!energies || !target_ids || !residuals)) return fail(ctx, PNUC_ERR_ARG, "null input/output");
     if (sec_capacity > 0 && !secondaries) return fail(ctx, PNUC_ERR_ARG, "null secondaries with capacity > 0");
+    if (method == PNUC_SORTED) return fail(ctx, PNUC_ERR_ARG, "the sorted method needs a context buffer");
     // scratch layout: [queue head | count], energies, target ids, residuals, secondaries
     const size_t off_e = 256;
     const size_t off_t = off_e + round256(sizeof(double) * n);

@@ -34,6 +34,9 @@ struct pnuc_ctx {
     pnuc_secondary *h_sec = nullptr;
     uint64_t h_sec_cap = 0;
     unsigned long long *h_count = nullptr;
+    // sorted method: particle stacks of every resident slot (grown as needed)
+    void *sorted_stacks = nullptr;
+    size_t sorted_stacks_bytes = 0;
     // pnuc_kernel_timing: three events per recorded launch
     bool timing = false;
     std::vector<cudaEvent_t> tev;

@@ -25,6 +25,16 @@ cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count
 {
     return count ? dev::launch_evap<float, true>(p, grid, block, s) : dev::launch_evap<float, false>(p, grid, block, s);
 }
+cudaError_t launch_sorted_fp32(const SimParams &p, void *stacks, int grid, int block, bool count, cudaStream_t s)
+{
+    return count ? dev::launch_sorted<float, true>(p, stacks, grid, block, s)
+                 : dev::launch_sorted<float, false>(p, stacks, grid, block, s);
+}
+int occupancy_sorted_fp32(int block, bool count)
+{
+    return count ? dev::occupancy_sorted<float, true>(block) : dev::occupancy_sorted<float, false>(block);
+}
+size_t sorted_stack_bytes_fp32() { return sizeof(dev::Particle<float>) * kStackCap; }
 int occupancy_evap_fp32(int block, bool count)
 {
     return count ? dev::occupancy_evap<float, true>(block) : dev::occupancy_evap<float, false>(block);

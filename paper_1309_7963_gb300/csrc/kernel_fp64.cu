@@ -19,5 +19,11 @@ cudaError_t launch_evap_fp64(const SimParams &p, int grid, int block, cudaStream
 }
 int occupancy_persistent_fp64(int block) { return dev::occupancy_persistent<double, true>(block); }
 int occupancy_evap_fp64(int block) { return dev::occupancy_evap<double, true>(block); }
+cudaError_t launch_sorted_fp64(const SimParams &p, void *stacks, int grid, int block, cudaStream_t s)
+{
+    return dev::launch_sorted<double, true>(p, stacks, grid, block, s);
+}
+int occupancy_sorted_fp64(int block) { return dev::occupancy_sorted<double, true>(block); }
+size_t sorted_stack_bytes_fp64() { return sizeof(dev::Particle<double>) * kStackCap; }
 
 }  // namespace pnuc

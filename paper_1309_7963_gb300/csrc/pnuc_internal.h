@@ -78,6 +78,14 @@ int occupancy_persistent_fp64(int block);
 int occupancy_persistent_fp32(int block, bool count);
 int occupancy_evap_fp64(int block);
 int occupancy_evap_fp32(int block, bool count);
+// Sorted method (cascade kernel regrouping slots by action): launchers, resident blocks per
+// SM, and the bytes of one slot's particle stack (the stacks live in a context buffer).
+cudaError_t launch_sorted_fp64(const SimParams &p, void *stacks, int grid, int block, cudaStream_t s);
+cudaError_t launch_sorted_fp32(const SimParams &p, void *stacks, int grid, int block, bool count, cudaStream_t s);
+int occupancy_sorted_fp64(int block);
+int occupancy_sorted_fp32(int block, bool count);
+size_t sorted_stack_bytes_fp64();
+size_t sorted_stack_bytes_fp32();
 
 // Pipe microbenchmarks (microbench.cu): FP32 FMA, FP64 FMA, MUFU, INT32 MAD lane ops/s.
 cudaError_t measure_peaks(int sm_count, double out[4]);

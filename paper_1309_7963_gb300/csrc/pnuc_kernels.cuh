@@ -291,6 +291,132 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
     flush_counters<kCount>(P, cnt);
 }
 
+// ------------------------------------------------------------------ sorted method
+// The block holds blockDim.x events in flight ("slots"), their lane state in shared memory.
+// Every iteration each busy slot takes one action (an entry, a transport step, its collision
+// kinematics), with its draw ring topped up first if it runs short; the block counts the
+// slots by (action, top-up) and its threads take them in that order, so that each warp runs
+// one action, and the Philox blocks, with all its lanes. Candidate tests stay inside the
+// transport step; accepted collisions wait one iteration and then run together, whatever
+// warp their slots started in.
+enum SortKey : int { kNoKey = -1, kKeyEntry = 0, kKeyTransport = 2, kKeyKin = 4, kKeys = 6 };
+
+template <typename R>
+__host__ __device__ constexpr size_t slot_bytes()
+{
+    // 16-byte units, an odd number of them (conflict-free 16-byte loads of neighbouring slots)
+    return (((sizeof(Lane<R>) + 15) / 16) | 1) * 16;
+}
+
+template <typename R>
+__host__ __device__ constexpr size_t sorted_smem_bytes(int n_targets, int block)
+{
+    return smem_bytes<R>(n_targets, block) + (size_t)block * slot_bytes<R>();
+}
+
+template <typename R, bool kCount>
+__device__ __forceinline__ void sorted_body(const SimParams &P, Particle<R> *stacks)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long cnt[PNUC_N_COUNTERS];
+    __shared__ int order[512];
+    __shared__ int key_count[kKeys], key_fill[kKeys], key_off[kKeys + 1];
+    __shared__ unsigned long long s_base;
+    __shared__ int s_rank, s_drained;
+    ShellTable<R> *sh = reinterpret_cast<ShellTable<R> *>(smem);
+    TargetScalars *ts = reinterpret_cast<TargetScalars *>(smem + P.n_targets * sizeof(ShellTable<R>));
+    stage_tables<R>(P, sh, ts);
+    if (kCount)
+        for (int k = threadIdx.x; k < PNUC_N_COUNTERS; k += blockDim.x) cnt[k] = 0;
+    unsigned char *slot_base = smem + smem_bytes<R>(P.n_targets, blockDim.x);
+    const int me = threadIdx.x;
+    {
+        Lane<R> &L0 = *reinterpret_cast<Lane<R> *>(slot_base + (size_t)me * slot_bytes<R>());
+        L0.phase = kIdle;
+        L0.rng.reset(0, 0);
+        L0.rng.buf = ring_base<R>(P, smem);  // slot me's ring column
+        L0.rng.stride = blockDim.x;
+    }
+    if (me == 0) s_drained = 0;
+    __syncthreads();
+    Counters<kCount> C{cnt};
+    Particle<R> *my_stack_base = stacks + (size_t)blockIdx.x * blockDim.x * kStackCap;
+    while (true) {
+        // finished events leave; idle slots take new events (one queue atomic per round)
+        Lane<R> &Lm = *reinterpret_cast<Lane<R> *>(slot_base + (size_t)me * slot_bytes<R>());
+        if (Lm.phase == kFinish) {
+            finish_event<R, kCount>(P, Lm, C);
+            Lm.phase = kIdle;
+        }
+        const bool idle = Lm.phase == kIdle;
+        const int nidle = __syncthreads_count(idle);
+        const int nbusy = __syncthreads_count(Lm.phase == kEntry || Lm.phase == kTransport || Lm.phase == kKinWait);
+        if (nidle && (nidle >= P.refill_threshold || nbusy == 0) && !s_drained) {
+            if (me == 0) {
+                s_base = atomicAdd(P.queue_head, (unsigned long long)nidle);
+                s_rank = 0;
+            }
+            __syncthreads();
+            if (idle) {
+                const unsigned long long ev = s_base + (unsigned long long)atomicAdd(&s_rank, 1);
+                if (ev < P.n) begin_event<R>(P, ts, Lm, (uint32_t)ev);
+                else Lm.phase = kExhausted;
+            }
+            __syncthreads();
+            if (me == 0 && s_base + nidle >= P.n) s_drained = 1;
+        } else if (s_drained && idle) {
+            Lm.phase = kExhausted;
+        }
+        if (__syncthreads_and(Lm.phase == kExhausted || Lm.phase == kIdle) &&
+            __syncthreads_and(Lm.phase == kExhausted || s_drained))
+            break;
+        // sort the busy slots by (action, top-up)
+        int key = kNoKey;
+        if (Lm.phase == kEntry) key = kKeyEntry;
+        else if (Lm.phase == kTransport) key = kKeyTransport;
+        else if (Lm.phase == kKinWait) key = kKeyKin;
+        if (key != kNoKey && Lm.rng.left < 8) key += 1;
+        if (me < kKeys) {
+            key_count[me] = 0;
+            key_fill[me] = 0;
+        }
+        __syncthreads();
+        if (key != kNoKey) atomicAdd(&key_count[key], 1);
+        __syncthreads();
+        if (me == 0) {
+            int o = 0;
+            for (int k = 0; k < kKeys; ++k) {
+                key_off[k] = o;
+                o += key_count[k];
+            }
+            key_off[kKeys] = o;
+        }
+        __syncthreads();
+        if (key != kNoKey) order[key_off[key] + atomicAdd(&key_fill[key], 1)] = me;
+        __syncthreads();
+        // each thread takes one slot of the sorted list
+        if (me < key_off[kKeys]) {
+            const int slot = order[me];
+            Lane<R> *lp = reinterpret_cast<Lane<R> *>(slot_base + (size_t)slot * slot_bytes<R>());
+            Lane<R> L = *lp;
+            Particle<R> *stack = my_stack_base + (size_t)slot * kStackCap;
+            if (L.rng.left < 8) L.rng.ensure(8);
+            if (L.phase == kKinWait) finish_collision<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+            else if (L.phase == kTransport) step_transport<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+            else if (L.phase == kEntry) step_entry<R, kCount>(P, sh[L.tgt], ts[L.tgt].R, L, C);
+            *lp = L;
+        }
+        __syncthreads();
+    }
+    flush_counters<kCount>(P, cnt);
+}
+
+template <typename R, bool kCount>
+__global__ void __launch_bounds__(512) sorted_kernel(const SimParams P, Particle<R> *stacks)
+{
+    sorted_body<R, kCount>(P, stacks);
+}
+
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes)
 {
@@ -344,6 +470,17 @@ cudaError_t launch_persistent(const SimParams &p, int grid, int block, cudaStrea
     return cudaGetLastError();
 }
 
+template <typename R, bool kCount>
+cudaError_t launch_sorted(const SimParams &p, void *stacks, int grid, int block, cudaStream_t s)
+{
+    if (p.n == 0) return cudaSuccess;
+    size_t smem = sorted_smem_bytes<R>(p.n_targets, block);
+    cudaError_t e = allow_smem(sorted_kernel<R, kCount>, smem);
+    if (e != cudaSuccess) return e;
+    sorted_kernel<R, kCount><<<grid, block, smem, s>>>(p, static_cast<Particle<R> *>(stacks));
+    return cudaGetLastError();
+}
+
 template <typename K>
 cudaError_t launch_kernel(K kernel, size_t smem, const SimParams &p, int grid, int block, cudaStream_t s)
 {
@@ -361,6 +498,12 @@ int occupancy_of(K kernel, size_t smem, int block)
     allow_smem(kernel, smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem);
     return nb;
+}
+
+template <typename R, bool kCount>
+int occupancy_sorted(int block)
+{
+    return occupancy_of(sorted_kernel<R, kCount>, sorted_smem_bytes<R>(kMaxTargets, block), block);
 }
 
 template <typename R, bool kCount>

@@ -16,6 +16,7 @@ namespace {
 
 constexpr int kTallyBlock = 256;
 constexpr int kSmemBins = 12288;  // 32-bit shared counters per block (48 KB)
+constexpr int kUnroll = 4;        // records in flight per thread
 
 __device__ __forceinline__ void add_cell(unsigned long long *hist, int idx)
 {
@@ -24,34 +25,66 @@ __device__ __forceinline__ void add_cell(unsigned long long *hist, int idx)
     if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[idx], (unsigned long long)__popc(peers));
 }
 
+__device__ __forceinline__ void add_cell_shared(unsigned int *cells, int idx)
+{
+    // the same for shared counters: most records fall in a few low-energy bins, and lanes
+    // adding to one address would otherwise serialise
+    const unsigned peers = __match_any_sync(__activemask(), idx);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cells[idx], (unsigned int)__popc(peers));
+}
+
 __global__ void __launch_bounds__(kTallyBlock)
     secondary_tally_kernel(const uint4 *__restrict__ rec, uint64_t n, double T_min, double sT, int nT, double hc,
                            int ncos, unsigned long long *hist, int nbins)
 {
+    // shared counters: one copy per warp when they fit (the low-energy evaporation bins
+    // take most records, so per-warp copies spread the contention), else one per block
     extern __shared__ unsigned int cells[];
     const bool priv = nbins <= kSmemBins;
+    const int copies = priv && nbins * (kTallyBlock / 32) <= kSmemBins ? kTallyBlock / 32 : 1;
+    const int total = priv ? nbins * copies : 0;
     if (priv) {
-        for (int i = threadIdx.x; i < nbins; i += blockDim.x) cells[i] = 0u;
+        for (int i = threadIdx.x; i < total; i += blockDim.x) cells[i] = 0u;
         __syncthreads();
     }
+    unsigned int *mine = cells + (copies > 1 ? (int)(threadIdx.x >> 5) * nbins : 0);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint4 a = __ldcs(rec + 2 * i), b = __ldcs(rec + 2 * i + 1);
-        const unsigned sp = a.y & 0xffu, org = (a.y >> 8) & 0xffu;
-        const double T = __hiloint2double((int)a.w, (int)a.z);
-        const double t = __dmul_rn(__dsub_rn(T, T_min), sT);
-        if (!(t >= 0.0 && t < (double)nT) || sp > 5u || org > 1u) continue;
-        const double c = __dmul_rn((double)__uint_as_float(b.z) + 1.0, hc);
-        int ic = c > 0.0 ? (int)c : 0;
-        if (ic > ncos - 1) ic = ncos - 1;
-        const int idx = (((int)org * 6 + (int)sp) * ncos + ic) * nT + (int)t;
-        if (priv) atomicAdd(&cells[idx], 1u);
-        else add_cell(hist, idx);
+    // four records in flight per thread: the loads of a group are issued together
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kUnroll * stride) {
+        uint4 ra[kUnroll], rb[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint64_t i = i0 + u * stride;
+            if (i < n) {
+                ra[u] = __ldcs(rec + 2 * i);
+                rb[u] = __ldcs(rec + 2 * i + 1);
+            } else {
+                ra[u] = make_uint4(0u, 0xffu, 0u, 0u);  // species 255: skipped below
+                rb[u] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const uint4 a = ra[u], b = rb[u];
+            const unsigned sp = a.y & 0xffu, org = (a.y >> 8) & 0xffu;
+            const double T = __hiloint2double((int)a.w, (int)a.z);
+            const double t = __dmul_rn(__dsub_rn(T, T_min), sT);
+            if (!(t >= 0.0 && t < (double)nT) || sp > 5u || org > 1u) continue;
+            const double c = __dmul_rn((double)__uint_as_float(b.z) + 1.0, hc);
+            int ic = c > 0.0 ? (int)c : 0;
+            if (ic > ncos - 1) ic = ncos - 1;
+            const int idx = (((int)org * 6 + (int)sp) * ncos + ic) * nT + (int)t;
+            if (priv) add_cell_shared(mine, idx);
+            else add_cell(hist, idx);
+        }
     }
     if (priv) {
         __syncthreads();
-        for (int i = threadIdx.x; i < nbins; i += blockDim.x)
-            if (cells[i]) atomicAdd(&hist[i], (unsigned long long)cells[i]);
+        for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
+            unsigned long long c = 0;
+            for (int k = 0; k < copies; ++k) c += cells[k * nbins + i];
+            if (c) atomicAdd(&hist[i], c);
+        }
     }
 }
 
@@ -66,15 +99,32 @@ __global__ void __launch_bounds__(kTallyBlock)
         __syncthreads();
     }
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const uint4 a = __ldcs(res + 4 * i), b = __ldcs(res + 4 * i + 1);  // Z/A fields, then flags
-        if (b.x & (PNUC_FLAG_BAD_INPUT | PNUC_FLAG_ATTEMPT_CAP)) continue;
-        const double e = __dmul_rn(__dsub_rn(__ldcs(energies + i), E_min), sE);
-        const int Z = (int)(a.y & 0xffffu), A = (int)(a.y >> 16);
-        if (!(e >= 0.0 && e < (double)nE) || Z > Zmax || A > Amax) continue;
-        const int idx = ((int)e * (Zmax + 1) + Z) * (Amax + 1) + A;
-        if (priv) atomicAdd(&cells[idx], 1u);
-        else add_cell(hist, idx);
+    for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kUnroll * stride) {
+        uint4 ra[kUnroll], rb[kUnroll];
+        double re[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {  // the Z/A fields, the flags, the energy
+            const uint64_t i = i0 + u * stride;
+            if (i < n) {
+                ra[u] = __ldcs(res + 4 * i);
+                rb[u] = __ldcs(res + 4 * i + 1);
+                re[u] = __ldcs(energies + i);
+            } else {
+                ra[u] = make_uint4(0u, 0u, 0u, 0u);
+                rb[u] = make_uint4(PNUC_FLAG_BAD_INPUT, 0u, 0u, 0u);  // skipped below
+                re[u] = 0.0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (rb[u].x & (PNUC_FLAG_BAD_INPUT | PNUC_FLAG_ATTEMPT_CAP)) continue;
+            const double e = __dmul_rn(__dsub_rn(re[u], E_min), sE);
+            const int Z = (int)(ra[u].y & 0xffffu), A = (int)(ra[u].y >> 16);
+            if (!(e >= 0.0 && e < (double)nE) || Z > Zmax || A > Amax) continue;
+            const int idx = ((int)e * (Zmax + 1) + Z) * (Amax + 1) + A;
+            if (priv) add_cell_shared(cells, idx);
+            else add_cell(hist, idx);
+        }
     }
     if (priv) {
         __syncthreads();
@@ -83,10 +133,12 @@ __global__ void __launch_bounds__(kTallyBlock)
     }
 }
 
+// two resident blocks per SM: enough loads in flight with four records per thread, and few
+// per-block histograms to add up at the end
 int tally_grid(uint64_t n, int sm_count)
 {
     const uint64_t need = (n + kTallyBlock - 1) / kTallyBlock;
-    return (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)sm_count * 8));
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)sm_count * 2));
 }
 
 }  // namespace
@@ -112,7 +164,8 @@ extern "C" pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, co
         if (n_secondaries > 0) {
             const double sT = (double)s.n_T / (s.T_max - s.T_min);
             const double hc = 0.5 * (double)s.n_cos;
-            const size_t smem = cells <= (uint64_t)kSmemBins ? cells * sizeof(unsigned int) : 0;
+            const uint64_t copies = cells * (kTallyBlock / 32) <= (uint64_t)kSmemBins ? kTallyBlock / 32 : 1;
+            const size_t smem = cells <= (uint64_t)kSmemBins ? cells * copies * sizeof(unsigned int) : 0;
             secondary_tally_kernel<<<tally_grid(n_secondaries, ctx->sm_count), kTallyBlock, smem, st>>>(
                 reinterpret_cast<const uint4 *>(secondaries), n_secondaries, s.T_min, sT, s.n_T, hc, s.n_cos,
                 secondary_hist, (int)cells);

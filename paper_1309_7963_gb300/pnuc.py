@@ -32,7 +32,7 @@ COUNTER_NAMES = ("steps", "candidates", "kinematics", "pauli_blocked", "collisio
 FLAGS = dict(bad_input=1, attempt_cap=2, step_cap=4, stack_overflow=8, bad_residual=16, no_excitation=32,
              evap_trial_cap=64, evap_step_cap=128, output_overflow=256)
 PRECISION = {"fp32": 0, "fp64": 1}
-METHOD = {"plain": 0, "persistent": 1}
+METHOD = {"plain": 0, "persistent": 1, "sorted": 2}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of range", 3: "capacity exceeded", 4: "CUDA error",
           5: "timeout", 6: "invalid state"}
 
@@ -269,10 +269,11 @@ class Context:
         return dict(cascade_ms=c.value, evaporation_ms=v.value, launches=n.value)
 
     def tally(self, result: "Result", energies, T_range=(0.0, 250.0), n_T=125, n_cos=1, E_range=(20.0, 250.0),
-              n_E=1, Z_max=100, A_max=250, hists=None, stream=None):
+              n_E=1, Z_max=100, A_max=250, hists=None, stream=None, n_secondaries: int | None = None):
         """pnuc_tally: yield histograms of a batch's results (int64 tensors on the device,
         accumulated into `hists` if given): secondaries [2 origins][6 species][n_cos][n_T] over
-        T_range (MeV), residual nuclei [n_E][Z_max + 1][A_max + 1] over incident E_range."""
+        T_range (MeV), residual nuclei [n_E][Z_max + 1][A_max + 1] over incident E_range.
+        n_secondaries: the batch's record count if known (else it is read from the device)."""
         torch = self._torch
         dev = torch.device("cuda", self.device)
         if hists is None:
@@ -281,7 +282,8 @@ class Context:
         spec = pnuc_tally_spec(n_T, n_cos, T_range[0], T_range[1], n_E, Z_max, E_range[0], E_range[1], A_max, 0)
         n = int(energies.shape[0])
         s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
-        n_sec = min(result.n_secondaries(), int(result.secondaries.shape[0]))
+        n_sec = min(result.n_secondaries() if n_secondaries is None else n_secondaries,
+                    int(result.secondaries.shape[0]))
         self._check(self.lib.pnuc_tally(self.handle, C.byref(spec), _ptr(result.secondaries), n_sec,
                                         _ptr(result.residuals), _ptr(energies), n, _ptr(hists[0]), _ptr(hists[1]),
                                         C.c_void_p(s)))

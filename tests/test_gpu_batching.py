@@ -144,3 +144,24 @@ def test_small_batches_leave_idle_lanes_quiet(ctx):
     torch.cuda.synchronize()
     assert time.perf_counter() - t0 < 5.0
     assert same(results(out), ref)
+
+
+def test_sorted_method_tiny_and_ragged_batches(ctx):
+    """The sorted method on batches smaller than a block, of one event, and ragged against the
+    block size, with per-event parity to the plain kernel; it is refused by the entry point
+    that allocates nothing."""
+    import torch
+    for n in (1, 3, 127, 129, 5000):
+        w = inputs.mixed(n, seed=n)
+        e, t = device_inputs(ctx, w)
+        a = results(ctx.simulate(e, t, seed=n, precision="fp64", method="plain"))
+        b = results(ctx.simulate(e, t, seed=n, precision="fp64", method="sorted"))
+        torch.cuda.synchronize()
+        assert same(a, b), n
+    import ctypes as C
+    e, t = np.full(4, 100.0), np.zeros(4, np.int32)
+    sec, res, cnt = np.empty(64, pnuc.SECONDARY_DTYPE), np.empty(4, pnuc.RESIDUAL_DTYPE), C.c_uint64()
+    st = ctx.lib.pnuc_simulate_host_noalloc(ctx.handle, pnuc.PRECISION["fp32"], pnuc.METHOD["sorted"], e.ctypes.data,
+                                            t.ctypes.data, 4, 1, 0, sec.ctypes.data, 64, C.byref(cnt),
+                                            res.ctypes.data, None)
+    assert st == 1

@@ -73,11 +73,12 @@ def test_fp64_per_event_parity_heavy(ctx, za):
     assert c["max_rel_energy_same"] < 1e-6
 
 
+@pytest.mark.parametrize("method", ["persistent", "sorted"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_persistent_equals_plain_bitwise(ctx, precision):
+def test_batched_methods_equal_plain_bitwise(ctx, precision, method):
     w = inputs.mixed(20_000, seed=11)
     a = run_gpu(ctx, w, precision, "plain")
-    b = run_gpu(ctx, w, precision, "persistent")
+    b = run_gpu(ctx, w, precision, method)
     assert np.array_equal(a.residuals_np(), b.residuals_np())
     sa, sb = pnuc.sort_secondaries(a.secondaries_np()), pnuc.sort_secondaries(b.secondaries_np())
     assert np.array_equal(sa, sb)

@@ -21,7 +21,7 @@ def run(ctx, w, precision):
     return e, r
 
 
-@pytest.mark.parametrize("n_cos,n_T,n_E", [(1, 125, 2), (40, 125, 23)])  # shared-memory, then global cells
+@pytest.mark.parametrize("n_cos,n_T,n_E", [(1, 125, 2), (4, 125, 2), (40, 125, 23)])  # per-warp, per-block, global
 def test_tally_equals_reference_on_the_same_records(ctx, n_cos, n_T, n_E):
     import torch
     w = inputs.mixed(60_000, seed=8)
