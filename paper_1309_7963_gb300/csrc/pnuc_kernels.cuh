@@ -370,11 +370,16 @@ __device__ __forceinline__ void sorted_body(const SimParams &P, Particle<R> *sta
         if (__syncthreads_and(Lm.phase == kExhausted || Lm.phase == kIdle) &&
             __syncthreads_and(Lm.phase == kExhausted || s_drained))
             break;
+        // accepted collisions wait until a full warp of them (or nothing else) is ready, so
+        // that the FP64 kinematics run with all lanes and not in every iteration
+        const int nkin = __syncthreads_count(Lm.phase == kKinWait);
+        const int nrun = __syncthreads_count(Lm.phase == kEntry || Lm.phase == kTransport);
+        const bool kin_now = nkin >= 32 || nrun == 0;
         // sort the busy slots by (action, top-up)
         int key = kNoKey;
         if (Lm.phase == kEntry) key = kKeyEntry;
         else if (Lm.phase == kTransport) key = kKeyTransport;
-        else if (Lm.phase == kKinWait) key = kKeyKin;
+        else if (Lm.phase == kKinWait && kin_now) key = kKeyKin;
         if (key != kNoKey && Lm.rng.left < 8) key += 1;
         if (me < kKeys) {
             key_count[me] = 0;

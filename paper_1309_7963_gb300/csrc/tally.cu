@@ -6,10 +6,13 @@
 // (the residual kernel reads only the first 32 bytes of each 64-byte record), per-block
 // shared-memory histograms when the histogram fits, and warp-aggregated 64-bit atomics
 // (lanes that hit the same cell add once) otherwise. The bin arithmetic is FP64 with
-// explicit round-to-nearest operations, so the host can reproduce every bin index.
+// explicit round-to-nearest operations, so the host can reproduce every bin index; the
+// floors and range tests are taken from the bit fields on the integer pipes.
 #include <algorithm>
+#include <climits>
 
 #include "api_internal.h"
+#include "fpconv.h"
 
 namespace pnuc {
 namespace {
@@ -17,6 +20,20 @@ namespace {
 constexpr int kTallyBlock = 256;
 constexpr int kSmemBins = 12288;  // 32-bit shared counters per block (48 KB)
 constexpr int kUnroll = 4;        // records in flight per thread
+
+// floor(t) from the bit fields of t on the integer pipes (the FP64 pipe, GB300's scarce one,
+// would otherwise take a conversion and two comparisons per record): -1 for t < 0, INT_MAX
+// for t >= 2^31, infinities and NaN; -0 counts as 0.
+__device__ __forceinline__ int floor_bits(double t)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+    if (b >> 63) return (b << 1) == 0ull ? 0 : -1;
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    if (e < 0) return 0;
+    if (e > 30) return INT_MAX;
+    const unsigned long long m = (b & 0xfffffffffffffull) | (1ull << 52);
+    return (int)(m >> (52 - e));
+}
 
 __device__ __forceinline__ void add_cell(unsigned long long *hist, int idx)
 {
@@ -68,12 +85,15 @@ __global__ void __launch_bounds__(kTallyBlock)
             const uint4 a = ra[u], b = rb[u];
             const unsigned sp = a.y & 0xffu, org = (a.y >> 8) & 0xffu;
             const double T = __hiloint2double((int)a.w, (int)a.z);
-            const double t = __dmul_rn(__dsub_rn(T, T_min), sT);
-            if (!(t >= 0.0 && t < (double)nT) || sp > 5u || org > 1u) continue;
-            const double c = __dmul_rn((double)__uint_as_float(b.z) + 1.0, hc);
-            int ic = c > 0.0 ? (int)c : 0;
-            if (ic > ncos - 1) ic = ncos - 1;
-            const int idx = (((int)org * 6 + (int)sp) * ncos + ic) * nT + (int)t;
+            const int iT = floor_bits(__dmul_rn(__dsub_rn(T, T_min), sT));
+            if (iT < 0 || iT >= nT || sp > 5u || org > 1u) continue;
+            int ic = 0;
+            if (ncos > 1) {
+                ic = floor_bits(__dmul_rn(__dadd_rn(f2d(__uint_as_float(b.z)), 1.0), hc));
+                if (ic < 0) ic = 0;
+                if (ic > ncos - 1) ic = ncos - 1;
+            }
+            const int idx = (((int)org * 6 + (int)sp) * ncos + ic) * nT + iT;
             if (priv) add_cell_shared(mine, idx);
             else add_cell(hist, idx);
         }
@@ -118,10 +138,10 @@ __global__ void __launch_bounds__(kTallyBlock)
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             if (rb[u].x & (PNUC_FLAG_BAD_INPUT | PNUC_FLAG_ATTEMPT_CAP)) continue;
-            const double e = __dmul_rn(__dsub_rn(re[u], E_min), sE);
+            const int iE = floor_bits(__dmul_rn(__dsub_rn(re[u], E_min), sE));
             const int Z = (int)(ra[u].y & 0xffffu), A = (int)(ra[u].y >> 16);
-            if (!(e >= 0.0 && e < (double)nE) || Z > Zmax || A > Amax) continue;
-            const int idx = ((int)e * (Zmax + 1) + Z) * (Amax + 1) + A;
+            if (iE < 0 || iE >= nE || Z > Zmax || A > Amax) continue;
+            const int idx = (iE * (Zmax + 1) + Z) * (Amax + 1) + A;
             if (priv) add_cell_shared(cells, idx);
             else add_cell(hist, idx);
         }
