@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -28,10 +29,37 @@ pnuc_status fail(pnuc_ctx *ctx, pnuc_status st, const char *fmt, ...)
 namespace {
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-int occupancy(pnuc_precision prec, int block, bool count)
+// Resident blocks per SM of a kernel kind (0 cascade, 1 evaporation, 2 sorted cascade) for a
+// precision, block size and counting variant. The runtime's occupancy query costs tens of
+// microseconds, which small serving requests feel, so results are kept per process (they
+// depend only on the compiled kernels and the device, one device per process here).
+enum OccKind { kOccCascade = 0, kOccEvap = 1, kOccSorted = 2 };
+
+int occupancy_kind(OccKind kind, pnuc_precision prec, int block, bool count)
 {
-    return prec == PNUC_FP64 ? occupancy_persistent_fp64(block) : occupancy_persistent_fp32(block, count);
+    static std::atomic<int> cache[3][2][4][2];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (auto &a : cache)
+            for (auto &b : a)
+                for (auto &c : b)
+                    for (auto &d : c) d.store(-1);
+    });
+    const int bi = block == 64 ? 0 : block == 128 ? 1 : block == 256 ? 2 : 3;
+    std::atomic<int> &slot = cache[kind][prec == PNUC_FP64 ? 1 : 0][bi][count ? 1 : 0];
+    int v = slot.load();
+    if (v >= 0) return v;
+    if (kind == kOccCascade)
+        v = prec == PNUC_FP64 ? occupancy_persistent_fp64(block) : occupancy_persistent_fp32(block, count);
+    else if (kind == kOccEvap)
+        v = prec == PNUC_FP64 ? occupancy_evap_fp64(block) : occupancy_evap_fp32(block, count);
+    else
+        v = prec == PNUC_FP64 ? occupancy_sorted_fp64(block) : occupancy_sorted_fp32(block, count);
+    slot.store(v);
+    return v;
 }
+
+int occupancy(pnuc_precision prec, int block, bool count) { return occupancy_kind(kOccCascade, prec, block, count); }
 }  // namespace
 
 pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t)
@@ -101,7 +129,7 @@ cudaError_t launch_evap_for(pnuc_ctx *ctx, pnuc_precision precision, const SimPa
                             bool count, uint64_t n, cudaStream_t s)
 {
     auto occ_evap = [&](int b) {
-        return precision == PNUC_FP64 ? occupancy_evap_fp64(b) : occupancy_evap_fp32(b, count);
+        return occupancy_kind(kOccEvap, precision, b, count);
     };
     int eblock = t.block_size, occ_e = occ_evap(eblock);
     while (occ_e < 1 && eblock > 64) occ_e = occ_evap(eblock /= 2);
@@ -157,8 +185,7 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
         if (ev) ctx->tev_two[ctx->tev_used / 3 - 1] = 0;
     } else if (method == PNUC_SORTED) {
-        int occ = precision == PNUC_FP64 ? occupancy_sorted_fp64(t.block_size)
-                                         : occupancy_sorted_fp32(t.block_size, count);
+        int occ = occupancy_kind(kOccSorted, precision, t.block_size, count);
         if (occ < 1) return fail(ctx, PNUC_ERR_ARG, "sorted method: block size %d does not fit an SM", t.block_size);
         int bps = std::min(t.blocks_per_sm, occ);
         unsigned long long grid = (unsigned long long)bps * ctx->sm_count;
