@@ -277,12 +277,14 @@ pnuc_status pnuc_graph_destroy(pnuc_graph *graph);
  * they arise; a scheduler thread admits queued requests in order whenever one of `streams`
  * CUDA streams is free and both the device output arena and a pinned host arena of
  * arena_bytes have room for the request's inputs, residuals and sec_per_event secondaries
- * per event (memory-based admission). Each admitted request is one persistent launch on its
- * own stream, so requests that arrive while others run are admitted as streams and memory
- * free up and their work overlaps on the GPU (continuous batching). A request that produces
- * more secondaries than reserved is run again with room for exactly its count; as results
- * depend only on (seed, event id), every request's results equal those of a lone
- * pnuc_simulate call. Latency is measured from submit to results ready on the host. */
+ * per event (memory-based admission). Queued requests with the same seed are merged, up to
+ * max_merge of them (and 2^22 events), into one persistent launch on a free stream, each
+ * event keeping its own id; a partition kernel then gives every request a contiguous range of
+ * secondaries. Launches on different streams overlap on the GPU (continuous batching). A
+ * request that produces more secondaries than reserved is run again alone, with room for
+ * exactly its count; as results depend only on (seed, event id), every request's results
+ * equal those of a lone pnuc_simulate call. Latency is measured from submit to results ready
+ * on the host. */
 typedef struct {
     int32_t precision;           /* pnuc_precision */
     int32_t streams;             /* requests in flight at once, 1..64 (default 8) */
@@ -290,6 +292,8 @@ typedef struct {
     uint32_t sec_per_event;      /* secondaries reserved per event at admission, 1..256 (default 12) */
     uint32_t max_pending;        /* queued requests before submit refuses (default 4096) */
     uint64_t max_request_events; /* largest request accepted (default 2^24) */
+    uint32_t max_merge;          /* requests merged into one launch, 1..64 (default 32; 1 = never) */
+    uint32_t reserved;
 } pnuc_server_config;
 
 typedef struct {
@@ -298,6 +302,7 @@ typedef struct {
     double queue_p50_ms, queue_p99_ms;                     /* submit -> admission */
     double elapsed_s, events_per_s;                        /* since creation or the last reset */
     uint64_t arena_peak_bytes;
+    uint64_t launches;                                     /* kernel launches (merged groups and re-runs) */
 } pnuc_server_stats;
 
 typedef struct pnuc_server pnuc_server;

@@ -143,7 +143,8 @@ cudaError_t launch_evap_for(pnuc_ctx *ctx, pnuc_precision precision, const SimPa
 }
 
 pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
-                         const pnuc_output *out, cudaStream_t s, const pnuc_tuning &t, unsigned long long *queue_head)
+                         const pnuc_output *out, cudaStream_t s, const pnuc_tuning &t, unsigned long long *queue_head,
+                         const Segments &seg)
 {
     CU(ctx, cudaSetDevice(ctx->cfg.device));
     CU(ctx, cudaMemsetAsync(out->count, 0, sizeof(unsigned long long), s));
@@ -152,6 +153,9 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
     p.energies = batch->energies;
     p.target_ids = batch->target_ids;
     p.projectiles = batch->projectiles;
+    p.seg_first = seg.first;
+    p.seg_start = seg.start;
+    p.n_seg = seg.n;
     p.n = batch->n;
     p.seed = batch->seed;
     p.first_event_id = batch->first_event_id;

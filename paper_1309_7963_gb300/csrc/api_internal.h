@@ -59,11 +59,18 @@ pnuc_status fail(pnuc_ctx *ctx, pnuc_status st, const char *fmt, ...);
 pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t);
 pnuc_status check_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
                         const pnuc_output *out);
+// Merged requests of one launch (device arrays; the fields of the same names in SimParams).
+struct Segments {
+    const unsigned long long *first = nullptr;
+    const uint32_t *start = nullptr;
+    int n = 0;
+};
+
 // Enqueues the count reset, the queue-head reset and the kernel of one batch on stream s
 // with tuning t. queue_head: the persistent kernel's queue head, or null for the next slot of
-// the context's ring.
+// the context's ring. seg: merged requests, if any.
 pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
                          const pnuc_output *out, cudaStream_t s, const pnuc_tuning &t,
-                         unsigned long long *queue_head);
+                         unsigned long long *queue_head, const Segments &seg = Segments());
 
 }  // namespace pnuc

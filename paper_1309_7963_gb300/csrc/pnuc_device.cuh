@@ -452,12 +452,26 @@ __device__ void write_residual(const SimParams &P, const Lane<R> &L)
     for (int k = 0; k < 4; ++k) dst[k] = src[k];
 }
 
+// Id of event ev of the launch: its position in its segment plus the segment's first id
+// (merged serving requests), else first_event_id + ev.
+__device__ __forceinline__ unsigned long long event_id(const SimParams &P, uint32_t ev)
+{
+    if (P.n_seg <= 0) return P.first_event_id + ev;
+    int lo = 0, hi = P.n_seg - 1;  // the last segment k with seg_start[k] <= ev
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&P.seg_start[mid]) <= ev) lo = mid;
+        else hi = mid - 1;
+    }
+    return __ldg(&P.seg_first[lo]) + (ev - __ldg(&P.seg_start[lo]));
+}
+
 // Starts event ev in lane L (reads its energy and target id).
 template <typename R>
 __device__ void begin_event(const SimParams &P, const TargetScalars *tabs, Lane<R> &L, uint32_t ev)
 {
     L.ev = ev;
-    L.rng.reset(P.seed, P.first_event_id + ev);
+    L.rng.reset(P.seed, event_id(P, ev));
     L.T0 = __ldg(&P.energies[ev]);
     L.tgt = __ldg(&P.target_ids[ev]);
     L.proj = P.projectiles ? (int)__ldg(&P.projectiles[ev]) : 1;
@@ -597,7 +611,7 @@ __device__ void begin_evap(const SimParams &P, Lane<R> &L, uint32_t ev)
     L.T0 = __ldg(&P.energies[ev]);
     const int tgt = __ldg(&P.target_ids[ev]);
     L.proj = P.projectiles ? (int)__ldg(&P.projectiles[ev]) : 1;
-    L.rng.reset(P.seed, P.first_event_id + ev);
+    L.rng.reset(P.seed, event_id(P, ev));
     L.rng.seek(o.reserved - 1u);
     if (tgt < 0 || tgt >= P.n_targets) {  // cannot happen: the cascade checked it
         L.flags |= PNUC_FLAG_BAD_INPUT;

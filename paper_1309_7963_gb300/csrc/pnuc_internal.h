@@ -46,6 +46,11 @@ struct SimParams {
     const double *energies;
     const int32_t *target_ids;
     const uint8_t *projectiles;      // per event 1 proton, 0 neutron; null = all protons
+    // merged requests (serving): event i of segment k (seg_start[k] <= i < seg_start[k+1]) has
+    // id seg_first[k] + i - seg_start[k]; n_seg = 0: id first_event_id + i
+    const unsigned long long *seg_first;
+    const uint32_t *seg_start;
+    int32_t n_seg;
     uint64_t n;
     uint64_t seed;
     uint64_t first_event_id;

@@ -1,10 +1,13 @@
-// Serving loop (host code): continuous batching of interaction requests from a transport
-// driver. Requests are queued on submit; a scheduler thread admits them in order whenever a
-// stream is free and both the device output arena and the pinned host arena have room for
-// the request (memory-based admission). Every admitted request is one persistent-kernel
-// launch on its own stream, so requests that arrive while others run overlap on the GPU.
-// A request whose secondaries overflow its reservation is run again with room for exactly
-// its count: results depend only on (seed, event id), so the re-run is identical.
+// Serving loop (host code, plus the partition kernel of merged launches): continuous batching
+// of interaction requests from a transport driver. Requests are queued on submit; a scheduler
+// thread admits them in order whenever a stream is free and both the device arena and the
+// pinned host arena have room (memory-based admission). Queued requests with the same seed
+// are merged into one persistent launch ("group"), each event keeping its own id, so that
+// many small requests share one launch instead of each paying the tail of its slowest event;
+// a partition kernel then gives every request of the group its own contiguous range of
+// secondaries, renumbered to its own events. A request whose secondaries overflow its
+// reservation is run again alone with room for exactly its count: results depend only on
+// (seed, event id), so the re-run is identical.
 #include <string.h>
 
 #include <algorithm>
@@ -24,6 +27,9 @@ using namespace pnuc;
 using Clock = std::chrono::steady_clock;
 
 namespace {
+
+constexpr int kMaxSeg = 64;                   // requests per group
+constexpr uint64_t kMaxGroupEvents = 1u << 22;  // events per group
 
 // First-fit allocator over [0, size) with 256-byte granules.
 class Arena {
@@ -62,7 +68,6 @@ class Arena {
             }
         }
     }
-    size_t size() const { return size_; }
     size_t peak() const { return peak_; }
 
   private:
@@ -77,29 +82,83 @@ struct Request {
     std::vector<double> e;
     std::vector<int32_t> t;
     uint64_t cap = 0;  // secondaries reserved
+    bool solo = false; // run alone (after an overflow)
     State state = kPending;
     pnuc_status status = PNUC_OK;
-    int stream = -1;
-    size_t dev_off = 0, host_off = 0, bytes = 0;
-    bool has_dev = false, has_host = false;
+    uint64_t group = 0;  // its group while running or until released
     unsigned long long count = 0;
+    const pnuc_residual *res_view = nullptr;   // results in the group's host region
+    const pnuc_secondary *sec_view = nullptr;
     int reruns = 0;
     Clock::time_point t_submit, t_admit, t_done;
 };
 
-// byte offsets inside one reservation
-struct Layout {
-    size_t count = 0, e, t, r, s, total;
-    Layout(uint64_t n, uint64_t cap)
+auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+
+// Byte offsets of one group in the arenas. Device: header, inputs, residuals, the launch's
+// secondaries, and (for more than one request) the partitioned copy; host: header,
+// residuals, the partitioned secondaries (or the launch's for a single request).
+struct GroupLayout {
+    // header: [0] launch count, [8 .. 8+8*kMaxSeg) per-request counts (device -> host), then
+    // the segment tables (host -> device): seg_start (u32, kMaxSeg + 1), seg_first (u64,
+    // kMaxSeg), cap_start (u64, kMaxSeg + 1)
+    static constexpr size_t count = 0, seg_count = 8, seg_start = 8 + 8 * kMaxSeg, seg_first = 1024,
+                            cap_start = seg_first + 8 * kMaxSeg, header = 2304;
+    static_assert(seg_start + 4 * (kMaxSeg + 1) <= seg_first && cap_start + 8 * (kMaxSeg + 1) <= header,
+                  "group header fields overlap");
+    size_t e, t, r, s, p, dev_total, host_r, host_s, host_total;
+    GroupLayout(uint64_t n, uint64_t cap, int n_seg)
     {
-        auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-        e = 256;
+        e = header;
         t = e + up(8 * n);
         r = t + up(4 * n);
         s = r + up(sizeof(pnuc_residual) * n);
-        total = s + up(sizeof(pnuc_secondary) * cap);
+        p = s + up(sizeof(pnuc_secondary) * cap);
+        dev_total = n_seg > 1 ? p + up(sizeof(pnuc_secondary) * cap) : p;
+        host_r = header;
+        host_s = host_r + up(sizeof(pnuc_residual) * n);
+        host_total = host_s + up(sizeof(pnuc_secondary) * cap);
     }
 };
+
+struct Group {
+    uint64_t id;
+    std::vector<uint64_t> tickets;  // segment order
+    uint64_t n = 0, cap = 0;
+    size_t dev_off = 0, host_off = 0, dev_bytes = 0, host_bytes = 0;
+    bool has_dev = false;
+    int stream = -1;
+    int live = 0;  // requests not yet released: the host region is freed at 0
+};
+
+// Partition of a merged launch's secondaries: record i of event e (segment k) goes to
+// out[cap_start[k] + (its rank in segment k)], with its event renumbered e - seg_start[k].
+// Ranks come from atomics on the per-segment counts, which also report overflows.
+__global__ void partition_kernel(const uint4 *__restrict__ in, const unsigned long long *launch_count,
+                                 uint64_t cap, const uint32_t *__restrict__ seg_start,
+                                 const unsigned long long *__restrict__ cap_start, int n_seg,
+                                 unsigned long long *seg_count, uint4 *out)
+{
+    const unsigned long long n = min(*launch_count, (unsigned long long)cap);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        uint4 a = in[2 * i];
+        const uint4 b = in[2 * i + 1];
+        const uint32_t ev = a.x;
+        int lo = 0, hi = n_seg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (seg_start[mid] <= ev) lo = mid;
+            else hi = mid - 1;
+        }
+        const unsigned long long rank = atomicAdd(&seg_count[lo], 1ull);
+        if (rank < cap_start[lo + 1] - cap_start[lo]) {
+            a.x = ev - seg_start[lo];
+            out[2 * (cap_start[lo] + rank)] = a;
+            out[2 * (cap_start[lo] + rank) + 1] = b;
+        }
+    }
+}
 
 }  // namespace
 
@@ -111,38 +170,45 @@ struct pnuc_server {
     std::unique_ptr<Arena> dev_arena, host_arena;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
-    std::vector<uint64_t> stream_owner;  // ticket of the request on each stream, 0 if free
+    std::vector<uint64_t> stream_owner;  // group on each stream, 0 if free
     std::mutex mu;
     std::condition_variable cv;
     std::deque<uint64_t> pending;
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
-    uint64_t next_ticket = 1;
+    std::unordered_map<uint64_t, std::unique_ptr<Group>> groups;
+    uint64_t next_ticket = 1, next_group = 1;
     bool stop = false;
     std::thread worker;
     // statistics
     std::vector<double> latencies_ms, queue_ms;
-    uint64_t completed = 0, events_done = 0, failed = 0, reruns = 0;
+    uint64_t completed = 0, events_done = 0, failed = 0, reruns = 0, launches = 0;
     Clock::time_point t_start;
-    char err[256] = {0};
 };
 
 namespace {
+
+// Drops a request's claim on its group; frees the group's host region when none is left.
+void leave_group(pnuc_server *S, Request &r)
+{
+    if (!r.group) return;
+    auto it = S->groups.find(r.group);
+    r.group = 0;
+    r.res_view = nullptr;
+    r.sec_view = nullptr;
+    if (it == S->groups.end()) return;
+    Group &g = *it->second;
+    if (--g.live == 0) {
+        if (g.has_dev) S->dev_arena->release(g.dev_off, g.dev_bytes);
+        S->host_arena->release(g.host_off, g.host_bytes);
+        S->groups.erase(it);
+    }
+}
 
 void finish(pnuc_server *S, Request &r, State st, pnuc_status status)
 {
     r.state = st;
     r.status = status;
     r.t_done = Clock::now();
-    if (r.has_dev) {
-        S->dev_arena->release(r.dev_off, r.bytes);
-        r.has_dev = false;
-    }
-    if (st == kFailed && r.has_host) {
-        S->host_arena->release(r.host_off, r.bytes);
-        r.has_host = false;
-    }
-    if (r.stream >= 0) S->stream_owner[r.stream] = 0;
-    r.stream = -1;
     if (st == kDone) {
         S->completed++;
         S->events_done += r.n;
@@ -150,11 +216,13 @@ void finish(pnuc_server *S, Request &r, State st, pnuc_status status)
         S->queue_ms.push_back(std::chrono::duration<double, std::milli>(r.t_admit - r.t_submit).count());
     } else {
         S->failed++;
+        leave_group(S, r);
     }
 }
 
-// Tries to admit request r on a free stream; returns false if it must wait.
-bool admit(pnuc_server *S, Request &r)
+// Admits the requests at the front of the queue as one group on a free stream; returns
+// false if it must wait (no stream, or no room for even the first request).
+bool admit(pnuc_server *S)
 {
     int si = -1;
     for (size_t k = 0; k < S->streams.size(); ++k)
@@ -163,81 +231,201 @@ bool admit(pnuc_server *S, Request &r)
             break;
         }
     if (si < 0) return false;
-    Layout L(r.n, r.cap);
-    size_t doff, hoff;
-    if (!S->dev_arena->alloc(L.total, doff)) return false;
-    if (!S->host_arena->alloc(L.total, hoff)) {
-        S->dev_arena->release(doff, L.total);
-        return false;
+    // the candidates: the first pending request, then followers with the same seed
+    std::vector<Request *> cand;
+    uint64_t n = 0, cap = 0;
+    for (uint64_t tk : S->pending) {
+        auto it = S->reqs.find(tk);
+        if (it == S->reqs.end()) break;  // the candidates are the first entries of the queue
+        Request &r = *it->second;
+        if (!cand.empty() && (r.solo || cand[0]->solo || r.seed != cand[0]->seed ||
+                              (int)cand.size() >= std::min<int>(S->cfg.max_merge, kMaxSeg) ||
+                              n + r.n > kMaxGroupEvents))
+            break;
+        cand.push_back(&r);
+        n += r.n;
+        cap += r.cap;
+        if (r.solo) break;
     }
-    r.dev_off = doff;
-    r.host_off = hoff;
-    r.bytes = L.total;
-    r.has_dev = r.has_host = true;
-    r.stream = si;
-    S->stream_owner[si] = r.ticket;
-    if (r.reruns == 0) r.t_admit = Clock::now();
+    if (cand.empty()) return false;
+    // the largest prefix of the candidates that fits both arenas
+    size_t doff = 0, hoff = 0;
+    int k = (int)cand.size();
+    for (; k >= 1; --k) {
+        if (k < (int)cand.size()) {
+            n -= cand[k]->n;
+            cap -= cand[k]->cap;
+        }
+        GroupLayout L(n, cap, k);
+        if (!S->dev_arena->alloc(L.dev_total, doff)) continue;
+        if (!S->host_arena->alloc(L.host_total, hoff)) {
+            S->dev_arena->release(doff, L.dev_total);
+            continue;
+        }
+        break;
+    }
+    if (k < 1) return false;
+    cand.resize(k);
+    std::unique_ptr<Group> g(new Group());
+    g->id = S->next_group++;
+    g->n = n;
+    g->cap = cap;
+    GroupLayout L(n, cap, k);
+    g->dev_off = doff;
+    g->host_off = hoff;
+    g->dev_bytes = L.dev_total;
+    g->host_bytes = L.host_total;
+    g->has_dev = true;
+    g->stream = si;
+    g->live = k;
     unsigned char *d = S->dev + doff, *h = S->host + hoff;
+    // inputs and the segment tables, staged in the pinned arena (the header area of the host
+    // region, then the device region's own input area)
+    uint32_t *h_start = reinterpret_cast<uint32_t *>(h + GroupLayout::seg_start);
+    unsigned long long *h_first = reinterpret_cast<unsigned long long *>(h + GroupLayout::seg_first);
+    unsigned long long *h_cap = reinterpret_cast<unsigned long long *>(h + GroupLayout::cap_start);
+    // the residual area of the host region stages the inputs until the results overwrite it
+    // (in stream order): 12 bytes per event in a 64-byte record
+    unsigned char *h_in = h + L.host_r;
+    uint64_t pos = 0, cpos = 0;
+    for (int j = 0; j < k; ++j) {
+        Request &r = *cand[j];
+        h_start[j] = (uint32_t)pos;
+        h_first[j] = r.first;
+        h_cap[j] = cpos;
+        memcpy(h_in + 8 * pos, r.e.data(), 8 * r.n);
+        memcpy(h_in + 8 * n + 4 * pos, r.t.data(), 4 * r.n);
+        pos += r.n;
+        cpos += r.cap;
+        r.state = kRunning;
+        r.group = g->id;
+        if (r.reruns == 0) r.t_admit = Clock::now();
+        g->tickets.push_back(r.ticket);
+    }
+    h_start[k] = (uint32_t)pos;
+    h_cap[k] = cpos;
+    for (int j = 0; j < k; ++j) S->pending.pop_front();
     cudaStream_t s = S->streams[si];
-    memcpy(h + L.e, r.e.data(), 8 * r.n);
-    memcpy(h + L.t, r.t.data(), 4 * r.n);
-    pnuc_batch b = {(const double *)(d + L.e), (const int32_t *)(d + L.t), r.n, r.seed, r.first};
-    pnuc_output o = {r.cap ? (pnuc_secondary *)(d + L.s) : nullptr, r.cap, (unsigned long long *)(d + L.count),
-                     (pnuc_residual *)(d + L.r), nullptr};
     pnuc_status st = PNUC_OK;
-    if (cudaMemcpyAsync(d + L.e, h + L.e, 8 * r.n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(d + L.t, h + L.t, 4 * r.n, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    static_assert(sizeof(pnuc_residual) >= 12, "inputs are staged in the residual area");
+    if (cudaMemcpyAsync(d + L.e, h_in, 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d + L.t, h_in + 8 * n, 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d + GroupLayout::seg_start, h + GroupLayout::seg_start,
+                        GroupLayout::header - GroupLayout::seg_start, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(d + GroupLayout::seg_count, 0, 8 * kMaxSeg, s) != cudaSuccess)
         st = PNUC_ERR_CUDA;
-    if (st == PNUC_OK) st = launch_batch(S->ctx, (pnuc_precision)S->cfg.precision, PNUC_PERSISTENT, &b, &o, s,
-                                         S->ctx->tuning[S->cfg.precision], nullptr);
-    // the count, the residuals and the whole reservation of secondaries come back in the same
-    // stream order, so one completion event covers them (a count above the reservation
-    // sends the request round again)
+    pnuc_batch b = {(const double *)(d + L.e), (const int32_t *)(d + L.t), n, cand[0]->seed, cand[0]->first};
+    pnuc_output o = {cap ? (pnuc_secondary *)(d + L.s) : nullptr, cap, (unsigned long long *)(d + GroupLayout::count),
+                     (pnuc_residual *)(d + L.r), nullptr};
+    Segments seg;
+    if (k > 1) {
+        seg.first = (const unsigned long long *)(d + GroupLayout::seg_first);
+        seg.start = (const uint32_t *)(d + GroupLayout::seg_start);
+        seg.n = k;
+    }
+    if (st == PNUC_OK)
+        st = launch_batch(S->ctx, (pnuc_precision)S->cfg.precision, PNUC_PERSISTENT, &b, &o, s,
+                          S->ctx->tuning[S->cfg.precision], nullptr, seg);
+    if (st == PNUC_OK && k > 1 && cap) {
+        const int grid = std::max(1, std::min<int>((int)((cap + 255) / 256), S->ctx->sm_count * 4));
+        partition_kernel<<<grid, 256, 0, s>>>(
+            (const uint4 *)(d + L.s), (const unsigned long long *)(d + GroupLayout::count), cap,
+            (const uint32_t *)(d + GroupLayout::seg_start), (const unsigned long long *)(d + GroupLayout::cap_start),
+            k, (unsigned long long *)(d + GroupLayout::seg_count), (uint4 *)(d + L.p));
+        if (cudaGetLastError() != cudaSuccess) st = PNUC_ERR_CUDA;
+    }
+    // counts, residuals and the secondary reservation come back in stream order behind the
+    // kernels, so one completion event covers the whole group
     if (st == PNUC_OK &&
-        (cudaMemcpyAsync(h + L.count, d + L.count, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         cudaMemcpyAsync(h + L.r, d + L.r, sizeof(pnuc_residual) * r.n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         (r.cap && cudaMemcpyAsync(h + L.s, d + L.s, sizeof(pnuc_secondary) * r.cap, cudaMemcpyDeviceToHost, s) !=
-                       cudaSuccess) ||
+        (cudaMemcpyAsync(h, d, GroupLayout::seg_start, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(h + L.host_r, d + L.r, sizeof(pnuc_residual) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         (cap && cudaMemcpyAsync(h + L.host_s, d + (k > 1 ? L.p : L.s), sizeof(pnuc_secondary) * cap,
+                                 cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
          cudaEventRecord(S->events[si], s) != cudaSuccess))
         st = PNUC_ERR_CUDA;
+    S->launches++;
+    const uint64_t gid = g->id;
+    S->groups[gid] = std::move(g);
     if (st != PNUC_OK) {
-        finish(S, r, kFailed, st);
+        // copies may still be in flight into the group's regions: let them end before the
+        // regions go back to the arenas
+        cudaStreamSynchronize(s);
+        for (Request *r : cand) finish(S, *r, kFailed, st);
         return true;
     }
-    r.state = kRunning;
+    S->stream_owner[si] = gid;
     return true;
 }
 
-void poll(pnuc_server *S, Request &r)
+// The group on stream si is complete: hand each request its results, or send overflowing
+// requests round again alone.
+void complete(pnuc_server *S, Group &g)
 {
-    cudaError_t q = cudaEventQuery(S->events[r.stream]);
-    if (q == cudaErrorNotReady) return;
-    if (q != cudaSuccess) {
-        finish(S, r, kFailed, PNUC_ERR_CUDA);
-        return;
-    }
-    Layout L(r.n, r.cap);
-    const unsigned char *h = S->host + r.host_off;
-    r.count = *(volatile const unsigned long long *)(h + L.count);
-    if (r.count > r.cap) {
-        // overflow: release and run again with room for exactly the count
-        S->dev_arena->release(r.dev_off, r.bytes);
-        S->host_arena->release(r.host_off, r.bytes);
-        r.has_dev = r.has_host = false;
-        S->stream_owner[r.stream] = 0;
-        r.stream = -1;
-        if (Layout(r.n, r.count).total > S->cfg.arena_bytes) {
-            finish(S, r, kFailed, PNUC_ERR_CAPACITY);
-            return;
+    S->stream_owner[g.stream] = 0;
+    const unsigned char *h = S->host + g.host_off;
+    GroupLayout L(g.n, g.cap, (int)g.tickets.size());
+    const unsigned long long launch_count = *(volatile const unsigned long long *)(h + GroupLayout::count);
+    const unsigned long long *seg_count = (const unsigned long long *)(h + GroupLayout::seg_count);
+    const uint32_t *seg_start = (const uint32_t *)(h + GroupLayout::seg_start);
+    const unsigned long long *cap_start = (const unsigned long long *)(h + GroupLayout::cap_start);
+    const bool single = g.tickets.size() == 1;  // no partition: the launch's count and records
+    // the device region is no longer needed: results are in the host region
+    S->dev_arena->release(g.dev_off, g.dev_bytes);
+    g.has_dev = false;
+    // When the launch itself dropped records (count above the group's reservation), every
+    // per-request count is a lower bound only, so the whole group runs again.
+    const bool dropped = launch_count > g.cap;
+    const std::vector<uint64_t> tickets = g.tickets;  // the group may be freed in the loop
+    std::vector<uint64_t> again;
+    for (size_t j = 0; j < tickets.size(); ++j) {
+        auto it = S->reqs.find(tickets[j]);
+        if (it == S->reqs.end()) continue;
+        Request &r = *it->second;
+        const unsigned long long cnt = single ? launch_count : seg_count[j];
+        if (dropped || cnt > r.cap) {
+            // run again alone, with room for its count (exact unless the launch dropped records;
+            // a lone run that drops records learns its exact count and runs once more)
+            leave_group(S, r);
+            r.solo = true;
+            r.cap = std::max<uint64_t>(r.cap, cnt);
+            if (GroupLayout(r.n, r.cap, 1).dev_total > S->cfg.arena_bytes) {
+                finish(S, r, kFailed, PNUC_ERR_CAPACITY);
+                continue;
+            }
+            r.reruns++;
+            S->reruns++;
+            r.state = kPending;
+            again.push_back(r.ticket);
+            continue;
         }
-        r.cap = r.count;
-        r.reruns++;
-        S->reruns++;
-        r.state = kPending;
-        S->pending.push_front(r.ticket);
+        r.count = cnt;
+        r.res_view = (const pnuc_residual *)(h + L.host_r) + seg_start[j];
+        r.sec_view = (const pnuc_secondary *)(h + L.host_s) + cap_start[j];
+        finish(S, r, kDone, PNUC_OK);
+    }
+    for (auto it = again.rbegin(); it != again.rend(); ++it) S->pending.push_front(*it);
+}
+
+void poll(pnuc_server *S, int si)
+{
+    auto it = S->groups.find(S->stream_owner[si]);
+    if (it == S->groups.end()) {
+        S->stream_owner[si] = 0;
         return;
     }
-    finish(S, r, kDone, PNUC_OK);  // results are in the pinned host arena until fetched
+    cudaError_t q = cudaEventQuery(S->events[si]);
+    if (q == cudaErrorNotReady) return;
+    Group &g = *it->second;
+    if (q != cudaSuccess) {
+        S->stream_owner[si] = 0;
+        std::vector<uint64_t> tickets = g.tickets;
+        for (uint64_t tk : tickets) {
+            auto rt = S->reqs.find(tk);
+            if (rt != S->reqs.end()) finish(S, *rt->second, kFailed, PNUC_ERR_CUDA);
+        }
+        return;
+    }
+    complete(S, g);
 }
 
 void scheduler(pnuc_server *S)
@@ -245,26 +433,25 @@ void scheduler(pnuc_server *S)
     cudaSetDevice(S->ctx->cfg.device);
     std::unique_lock<std::mutex> lock(S->mu);
     while (true) {
+        bool changed = false;
         for (size_t k = 0; k < S->streams.size(); ++k) {
             if (!S->stream_owner[k]) continue;
-            auto it = S->reqs.find(S->stream_owner[k]);
-            if (it == S->reqs.end()) continue;
-            State before = it->second->state;
-            poll(S, *it->second);
-            if (it->second->state != before) S->cv.notify_all();
+            const uint64_t before = S->stream_owner[k];
+            poll(S, (int)k);
+            changed = changed || S->stream_owner[k] != before;
         }
         while (!S->pending.empty()) {
-            auto it = S->reqs.find(S->pending.front());
-            if (it == S->reqs.end()) {
+            // drop tickets of requests that no longer exist
+            if (S->reqs.find(S->pending.front()) == S->reqs.end()) {
                 S->pending.pop_front();
                 continue;
             }
-            if (!admit(S, *it->second)) break;
-            S->pending.pop_front();
-            if (it->second->state == kFailed) S->cv.notify_all();
+            if (!admit(S)) break;
+            changed = true;
         }
+        if (changed) S->cv.notify_all();
         bool inflight = false;
-        for (uint64_t t : S->stream_owner) inflight = inflight || t != 0;
+        for (uint64_t g : S->stream_owner) inflight = inflight || g != 0;
         if (S->stop && !inflight) break;
         S->cv.wait_for(lock, inflight ? std::chrono::microseconds(50) : std::chrono::milliseconds(2));
     }
@@ -285,12 +472,14 @@ extern "C" {
 void pnuc_server_default_config(pnuc_server_config *cfg)
 {
     if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
     cfg->precision = PNUC_FP32;
     cfg->streams = 8;
     cfg->arena_bytes = 1ull << 30;
     cfg->sec_per_event = 12;
     cfg->max_pending = 4096;
     cfg->max_request_events = 1ull << 24;
+    cfg->max_merge = 32;
 }
 
 pnuc_status pnuc_server_destroy(pnuc_server *S)
@@ -324,7 +513,7 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg_in, 
     if (cfg_in) cfg = *cfg_in;
     if ((cfg.precision != PNUC_FP32 && cfg.precision != PNUC_FP64) || cfg.streams < 1 || cfg.streams > 64 ||
         cfg.arena_bytes < (1u << 20) || cfg.sec_per_event < 1 || cfg.sec_per_event > 256 || cfg.max_pending < 1 ||
-        cfg.max_request_events < 1)
+        cfg.max_request_events < 1 || cfg.max_merge < 1 || cfg.max_merge > (uint32_t)kMaxSeg)
         return fail(ctx, PNUC_ERR_ARG, "bad server configuration");
     CU(ctx, cudaSetDevice(ctx->cfg.device));
     pnuc_server *S = new pnuc_server();
@@ -363,9 +552,10 @@ pnuc_status pnuc_server_submit(pnuc_server *S, const double *energies, const int
                                uint64_t seed, uint64_t first_event_id, uint64_t *ticket)
 {
     if (!S || !ticket || (n > 0 && (!energies || !target_ids))) return PNUC_ERR_ARG;
-    if (n == 0 || n > S->cfg.max_request_events) return fail(S->ctx, PNUC_ERR_ARG, "request of %llu events", (unsigned long long)n);
+    if (n == 0 || n > S->cfg.max_request_events)
+        return fail(S->ctx, PNUC_ERR_ARG, "request of %llu events", (unsigned long long)n);
     uint64_t cap = n * S->cfg.sec_per_event;
-    if (Layout(n, cap).total > S->cfg.arena_bytes)
+    if (GroupLayout(n, cap, 1).dev_total > S->cfg.arena_bytes)
         return fail(S->ctx, PNUC_ERR_ARG, "request of %llu events can never fit the %llu-byte arena",
                     (unsigned long long)n, (unsigned long long)S->cfg.arena_bytes);
     std::unique_ptr<Request> r(new Request());
@@ -373,6 +563,7 @@ pnuc_status pnuc_server_submit(pnuc_server *S, const double *energies, const int
     r->seed = seed;
     r->first = first_event_id;
     r->cap = cap;
+    r->solo = n > kMaxGroupEvents;
     r->e.assign(energies, energies + n);
     r->t.assign(target_ids, target_ids + n);
     r->t_submit = Clock::now();
@@ -417,11 +608,9 @@ pnuc_status pnuc_server_fetch(pnuc_server *S, uint64_t ticket, pnuc_secondary *s
     }
     if (r->state != kDone) return PNUC_ERR_STATE;
     if (!residuals || (r->count > 0 && (!secondaries || capacity < r->count))) return PNUC_ERR_CAPACITY;
-    Layout L(r->n, r->cap);
-    const unsigned char *h = S->host + r->host_off;
-    memcpy(residuals, h + L.r, sizeof(pnuc_residual) * r->n);
-    if (r->count) memcpy(secondaries, h + L.s, sizeof(pnuc_secondary) * r->count);
-    S->host_arena->release(r->host_off, r->bytes);
+    memcpy(residuals, r->res_view, sizeof(pnuc_residual) * r->n);
+    if (r->count) memcpy(secondaries, r->sec_view, sizeof(pnuc_secondary) * r->count);
+    leave_group(S, *r);
     S->reqs.erase(it);
     S->cv.notify_all();
     return PNUC_OK;
@@ -441,10 +630,8 @@ pnuc_status pnuc_server_view(pnuc_server *S, uint64_t ticket, const pnuc_seconda
         return st;
     }
     if (r->state != kDone) return PNUC_ERR_STATE;
-    Layout L(r->n, r->cap);
-    const unsigned char *h = S->host + r->host_off;
-    *residuals = reinterpret_cast<const pnuc_residual *>(h + L.r);
-    *secondaries = reinterpret_cast<const pnuc_secondary *>(h + L.s);
+    *residuals = r->res_view;
+    *secondaries = r->sec_view;
     *n_secondaries = r->count;
     return PNUC_OK;
 }
@@ -457,7 +644,7 @@ pnuc_status pnuc_server_release(pnuc_server *S, uint64_t ticket)
     if (it == S->reqs.end()) return PNUC_ERR_ARG;
     Request *r = it->second.get();
     if (r->state != kDone && r->state != kFailed) return PNUC_ERR_STATE;
-    if (r->has_host) S->host_arena->release(r->host_off, r->bytes);
+    leave_group(S, *r);
     S->reqs.erase(it);
     S->cv.notify_all();
     return PNUC_OK;
@@ -482,6 +669,7 @@ pnuc_status pnuc_server_get_stats(pnuc_server *S, pnuc_server_stats *out)
     out->elapsed_s = secs;
     out->events_per_s = secs > 0 ? S->events_done / secs : 0.0;
     out->arena_peak_bytes = S->dev_arena->peak();
+    out->launches = S->launches;
     return PNUC_OK;
 }
 
@@ -491,7 +679,7 @@ pnuc_status pnuc_server_reset_stats(pnuc_server *S)
     std::lock_guard<std::mutex> lock(S->mu);
     S->latencies_ms.clear();
     S->queue_ms.clear();
-    S->completed = S->events_done = S->failed = S->reruns = 0;
+    S->completed = S->events_done = S->failed = S->reruns = S->launches = 0;
     S->t_start = Clock::now();
     return PNUC_OK;
 }

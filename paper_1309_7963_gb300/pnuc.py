@@ -76,14 +76,16 @@ class pnuc_tally_spec(C.Structure):
 
 class pnuc_server_config(C.Structure):
     _fields_ = [("precision", C.c_int32), ("streams", C.c_int32), ("arena_bytes", C.c_uint64),
-                ("sec_per_event", C.c_uint32), ("max_pending", C.c_uint32), ("max_request_events", C.c_uint64)]
+                ("sec_per_event", C.c_uint32), ("max_pending", C.c_uint32), ("max_request_events", C.c_uint64),
+                ("max_merge", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class pnuc_server_stats(C.Structure):
     _fields_ = [("completed", C.c_uint64), ("failed", C.c_uint64), ("reruns", C.c_uint64), ("events", C.c_uint64),
                 ("pending", C.c_uint64), ("latency_p50_ms", C.c_double), ("latency_p99_ms", C.c_double),
                 ("latency_max_ms", C.c_double), ("queue_p50_ms", C.c_double), ("queue_p99_ms", C.c_double),
-                ("elapsed_s", C.c_double), ("events_per_s", C.c_double), ("arena_peak_bytes", C.c_uint64)]
+                ("elapsed_s", C.c_double), ("events_per_s", C.c_double), ("arena_peak_bytes", C.c_uint64),
+                ("launches", C.c_uint64)]
 
 
 class PnucError(RuntimeError):

@@ -132,3 +132,59 @@ def test_zero_copy_view_and_release(ctx):
         assert srv.stats()["completed"] == len(reqs) + 1
     finally:
         srv.close()
+
+
+def test_small_requests_are_merged_and_split_back(ctx):
+    """Many small same-seed requests share launches (fewer launches than requests); requests
+    with other seeds in between are never merged with them; every request's residuals and
+    secondaries (renumbered to its own events) equal its events run alone."""
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(96, rate_hz=1e6, seed=14, min_batch=50, max_batch=3000)
+    seeds = [21 if k % 8 else 22 for k in range(len(reqs))]
+    srv = pnuc.Server(ctx, precision="fp32", streams=2, arena_bytes=256 << 20, max_merge=16)
+    try:
+        tickets = [srv.submit(r["energies"], tids[r["tidx"]], s, r["first_event_id"]) for r, s in zip(reqs, seeds)]
+        for tk, r, s in zip(tickets, reqs, seeds):
+            sec, res = srv.fetch(tk, srv.wait(tk))
+            ref_sec, ref_res = alone(ctx, r, tids, s)
+            assert np.array_equal(res, ref_res)
+            assert np.array_equal(pnuc.sort_secondaries(sec), ref_sec)
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["failed"] == 0 and st["reruns"] == 0
+        # seed changes cut the queue into 12 runs of 7 same-seed requests and 12 single ones
+        assert 24 <= st["launches"] < len(reqs)
+    finally:
+        srv.close()
+
+
+def test_merging_can_be_switched_off(ctx):
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(12, rate_hz=1e6, seed=15, min_batch=200, max_batch=2000)
+    srv = pnuc.Server(ctx, precision="fp32", streams=1, arena_bytes=64 << 20, max_merge=1)
+    try:
+        tickets = [srv.submit(r["energies"], tids[r["tidx"]], 4, r["first_event_id"]) for r in reqs]
+        for tk, r in zip(tickets, reqs):
+            sec, res = srv.fetch(tk, srv.wait(tk))
+            ref_sec, ref_res = alone(ctx, r, tids, 4)
+            assert np.array_equal(res, ref_res) and np.array_equal(pnuc.sort_secondaries(sec), ref_sec)
+        assert srv.stats()["launches"] == len(reqs)
+    finally:
+        srv.close()
+
+
+def test_overflow_inside_a_merged_launch(ctx):
+    """One secondary reserved per event: merged requests overflow their ranges (and the
+    launch its reservation); each is run again alone and still equals its events run alone."""
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(20, rate_hz=1e6, seed=16, min_batch=100, max_batch=1500)
+    srv = pnuc.Server(ctx, precision="fp64", streams=1, arena_bytes=64 << 20, sec_per_event=1, max_merge=8)
+    try:
+        tickets = [srv.submit(r["energies"], tids[r["tidx"]], 6, r["first_event_id"]) for r in reqs]
+        for tk, r in zip(tickets, reqs):
+            sec, res = srv.fetch(tk, srv.wait(tk))
+            ref_sec, ref_res = alone(ctx, r, tids, 6, precision="fp64")
+            assert np.array_equal(res, ref_res) and np.array_equal(pnuc.sort_secondaries(sec), ref_sec)
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["reruns"] >= len(reqs)
+    finally:
+        srv.close()
