@@ -110,6 +110,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-divergence", action="store_true")
     return ap.parse_args()
 
 
@@ -202,6 +203,47 @@ def serving_bench(ctx, seconds: float = 1.5) -> dict:
                           "16 streams, 2 GiB arenas, FP32", "runs": runs}
     finally:
         srv.close()
+
+
+def divergence_bound(ctx, n: int = 1_000_000, run: int = 32, reps: int = 3) -> dict:
+    """The paper's divergence experiment (§3: every thread given the same random state ran
+    p-12C events 4x (70 MeV) and 5x (200 MeV) faster): each workload is timed once with
+    distinct event ids and once with runs of `run` lanes sharing one id (warp-uniform, so
+    no lane of a warp diverges from the others; the runs still sample n / run different
+    events, so the mix of event costs is kept). FP32 mode, plain kernel and persistent
+    method; events/s and the ratio uniform / distinct."""
+    import torch
+
+    from paper_1309_7963_gb300 import inputs
+    cases = [("p-12C 70 MeV", inputs.C12, 70.0), ("p-12C 200 MeV", inputs.C12, 200.0),
+             ("p-16O 200 MeV", inputs.O16, 200.0), ("p-40Ca 200 MeV", inputs.CA40, 200.0)]
+    out = {"run": run, "events": n, "cases": {}}
+    res_cap = ctx.alloc(n, capacity=16 * n)
+    stream = torch.cuda.current_stream()
+    for name, target, energy in cases:
+        tid = ctx.create_target(*target)
+        e = torch.full((n,), energy, dtype=torch.float64, device="cuda")
+        t = torch.full((n,), tid, dtype=torch.int32, device="cuda")
+        first = 1 << 40
+        ids = {"distinct": None, "uniform": first + torch.arange(n, device="cuda", dtype=torch.int64) // run}
+        row = {}
+        for method in ("plain", "persistent"):
+            for kind, ev_ids in ids.items():
+                ctx.simulate(e, t, seed=5, first_event_id=first, method=method, out=res_cap, event_ids=ev_ids)
+                torch.cuda.synchronize()
+                best = None
+                for _ in range(reps):
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    ctx.simulate(e, t, seed=5, first_event_id=first, method=method, out=res_cap, event_ids=ev_ids)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    ms = a.elapsed_time(b)
+                    best = ms if best is None else min(best, ms)
+                row[f"{method}_{kind}"] = n / (best * 1e-3)
+            row[f"{method}_ratio"] = row[f"{method}_uniform"] / row[f"{method}_distinct"]
+        out["cases"][name] = row
+    return out
 
 
 def cpu_baseline(n_each: int, threads: int | None = None) -> dict:
@@ -396,6 +438,7 @@ def main():
     cyc = {k[7:]: counters[k] for k in counters if k.startswith("cycles_")}
     phase_split = {k: v / max(1, sum(cyc.values())) for k, v in cyc.items()}
     serving = None if (args.no_serving or world > 1) else serving_bench(ctx)
+    divergence = None if (args.no_divergence or world > 1) else divergence_bound(ctx)
     if rank != 0:
         return
     cb = None
@@ -419,7 +462,7 @@ def main():
         "p99_ms": serving["runs"][-1]["p99_ms"] if serving else None,
         "serving": serving,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cb, "clocks": clk, "gpu_launches": 2 * args.steps,
-        "tally": tally,
+        "tally": tally, "divergence_bound": divergence,
     }
     print(json.dumps(line))
 

@@ -130,6 +130,10 @@ typedef struct {
                                   Neutron-induced events take the neutron's mass and the
                                   neutron well at entry, and the residual keeps the target's
                                   charge (an extension of the paper's proton-induced model) */
+    const uint64_t *event_ids;  /* device, n entries: the id of each event, in place of
+                                  first_event_id + i; NULL = first_event_id + i. Ids may repeat:
+                                  a batch of one repeated id runs one event on every lane, the
+                                  divergence-free bound of the paper's same-seed experiment (§3) */
 } pnuc_batch;
 
 /* Where a batch's results go. */
@@ -150,7 +154,8 @@ typedef struct {
     int32_t block_size;       /* threads per block: 64, 128, 256 or 512 */
     int32_t blocks_per_sm;    /* resident blocks per SM for the persistent grid (<= occupancy) */
     int32_t refill_threshold; /* a warp refills when at least this many lanes are idle (1..32) */
-    int32_t chunk;            /* events a warp takes from the queue per atomic (32 .. 2^20) */
+    int32_t chunk;            /* most events a warp takes from the queue per atomic (32 .. 2^20); claims
+                                 shrink towards 32 as the queue drains */
     int32_t kin_batch;        /* accepted collisions a warp gathers before their FP64 kinematics (1..32) */
 } pnuc_tuning;
 
@@ -278,7 +283,7 @@ pnuc_status pnuc_graph_destroy(pnuc_graph *graph);
  * CUDA streams is free and both the device output arena and a pinned host arena of
  * arena_bytes have room for the request's inputs, residuals and sec_per_event secondaries
  * per event (memory-based admission). Queued requests with the same seed are merged, up to
- * max_merge of them (and 2^22 events), into one persistent launch on a free stream, each
+ * max_merge of them and merge_events events, into one persistent launch on a free stream, each
  * event keeping its own id; a partition kernel then gives every request a contiguous range of
  * secondaries. Launches on different streams overlap on the GPU (continuous batching). A
  * request that produces more secondaries than reserved is run again alone, with room for
@@ -293,7 +298,8 @@ typedef struct {
     uint32_t max_pending;        /* queued requests before submit refuses (default 4096) */
     uint64_t max_request_events; /* largest request accepted (default 2^24) */
     uint32_t max_merge;          /* requests merged into one launch, 1..64 (default 32; 1 = never) */
-    uint32_t reserved;
+    uint32_t merge_events;       /* a group takes no further request that would bring it above this
+                                    many events, 1..2^22 (default 2^18) */
 } pnuc_server_config;
 
 typedef struct {

@@ -153,6 +153,7 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
     p.energies = batch->energies;
     p.target_ids = batch->target_ids;
     p.projectiles = batch->projectiles;
+    p.event_ids = reinterpret_cast<const unsigned long long *>(batch->event_ids);
     p.seg_first = seg.first;
     p.seg_start = seg.start;
     p.n_seg = seg.n;

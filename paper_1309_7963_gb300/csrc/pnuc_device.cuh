@@ -452,10 +452,11 @@ __device__ void write_residual(const SimParams &P, const Lane<R> &L)
     for (int k = 0; k < 4; ++k) dst[k] = src[k];
 }
 
-// Id of event ev of the launch: its position in its segment plus the segment's first id
-// (merged serving requests), else first_event_id + ev.
+// Id of event ev of the launch: the batch's per-event id if it has them; else its position in
+// its segment plus the segment's first id (merged serving requests); else first_event_id + ev.
 __device__ __forceinline__ unsigned long long event_id(const SimParams &P, uint32_t ev)
 {
+    if (P.event_ids) return __ldg(&P.event_ids[ev]);
     if (P.n_seg <= 0) return P.first_event_id + ev;
     int lo = 0, hi = P.n_seg - 1;  // the last segment k with seg_start[k] <= ev
     while (lo < hi) {

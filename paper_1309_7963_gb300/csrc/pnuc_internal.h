@@ -46,6 +46,7 @@ struct SimParams {
     const double *energies;
     const int32_t *target_ids;
     const uint8_t *projectiles;      // per event 1 proton, 0 neutron; null = all protons
+    const unsigned long long *event_ids;  // per-event ids, or null
     // merged requests (serving): event i of segment k (seg_start[k] <= i < seg_start[k+1]) has
     // id seg_first[k] + i - seg_start[k]; n_seg = 0: id first_event_id + i
     const unsigned long long *seg_first;

@@ -105,13 +105,17 @@ __global__ void __launch_bounds__(512) plain_kernel(const SimParams P)
 }
 
 // Warp-level reservoir [next, end) of claimed queue indices (warp-uniform state). take()
-// gives every idle lane one index, or ~0 once the queue is exhausted, and claims a new chunk
-// of `chunk` indices with one atomicAdd on the queue head when the reservoir runs short.
+// gives every idle lane one index, or ~0 once the queue is exhausted, and claims new indices
+// with one atomicAdd on the queue head when the reservoir runs short. Guided self-scheduling:
+// a claim takes the remaining indices (as of the warp's last claim) over `share`, a multiple
+// of 32 between 32 and `chunk`, so claims shrink as the queue drains and the launch ends
+// about one event per lane after the queue, not one chunk per warp.
 struct WarpQueue {
-    unsigned long long next = 0, end = 0;
+    unsigned long long next = 0, end = 0, seen = 0;
     bool drained = false;
     __device__ __forceinline__ unsigned long long take(unsigned idle, unsigned lane, unsigned long long *head,
-                                                       unsigned long long n, unsigned long long chunk)
+                                                       unsigned long long n, unsigned long long chunk,
+                                                       unsigned long long share)
     {
         const unsigned FULL = 0xffffffffu;
         const unsigned long long nidle = (unsigned long long)__popc(idle);
@@ -123,10 +127,13 @@ struct WarpQueue {
             next = avail >= nidle ? next + nidle : end;
             return ev;
         }
+        unsigned long long c = seen < n ? ((n - seen) / share) & ~31ull : 32ull;
+        c = c < 32ull ? 32ull : (c > chunk ? chunk : c);  // >= 32 >= nidle - avail
         unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(head, chunk);
+        if (lane == 0) got = atomicAdd(head, c);
         got = __shfl_sync(FULL, got, 0);
-        unsigned long long gend = got + chunk < n ? got + chunk : n;
+        seen = got + c;
+        unsigned long long gend = got + c < n ? got + c : n;
         if (got >= n) {
             drained = true;
             gend = got;
@@ -139,6 +146,12 @@ struct WarpQueue {
         return ev;
     }
 };
+
+// claims are sized for two per warp of the grid over what remains
+__device__ __forceinline__ unsigned long long queue_share()
+{
+    return 2ull * gridDim.x * (blockDim.x >> 5);
+}
 
 // Persistent cascade kernel: grid = resident blocks only. When at least refill_threshold lanes
 // of a warp are idle (or none is busy) they take events from the warp's queue reservoir.
@@ -166,6 +179,7 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
     L.rng.stride = blockDim.x;
     Particle<R> stack[kStackCap];
     WarpQueue Q;
+    const unsigned long long share = queue_share();
     while (true) {
         const long long t_top = kCount ? clock64() : 0;
         if (L.phase == kFinish) {
@@ -176,7 +190,7 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
         const unsigned busy = __ballot_sync(FULL, L.phase == kEntry || L.phase == kTransport || L.phase == kKinWait);
         const int nidle = __popc(idle);
         if (nidle && (nidle >= P.refill_threshold || busy == 0 || Q.drained)) {
-            const unsigned long long ev = Q.take(idle, lane, P.queue_head, P.n, (unsigned long long)P.chunk);
+            const unsigned long long ev = Q.take(idle, lane, P.queue_head, P.n, (unsigned long long)P.chunk, share);
             if (L.phase == kIdle) {
                 if (ev < P.n) begin_event<R>(P, ts, L, (uint32_t)ev);
                 else L.phase = kExhausted;
@@ -249,6 +263,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
     L.rng.stride = blockDim.x;
     uint32_t d0 = 0;  // draw index at which the lane's evaporation resumed
     WarpQueue Q;
+    const unsigned long long share = queue_share();
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     WidthJob<R> *jobs0 = reinterpret_cast<WidthJob<R> *>(smem + smem_bytes<R>(P.n_targets, blockDim.x));
     WidthJob<R> *jobs = jobs0 + warp * kWidthSlots;
@@ -264,7 +279,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
         const int nidle = __popc(idle);
         const unsigned busy = __ballot_sync(FULL, L.phase == kEvap);
         if (nidle && (nidle >= P.refill_threshold || busy == 0 || Q.drained)) {
-            const unsigned long long ev = Q.take(idle, lane, P.evap_head, P.n, (unsigned long long)P.chunk);
+            const unsigned long long ev = Q.take(idle, lane, P.evap_head, P.n, (unsigned long long)P.chunk, share);
             if (L.phase == kIdle) {
                 if (ev < P.n) {
                     begin_evap<R>(P, L, (uint32_t)ev);

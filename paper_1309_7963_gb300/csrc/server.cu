@@ -240,7 +240,7 @@ bool admit(pnuc_server *S)
         Request &r = *it->second;
         if (!cand.empty() && (r.solo || cand[0]->solo || r.seed != cand[0]->seed ||
                               (int)cand.size() >= std::min<int>(S->cfg.max_merge, kMaxSeg) ||
-                              n + r.n > kMaxGroupEvents))
+                              n + r.n > S->cfg.merge_events))
             break;
         cand.push_back(&r);
         n += r.n;
@@ -480,6 +480,7 @@ void pnuc_server_default_config(pnuc_server_config *cfg)
     cfg->max_pending = 4096;
     cfg->max_request_events = 1ull << 24;
     cfg->max_merge = 32;
+    cfg->merge_events = 1u << 18;
 }
 
 pnuc_status pnuc_server_destroy(pnuc_server *S)
@@ -513,7 +514,8 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg_in, 
     if (cfg_in) cfg = *cfg_in;
     if ((cfg.precision != PNUC_FP32 && cfg.precision != PNUC_FP64) || cfg.streams < 1 || cfg.streams > 64 ||
         cfg.arena_bytes < (1u << 20) || cfg.sec_per_event < 1 || cfg.sec_per_event > 256 || cfg.max_pending < 1 ||
-        cfg.max_request_events < 1 || cfg.max_merge < 1 || cfg.max_merge > (uint32_t)kMaxSeg)
+        cfg.max_request_events < 1 || cfg.max_merge < 1 || cfg.max_merge > (uint32_t)kMaxSeg || cfg.merge_events < 1 ||
+        cfg.merge_events > kMaxGroupEvents)
         return fail(ctx, PNUC_ERR_ARG, "bad server configuration");
     CU(ctx, cudaSetDevice(ctx->cfg.device));
     pnuc_server *S = new pnuc_server();

@@ -44,7 +44,8 @@ class pnuc_config(C.Structure):
 
 class pnuc_batch(C.Structure):
     _fields_ = [("energies", C.c_void_p), ("target_ids", C.c_void_p), ("n", C.c_uint64), ("seed", C.c_uint64),
-                ("first_event_id", C.c_uint64), ("projectiles", C.c_void_p)]
+                ("first_event_id", C.c_uint64), ("projectiles", C.c_void_p),
+                ("event_ids", C.c_void_p)]
 
 
 class pnuc_output(C.Structure):
@@ -77,7 +78,7 @@ class pnuc_tally_spec(C.Structure):
 class pnuc_server_config(C.Structure):
     _fields_ = [("precision", C.c_int32), ("streams", C.c_int32), ("arena_bytes", C.c_uint64),
                 ("sec_per_event", C.c_uint32), ("max_pending", C.c_uint32), ("max_request_events", C.c_uint64),
-                ("max_merge", C.c_uint32), ("reserved", C.c_uint32)]
+                ("max_merge", C.c_uint32), ("merge_events", C.c_uint32)]
 
 
 class pnuc_server_stats(C.Structure):
@@ -331,10 +332,11 @@ class Context:
 
     def simulate(self, energies, target_ids, seed: int, first_event_id: int = 0, precision: str = "fp32",
                  method: str = "persistent", out: Result | None = None, capacity: int | None = None,
-                 counters: bool = False, stream=None, projectiles=None) -> Result:
+                 counters: bool = False, stream=None, projectiles=None, event_ids=None) -> Result:
         """Launches pnuc_simulate on device tensors (energies float64, target_ids int32,
-        optional projectiles uint8: 1 proton, 0 neutron; None = protons). Asynchronous on
-        `stream` (default: torch's current stream)."""
+        optional projectiles uint8: 1 proton, 0 neutron; None = protons; optional event_ids
+        int64, the id of each event in place of first_event_id + i). Asynchronous on `stream`
+        (default: torch's current stream)."""
         torch = self._torch
         n = int(energies.shape[0])
         if energies.dtype != torch.float64 or target_ids.dtype != torch.int32:
@@ -350,7 +352,13 @@ class Context:
             if projectiles.dtype != torch.uint8 or not projectiles.is_cuda or projectiles.shape[0] != n:
                 raise ValueError("projectiles must be a uint8 CUDA tensor of the batch's length")
             pj = projectiles.contiguous()
-        b = pnuc_batch(_ptr(energies), _ptr(target_ids), n, seed, first_event_id, _ptr(pj) if pj is not None else None)
+        ids = None
+        if event_ids is not None:
+            if event_ids.dtype != torch.int64 or not event_ids.is_cuda or event_ids.shape[0] != n:
+                raise ValueError("event_ids must be an int64 CUDA tensor of the batch's length")
+            ids = event_ids.contiguous()
+        b = pnuc_batch(_ptr(energies), _ptr(target_ids), n, seed, first_event_id, _ptr(pj) if pj is not None else None,
+                       _ptr(ids) if ids is not None else None)
         o = pnuc_output(_ptr(out.secondaries), out.secondaries.shape[0], _ptr(out.count), _ptr(out.residuals),
                         _ptr(out.counters))
         s = (stream or torch.cuda.current_stream(self.device)).cuda_stream

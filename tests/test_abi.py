@@ -30,7 +30,7 @@ def test_record_layouts():
     assert pnuc.RESIDUAL_DTYPE.itemsize == 64
     assert pnuc.SECONDARY_DTYPE.fields["T"][1] == 8
     assert pnuc.RESIDUAL_DTYPE.fields["Estar_cascade"][1] == 24
-    assert C.sizeof(pnuc.pnuc_batch) == 48 and C.sizeof(pnuc.pnuc_output) == 40
+    assert C.sizeof(pnuc.pnuc_batch) == 56 and C.sizeof(pnuc.pnuc_output) == 40
     assert C.sizeof(pnuc.pnuc_tuning) == 20 and C.sizeof(pnuc.pnuc_config) == 20
 
 
