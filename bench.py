@@ -6,7 +6,8 @@ FP32 bulk mode (FP64 boosts, bookkeeping and evaporation widths), persistent ker
 warp-level lane refill. The same batch is also timed with the plain one-event-per-thread
 kernel ("batched vs plain"). Inputs are synthetic (seeded) and resident in HBM when the timed
 region starts; the e2e figure goes through the host-buffer C-ABI entry point with the
-host<->device copies inside the timed region.
+host<->device transfers inside the timed region (inputs copied in; outputs written by the
+kernels into the caller's pinned host buffers).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -379,7 +380,10 @@ def main():
             sec, _ = ctx.simulate_host(e_h, t_h, seed=w.seed, first_event_id=first, sec_out=sec_h, res_out=res_h)
         dt = time.perf_counter() - t0
         e2e = {"value": world * n * steps_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": int(e_h.nbytes + t_h.nbytes),
-               "d2h_bytes_per_step": int(res_h.nbytes + len(sec) * 32 + 8)}
+               "d2h_bytes_per_step": int(res_h.nbytes + len(sec) * 32 + 8),
+               "path": "pnuc_simulate_host with pinned host buffers: inputs copied in, residuals and "
+                       "secondaries written by the kernels into the pinned buffers (mapped host memory), "
+                       "host wall clock per call"}
 
     # yield tallies of the last step's outputs (an HBM-streaming pass): L2 flushed before each
     tally = None

@@ -204,7 +204,10 @@ pnuc_status pnuc_simulate(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method m
 /* pnuc_simulate with HOST buffers: energies/target_ids (host, n entries) are copied to
  * device staging buffers the context owns (grown as needed), the batch runs, and the
  * residuals (host, n entries), up to sec_capacity secondaries (host) and the produced
- * count (host) are copied back. Synchronous: returns after the results are on the host.
+ * count (host) are copied back. Output buffers in pinned host memory (cudaHostAlloc,
+ * cudaHostRegister, a framework's pinned tensor), 16-byte aligned, are instead written by
+ * the kernels directly (secondaries and residuals each, where it holds), with no copy after
+ * them. Synchronous: returns after the results are on the host.
  * Returns PNUC_ERR_CAPACITY if *sec_count > sec_capacity (the first sec_capacity
  * records are still written). Incident protons (neutron-induced events go through
  * pnuc_simulate with pnuc_batch.projectiles). */
@@ -223,9 +226,11 @@ pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_met
  * Same arguments, results and errors as pnuc_simulate_host, but the device copies of the
  * inputs and outputs and the persistent kernel's queue head live in one static device
  * array of PNUC_NOALLOC_SCRATCH_BYTES (8 MiB) that every GPU loading this library holds
- * until the process exits. A batch whose layout does not fit (about 8 MiB / (76 + 32 k)
- * events for room for k secondaries per event: 24,000 events at k = 8) is rejected with
- * PNUC_ERR_CAPACITY before anything runs. The entry point calls no cudaMalloc, cudaFree or
+ * until the process exits; output buffers in pinned host memory are written in place and
+ * take none of it. A batch whose layout does not fit (about 8 MiB / (76 + 32 k) events for
+ * room for k secondaries per event with pageable outputs: 24,000 events at k = 8; 8 MiB / 12
+ * = 690,000 events with pinned ones) is rejected with PNUC_ERR_CAPACITY before anything
+ * runs. The entry point calls no cudaMalloc, cudaFree or
  * allocating library routine. Its first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first call before any
  * stream capture. Every call shares the array and it keeps the last call's contents; the

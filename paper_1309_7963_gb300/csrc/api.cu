@@ -144,7 +144,7 @@ cudaError_t launch_evap_for(pnuc_ctx *ctx, pnuc_precision precision, const SimPa
 
 pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
                          const pnuc_output *out, cudaStream_t s, const pnuc_tuning &t, unsigned long long *queue_head,
-                         const Segments &seg)
+                         const Placement &seg)
 {
     CU(ctx, cudaSetDevice(ctx->cfg.device));
     CU(ctx, cudaMemsetAsync(out->count, 0, sizeof(unsigned long long), s));
@@ -340,6 +340,7 @@ pnuc_status pnuc_destroy(pnuc_ctx *ctx)
     cudaFree(ctx->h_res);
     cudaFree(ctx->h_sec);
     cudaFree(ctx->h_count);
+    cudaFreeHost(ctx->h_count_host);
     for (cudaEvent_t e : ctx->tev) cudaEventDestroy(e);
     cudaFree(ctx->sorted_stacks);
     delete ctx;
@@ -418,6 +419,29 @@ pnuc_status pnuc_simulate(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method m
     return launch_batch(ctx, precision, method, batch, out, (cudaStream_t)stream, ctx->tuning[precision], nullptr);
 }
 
+namespace {
+constexpr bool kZeroCopySecondaries = true;
+constexpr bool kZeroCopyResiduals = true;
+
+// The device address of the host range [p, p + bytes) if all of it is pinned, mapped into
+// the device's address space (one allocation) and 16-byte aligned, else null.
+void *mapped_range(void *p, size_t bytes)
+{
+    if (!p || bytes == 0 || (reinterpret_cast<uintptr_t>(p) & 15)) return nullptr;
+    cudaPointerAttributes a, b;
+    const unsigned char *last = reinterpret_cast<const unsigned char *>(p) + bytes - 1;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();  // not a CUDA pointer: clear the error
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    unsigned char *d = static_cast<unsigned char *>(a.devicePointer);
+    if (static_cast<unsigned char *>(b.devicePointer) != d + (bytes - 1)) return nullptr;
+    return d;
+}
+}  // namespace
+
 pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const double *energies,
                                const int32_t *target_ids, uint64_t n, uint64_t seed, uint64_t first_event_id,
                                pnuc_secondary *secondaries, uint64_t sec_capacity, uint64_t *sec_count,
@@ -428,20 +452,34 @@ pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_met
     if (sec_capacity > 0 && !secondaries) return fail(ctx, PNUC_ERR_ARG, "null secondaries with capacity > 0");
     cudaStream_t s = (cudaStream_t)stream;
     CU(ctx, cudaSetDevice(ctx->cfg.device));
-    if (n > ctx->h_events_cap) {
-        cudaFree(ctx->h_energies);
-        cudaFree(ctx->h_tids);
-        cudaFree(ctx->h_res);
-        ctx->h_energies = nullptr;
-        ctx->h_tids = nullptr;
-        ctx->h_res = nullptr;
-        ctx->h_events_cap = 0;
-        CU(ctx, cudaMalloc(&ctx->h_energies, sizeof(double) * n));
-        CU(ctx, cudaMalloc(&ctx->h_tids, sizeof(int32_t) * n));
-        CU(ctx, cudaMalloc(&ctx->h_res, sizeof(pnuc_residual) * n));
-        ctx->h_events_cap = n;
+    // Output buffers in pinned host memory are written by the kernels themselves (mapped
+    // memory over the chip-to-chip link; the kernels emit a few tens of GB/s), so no copy
+    // follows the kernels; other buffers are staged on the device and copied back.
+    pnuc_secondary *dsec = kZeroCopySecondaries ? static_cast<pnuc_secondary *>(
+                                                      mapped_range(secondaries, sizeof(pnuc_secondary) * sec_capacity))
+                                                : nullptr;
+    pnuc_residual *dres =
+        kZeroCopyResiduals ? static_cast<pnuc_residual *>(mapped_range(residuals, sizeof(pnuc_residual) * n)) : nullptr;
+    if (n > ctx->h_events_cap || (!dres && n > ctx->h_res_cap)) {
+        if (n > ctx->h_events_cap) {
+            cudaFree(ctx->h_energies);
+            cudaFree(ctx->h_tids);
+            ctx->h_energies = nullptr;
+            ctx->h_tids = nullptr;
+            ctx->h_events_cap = 0;
+            CU(ctx, cudaMalloc(&ctx->h_energies, sizeof(double) * n));
+            CU(ctx, cudaMalloc(&ctx->h_tids, sizeof(int32_t) * n));
+            ctx->h_events_cap = n;
+        }
+        if (!dres && n > ctx->h_res_cap) {
+            cudaFree(ctx->h_res);
+            ctx->h_res = nullptr;
+            ctx->h_res_cap = 0;
+            CU(ctx, cudaMalloc(&ctx->h_res, sizeof(pnuc_residual) * n));
+            ctx->h_res_cap = n;
+        }
     }
-    if (sec_capacity > ctx->h_sec_cap) {
+    if (!dsec && sec_capacity > ctx->h_sec_cap) {
         cudaFree(ctx->h_sec);
         ctx->h_sec = nullptr;
         ctx->h_sec_cap = 0;
@@ -449,20 +487,26 @@ pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_met
         ctx->h_sec_cap = sec_capacity;
     }
     if (!ctx->h_count) CU(ctx, cudaMalloc(&ctx->h_count, sizeof(unsigned long long)));
+    if (!ctx->h_count_host) CU(ctx, cudaMallocHost(&ctx->h_count_host, sizeof(unsigned long long)));
+    pnuc_batch b = {ctx->h_energies, ctx->h_tids, n, seed, first_event_id};
+    pnuc_output o = {sec_capacity ? (dsec ? dsec : ctx->h_sec) : nullptr, sec_capacity, ctx->h_count,
+                     dres ? dres : ctx->h_res, nullptr};
+    pnuc_status st = check_batch(ctx, precision, method, &b, &o);
+    if (st != PNUC_OK) return st;
+    *sec_count = 0;
     if (n > 0) {
         CU(ctx, cudaMemcpyAsync(ctx->h_energies, energies, sizeof(double) * n, cudaMemcpyHostToDevice, s));
         CU(ctx, cudaMemcpyAsync(ctx->h_tids, target_ids, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     }
-    pnuc_batch b = {ctx->h_energies, ctx->h_tids, n, seed, first_event_id};
-    pnuc_output o = {ctx->h_sec, sec_capacity, ctx->h_count, ctx->h_res, nullptr};
-    pnuc_status st = pnuc_simulate(ctx, precision, method, &b, &o, stream);
+    st = launch_batch(ctx, precision, method, &b, &o, s, ctx->tuning[precision], nullptr);
     if (st != PNUC_OK) return st;
-    unsigned long long cnt = 0;
-    CU(ctx, cudaMemcpyAsync(&cnt, ctx->h_count, sizeof cnt, cudaMemcpyDeviceToHost, s));
-    if (n > 0) CU(ctx, cudaMemcpyAsync(residuals, ctx->h_res, sizeof(pnuc_residual) * n, cudaMemcpyDeviceToHost, s));
+    CU(ctx, cudaMemcpyAsync(ctx->h_count_host, ctx->h_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    if (n > 0 && !dres)
+        CU(ctx, cudaMemcpyAsync(residuals, ctx->h_res, sizeof(pnuc_residual) * n, cudaMemcpyDeviceToHost, s));
     CU(ctx, cudaStreamSynchronize(s));
-    uint64_t ncopy = cnt < sec_capacity ? cnt : sec_capacity;
-    if (ncopy > 0) {
+    const unsigned long long cnt = *(volatile unsigned long long *)ctx->h_count_host;
+    const uint64_t ncopy = cnt < sec_capacity ? cnt : sec_capacity;
+    if (!dsec && ncopy > 0) {
         CU(ctx, cudaMemcpyAsync(secondaries, ctx->h_sec, sizeof(pnuc_secondary) * ncopy, cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaStreamSynchronize(s));
     }
@@ -495,12 +539,16 @@ pnuc_status pnuc_simulate_host_noalloc(pnuc_ctx *ctx, pnuc_precision precision, 
     if (n > 0 && (!energies || !target_ids || !residuals)) return fail(ctx, PNUC_ERR_ARG, "null input/output");
     if (sec_capacity > 0 && !secondaries) return fail(ctx, PNUC_ERR_ARG, "null secondaries with capacity > 0");
     if (method == PNUC_SORTED) return fail(ctx, PNUC_ERR_ARG, "the sorted method needs a context buffer");
-    // scratch layout: [queue head | count], energies, target ids, residuals, secondaries
+    // outputs in pinned host memory are written in place (as in pnuc_simulate_host) and take
+    // no scratch; scratch layout: [queue head | count], energies, target ids, residuals,
+    // secondaries
+    pnuc_secondary *zsec = static_cast<pnuc_secondary *>(mapped_range(secondaries, sizeof(pnuc_secondary) * sec_capacity));
+    pnuc_residual *zres = static_cast<pnuc_residual *>(mapped_range(residuals, sizeof(pnuc_residual) * n));
     const size_t off_e = 256;
     const size_t off_t = off_e + round256(sizeof(double) * n);
     const size_t off_r = off_t + round256(sizeof(int32_t) * n);
-    const size_t off_s = off_r + round256(sizeof(pnuc_residual) * n);
-    const size_t need = off_s + round256(sizeof(pnuc_secondary) * sec_capacity);
+    const size_t off_s = off_r + (zres ? 0 : round256(sizeof(pnuc_residual) * n));
+    const size_t need = off_s + (zsec ? 0 : round256(sizeof(pnuc_secondary) * sec_capacity));
     if (n > PNUC_NOALLOC_SCRATCH_BYTES || sec_capacity > PNUC_NOALLOC_SCRATCH_BYTES || need > PNUC_NOALLOC_SCRATCH_BYTES)
         return fail(ctx, PNUC_ERR_CAPACITY,
                     "pnuc_simulate_host_noalloc: %llu events with room for %llu secondaries need %llu bytes of "
@@ -528,8 +576,8 @@ pnuc_status pnuc_simulate_host_noalloc(pnuc_ctx *ctx, pnuc_precision precision, 
     unsigned long long *count = (unsigned long long *)(base + 128);
     double *d_e = (double *)(base + off_e);
     int32_t *d_t = (int32_t *)(base + off_t);
-    pnuc_residual *d_r = (pnuc_residual *)(base + off_r);
-    pnuc_secondary *d_s = (pnuc_secondary *)(base + off_s);
+    pnuc_residual *d_r = zres ? zres : (pnuc_residual *)(base + off_r);
+    pnuc_secondary *d_s = zsec ? zsec : (pnuc_secondary *)(base + off_s);
     // the scratch keeps the previous call's contents: the queue head and count restart at 0
     // (launch_batch clears both on the stream before the kernel)
     if (n > 0) {
@@ -544,10 +592,10 @@ pnuc_status pnuc_simulate_host_noalloc(pnuc_ctx *ctx, pnuc_precision precision, 
     if (st != PNUC_OK) return st;
     unsigned long long cnt = 0;
     CU(ctx, cudaMemcpyAsync(&cnt, count, sizeof cnt, cudaMemcpyDeviceToHost, s));
-    if (n > 0) CU(ctx, cudaMemcpyAsync(residuals, d_r, sizeof(pnuc_residual) * n, cudaMemcpyDeviceToHost, s));
+    if (n > 0 && !zres) CU(ctx, cudaMemcpyAsync(residuals, d_r, sizeof(pnuc_residual) * n, cudaMemcpyDeviceToHost, s));
     CU(ctx, cudaStreamSynchronize(s));
     uint64_t ncopy = cnt < sec_capacity ? cnt : sec_capacity;
-    if (ncopy > 0) {
+    if (ncopy > 0 && !zsec) {
         CU(ctx, cudaMemcpyAsync(secondaries, d_s, sizeof(pnuc_secondary) * ncopy, cudaMemcpyDeviceToHost, s));
         CU(ctx, cudaStreamSynchronize(s));
     }

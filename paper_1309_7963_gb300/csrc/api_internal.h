@@ -30,10 +30,11 @@ struct pnuc_ctx {
     double *h_energies = nullptr;
     int32_t *h_tids = nullptr;
     pnuc_residual *h_res = nullptr;
-    uint64_t h_events_cap = 0;
+    uint64_t h_events_cap = 0, h_res_cap = 0;
     pnuc_secondary *h_sec = nullptr;
     uint64_t h_sec_cap = 0;
     unsigned long long *h_count = nullptr;
+    unsigned long long *h_count_host = nullptr;  // pinned: the count read back
     // sorted method: particle stacks of every resident slot (grown as needed)
     void *sorted_stacks = nullptr;
     size_t sorted_stacks_bytes = 0;
@@ -59,8 +60,9 @@ pnuc_status fail(pnuc_ctx *ctx, pnuc_status st, const char *fmt, ...);
 pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t);
 pnuc_status check_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
                         const pnuc_output *out);
-// Merged requests of one launch (device arrays; the fields of the same names in SimParams).
-struct Segments {
+// Merged requests of one launch (device arrays; the SimParams fields seg_first, seg_start
+// and n_seg).
+struct Placement {
     const unsigned long long *first = nullptr;
     const uint32_t *start = nullptr;
     int n = 0;
@@ -68,9 +70,9 @@ struct Segments {
 
 // Enqueues the count reset, the queue-head reset and the kernel of one batch on stream s
 // with tuning t. queue_head: the persistent kernel's queue head, or null for the next slot of
-// the context's ring. seg: merged requests, if any.
+// the context's ring. seg: the launch's placement, if any.
 pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
                          const pnuc_output *out, cudaStream_t s, const pnuc_tuning &t,
-                         unsigned long long *queue_head, const Segments &seg = Segments());
+                         unsigned long long *queue_head, const Placement &seg = Placement());
 
 }  // namespace pnuc

@@ -8,7 +8,17 @@ namespace dev {
 namespace {
 // The FP32 cascade kernel capped at 96 registers: five resident 128-thread blocks per SM
 // instead of four (3.5% faster on GB300 than the 105 registers it uses unbounded).
-__global__ void __maxnreg__(96) persistent_kernel_f32(const SimParams P) { persistent_body<float, false>(P); }
+#ifndef PNUC_F32_CASCADE_REGS
+#define PNUC_F32_CASCADE_REGS 96
+#endif
+#ifndef PNUC_F32_EVAP_REGS
+#define PNUC_F32_EVAP_REGS 128
+#endif
+__global__ void __maxnreg__(PNUC_F32_CASCADE_REGS) persistent_kernel_f32(const SimParams P)
+{
+    persistent_body<float, false>(P);
+}
+__global__ void __maxnreg__(PNUC_F32_EVAP_REGS) evap_kernel_f32(const SimParams P) { evap_body<float, false>(P); }
 }  // namespace
 }  // namespace dev
 
@@ -23,7 +33,8 @@ cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool
 }
 cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s)
 {
-    return count ? dev::launch_evap<float, true>(p, grid, block, s) : dev::launch_evap<float, false>(p, grid, block, s);
+    if (count) return dev::launch_evap<float, true>(p, grid, block, s);
+    return dev::launch_kernel(dev::evap_kernel_f32, dev::evap_smem_bytes<float>(p.n_targets, block), p, grid, block, s);
 }
 cudaError_t launch_sorted_fp32(const SimParams &p, void *stacks, int grid, int block, bool count, cudaStream_t s)
 {
@@ -37,7 +48,8 @@ int occupancy_sorted_fp32(int block, bool count)
 size_t sorted_stack_bytes_fp32() { return sizeof(dev::Particle<float>) * kStackCap; }
 int occupancy_evap_fp32(int block, bool count)
 {
-    return count ? dev::occupancy_evap<float, true>(block) : dev::occupancy_evap<float, false>(block);
+    if (count) return dev::occupancy_evap<float, true>(block);
+    return dev::occupancy_of(dev::evap_kernel_f32, dev::evap_smem_bytes<float>(kMaxTargets, block), block);
 }
 int occupancy_persistent_fp32(int block, bool count)
 {

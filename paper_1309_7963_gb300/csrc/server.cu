@@ -317,7 +317,7 @@ bool admit(pnuc_server *S)
     pnuc_batch b = {(const double *)(d + L.e), (const int32_t *)(d + L.t), n, cand[0]->seed, cand[0]->first};
     pnuc_output o = {cap ? (pnuc_secondary *)(d + L.s) : nullptr, cap, (unsigned long long *)(d + GroupLayout::count),
                      (pnuc_residual *)(d + L.r), nullptr};
-    Segments seg;
+    Placement seg;
     if (k > 1) {
         seg.first = (const unsigned long long *)(d + GroupLayout::seg_first);
         seg.start = (const uint32_t *)(d + GroupLayout::seg_start);

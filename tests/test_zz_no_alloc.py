@@ -1,7 +1,8 @@
 """pnuc_simulate_host_noalloc: the host-buffer entry point for callers that cannot allocate
 device memory while they run (their device memory belongs to another allocator, or their
 footprint must not grow). It must give exactly what pnuc_simulate_host gives, call after
-call on its shared static scratch, and refuse a batch that does not fit that scratch."""
+call on its shared static scratch, and refuse a batch that does not fit that scratch; outputs
+in pinned host memory take no scratch, so larger batches fit."""
 import ctypes as C
 
 import numpy as np
@@ -14,12 +15,22 @@ pytestmark = pytest.mark.gpu
 PNUC_ERR_CAPACITY = 3
 
 
-def noalloc(ctx, energies, tids, seed, first, cap, precision, method):
-    """One call of the no-allocation entry point through the C ABI."""
+def pinned(n_bytes, dtype):
+    import torch
+    return torch.zeros(n_bytes, dtype=torch.uint8).pin_memory().numpy().view(dtype)
+
+
+def noalloc(ctx, energies, tids, seed, first, cap, precision, method, pinned_out=False):
+    """One call of the no-allocation entry point through the C ABI (outputs in pageable
+    numpy arrays, or in pinned host memory, which the kernels write in place)."""
     e = np.ascontiguousarray(energies, np.float64)
     t = np.ascontiguousarray(tids, np.int32)
-    sec = np.zeros(cap, pnuc.SECONDARY_DTYPE)
-    res = np.zeros(len(e), pnuc.RESIDUAL_DTYPE)
+    if pinned_out:
+        sec = pinned(32 * cap, pnuc.SECONDARY_DTYPE)
+        res = pinned(64 * len(e), pnuc.RESIDUAL_DTYPE)
+    else:
+        sec = np.zeros(cap, pnuc.SECONDARY_DTYPE)
+        res = np.zeros(len(e), pnuc.RESIDUAL_DTYPE)
     cnt = C.c_uint64()
     st = ctx.lib.pnuc_simulate_host_noalloc(ctx.handle, pnuc.PRECISION[precision], pnuc.METHOD[method], e.ctypes.data,
                                             t.ctypes.data, len(e), seed, first, sec.ctypes.data, cap, C.byref(cnt),
@@ -53,3 +64,13 @@ def test_noalloc_refuses_batches_beyond_its_scratch(ctx):
     assert st == PNUC_ERR_CAPACITY and len(sec) == 0
     with pytest.raises(pnuc.PnucError, match="static scratch"):
         ctx._check(st)
+
+
+def test_noalloc_with_pinned_outputs_takes_larger_batches(ctx):
+    w = inputs.mixed(300_000, seed=34)
+    tids = target_ids(ctx, w)
+    st, sec, res = noalloc(ctx, w.energies, tids, 34, 5, 8 * w.n, "fp32", "persistent", pinned_out=True)
+    assert st == 0, ctx._check(st)
+    ref_sec, ref_res = ctx.simulate_host(w.energies, tids, seed=34, first_event_id=5, capacity=8 * w.n)
+    assert np.array_equal(res, ref_res)
+    assert np.array_equal(pnuc.sort_secondaries(sec), pnuc.sort_secondaries(ref_sec))
