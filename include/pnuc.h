@@ -305,6 +305,11 @@ typedef struct {
     uint32_t max_merge;          /* requests merged into one launch, 1..64 (default 32; 1 = never) */
     uint32_t merge_events;       /* a group takes no further request that would bring it above this
                                     many events, 1..2^22 (default 2^18) */
+    uint32_t lane_events;        /* a launch gets blocks for about this many events per lane (at
+                                    most the resident limit), so that small launches leave SMs to
+                                    the others and do not each wait on their slowest event with
+                                    the whole GPU, 1..1024 (default 4) */
+    uint32_t reserved;
 } pnuc_server_config;
 
 typedef struct {

@@ -126,7 +126,7 @@ cudaEvent_t *timing_slot(pnuc_ctx *ctx, cudaStream_t s)
 // own resident grid (it uses more registers, and its shared-memory job lists can make the
 // block size too large: then it halves).
 cudaError_t launch_evap_for(pnuc_ctx *ctx, pnuc_precision precision, const SimParams &p, const pnuc_tuning &t,
-                            bool count, uint64_t n, cudaStream_t s)
+                            bool count, uint64_t n, cudaStream_t s, unsigned max_blocks)
 {
     auto occ_evap = [&](int b) {
         return occupancy_kind(kOccEvap, precision, b, count);
@@ -138,6 +138,7 @@ cudaError_t launch_evap_for(pnuc_ctx *ctx, pnuc_precision precision, const SimPa
         (unsigned long long)std::max<long long>(std::min<long long>(want, occ_e), 1) * ctx->sm_count;
     const unsigned long long eneed = (n + eblock - 1) / eblock;
     if (egrid > eneed) egrid = eneed;
+    if (max_blocks && egrid > max_blocks) egrid = max_blocks;
     return precision == PNUC_FP64 ? launch_evap_fp64(p, (int)egrid, eblock, s)
                                   : launch_evap_fp32(p, (int)egrid, eblock, count, s);
 }
@@ -217,13 +218,14 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
         e = precision == PNUC_FP64 ? launch_sorted_fp64(p, ctx->sorted_stacks, (int)grid, t.block_size, s)
                                    : launch_sorted_fp32(p, ctx->sorted_stacks, (int)grid, t.block_size, count, s);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
-        e = e == cudaSuccess ? launch_evap_for(ctx, precision, p, t, count, batch->n, s) : e;
+        e = e == cudaSuccess ? launch_evap_for(ctx, precision, p, t, count, batch->n, s, seg.max_blocks) : e;
     } else {
         int occ = occupancy(precision, t.block_size, count);
         int bps = std::min(t.blocks_per_sm, std::max(occ, 1));
         unsigned long long grid = (unsigned long long)bps * ctx->sm_count;
         unsigned long long need = (batch->n + t.block_size - 1) / t.block_size;
         if (grid > need) grid = need;
+        if (seg.max_blocks && grid > seg.max_blocks) grid = seg.max_blocks;
         // queue slot: [0] the cascade kernel's queue head, [1] the evaporation kernel's
         p.queue_head = queue_head ? queue_head : ctx->queue + (size_t)(ctx->queue_next++ % kQueueSlots) * kQueueStride;
         p.evap_head = p.queue_head + 1;
@@ -232,7 +234,7 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
         e = precision == PNUC_FP64 ? launch_persistent_fp64(p, (int)grid, t.block_size, s)
                                    : launch_persistent_fp32(p, (int)grid, t.block_size, count, s);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
-        e = e == cudaSuccess ? launch_evap_for(ctx, precision, p, t, count, batch->n, s) : e;
+        e = e == cudaSuccess ? launch_evap_for(ctx, precision, p, t, count, batch->n, s, seg.max_blocks) : e;
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], s);
     if (e != cudaSuccess && ev) ctx->tev_used -= 3;  // the slot is the last one taken

@@ -60,12 +60,14 @@ pnuc_status fail(pnuc_ctx *ctx, pnuc_status st, const char *fmt, ...);
 pnuc_status check_tuning(pnuc_ctx *ctx, const pnuc_tuning *t);
 pnuc_status check_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
                         const pnuc_output *out);
-// Merged requests of one launch (device arrays; the SimParams fields seg_first, seg_start
-// and n_seg).
+// Launch options of the serving loop: merged requests (device arrays; the SimParams fields
+// seg_first, seg_start and n_seg) and a cap on each kernel's blocks (0: the resident limit),
+// so that a launch leaves SMs to the launches beside it.
 struct Placement {
     const unsigned long long *first = nullptr;
     const uint32_t *start = nullptr;
     int n = 0;
+    unsigned max_blocks = 0;
 };
 
 // Enqueues the count reset, the queue-head reset and the kernel of one batch on stream s

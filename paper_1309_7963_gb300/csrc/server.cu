@@ -318,6 +318,10 @@ bool admit(pnuc_server *S)
     pnuc_output o = {cap ? (pnuc_secondary *)(d + L.s) : nullptr, cap, (unsigned long long *)(d + GroupLayout::count),
                      (pnuc_residual *)(d + L.r), nullptr};
     Placement seg;
+    {
+        const uint64_t per_block = (uint64_t)S->ctx->tuning[S->cfg.precision].block_size * S->cfg.lane_events;
+        seg.max_blocks = (unsigned)std::min<uint64_t>((n + per_block - 1) / per_block, 1u << 30);
+    }
     if (k > 1) {
         seg.first = (const unsigned long long *)(d + GroupLayout::seg_first);
         seg.start = (const uint32_t *)(d + GroupLayout::seg_start);
@@ -481,6 +485,7 @@ void pnuc_server_default_config(pnuc_server_config *cfg)
     cfg->max_request_events = 1ull << 24;
     cfg->max_merge = 32;
     cfg->merge_events = 1u << 18;
+    cfg->lane_events = 4;
 }
 
 pnuc_status pnuc_server_destroy(pnuc_server *S)
@@ -515,7 +520,7 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg_in, 
     if ((cfg.precision != PNUC_FP32 && cfg.precision != PNUC_FP64) || cfg.streams < 1 || cfg.streams > 64 ||
         cfg.arena_bytes < (1u << 20) || cfg.sec_per_event < 1 || cfg.sec_per_event > 256 || cfg.max_pending < 1 ||
         cfg.max_request_events < 1 || cfg.max_merge < 1 || cfg.max_merge > (uint32_t)kMaxSeg || cfg.merge_events < 1 ||
-        cfg.merge_events > kMaxGroupEvents)
+        cfg.merge_events > kMaxGroupEvents || cfg.lane_events < 1 || cfg.lane_events > 1024)
         return fail(ctx, PNUC_ERR_ARG, "bad server configuration");
     CU(ctx, cudaSetDevice(ctx->cfg.device));
     pnuc_server *S = new pnuc_server();
