@@ -7,18 +7,11 @@ namespace pnuc {
 namespace dev {
 namespace {
 // The FP32 cascade kernel capped at 96 registers: five resident 128-thread blocks per SM
-// instead of four (3.5% faster on GB300 than the 105 registers it uses unbounded).
-#ifndef PNUC_F32_CASCADE_REGS
-#define PNUC_F32_CASCADE_REGS 96
-#endif
-#ifndef PNUC_F32_EVAP_REGS
-#define PNUC_F32_EVAP_REGS 128
-#endif
-__global__ void __maxnreg__(PNUC_F32_CASCADE_REGS) persistent_kernel_f32(const SimParams P)
-{
-    persistent_body<float, false>(P);
-}
-__global__ void __maxnreg__(PNUC_F32_EVAP_REGS) evap_kernel_f32(const SimParams P) { evap_body<float, false>(P); }
+// instead of four (3.5% faster on GB300 than the 105 registers it uses unbounded; caps of 80
+// and 72 with six and seven blocks measured the same and 4% slower). The evaporation kernel
+// fits 96 without spilling (five blocks per SM instead of four; the same time).
+__global__ void __maxnreg__(96) persistent_kernel_f32(const SimParams P) { persistent_body<float, false>(P); }
+__global__ void __maxnreg__(96) evap_kernel_f32(const SimParams P) { evap_body<float, false>(P); }
 }  // namespace
 }  // namespace dev
 
