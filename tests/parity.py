@@ -103,8 +103,12 @@ def observable_table(gres, gsec, ores, osec, n):
     events: mean multiplicity per species and origin (difference in standard errors),
     kinetic-energy spectra (2 MeV bins) and cos(theta) spectra (0.05 bins), the spectra in 1
     degree windows at the angles of the paper's Fig. 2, the residual (Z, A) distribution after
-    evaporation, and the mean E* after the cascade. Returns the table row."""
-    row = {"events": int(n), "multiplicity": {}, "spectra_p": {}, "angle_p": {}, "fig2_p": {}}
+    evaporation, and the mean E* after the cascade; per species and origin also the mean
+    kinetic energy (difference in standard errors) and two-sample Kolmogorov-Smirnov p-values
+    of the unbinned kinetic energies and cos(theta). Returns the table row."""
+    from scipy import stats
+    row = {"events": int(n), "multiplicity": {}, "spectra_p": {}, "angle_p": {}, "fig2_p": {}, "mean_T": {},
+           "ks_T_p": {}, "ks_cos_p": {}}
     for origin, label in ((0, "cascade"), (1, "evaporated")):
         for sp, sname in enumerate(SPECIES):
             gm_sel = (gsec["species"] == sp) & (gsec["origin"] == origin)
@@ -119,6 +123,13 @@ def observable_table(gres, gsec, ores, osec, n):
             row["multiplicity"][key] = {"fp32": float(gm.mean()), "oracle": float(om.mean()), "z": float(z)}
             row["spectra_p"][key] = chi2_p(gsec["T"][gm_sel], osec["T"][om_sel], np.linspace(0, 250, 126))
             row["angle_p"][key] = chi2_p(gsec["uz"][gm_sel], osec["uz"][om_sel], np.linspace(-1, 1, 41))
+            gT, oT = gsec["T"][gm_sel].astype(np.float64), osec["T"][om_sel].astype(np.float64)
+            se_T = np.sqrt(gT.var() / len(gT) + oT.var() / len(oT))
+            row["mean_T"][key] = {"fp32": float(gT.mean()), "oracle": float(oT.mean()),
+                                  "z": float((gT.mean() - oT.mean()) / se_T) if se_T > 0 else 0.0}
+            row["ks_T_p"][key] = float(stats.ks_2samp(gT, oT, method="asymp").pvalue)
+            row["ks_cos_p"][key] = float(stats.ks_2samp(gsec["uz"][gm_sel].astype(np.float64),
+                                                        osec["uz"][om_sel].astype(np.float64), method="asymp").pvalue)
             if origin == 0 or sp > 1:
                 continue
             for ang in FIG2_ANGLES:  # evaporated n and p in 1-degree windows
@@ -127,7 +138,6 @@ def observable_table(gres, gsec, ores, osec, n):
                 ow = om_sel & (osec["uz"] >= lo) & (osec["uz"] < hi)
                 row["fig2_p"][f"{key} {ang:g} deg"] = chi2_p(gsec["T"][gw], osec["T"][ow], np.linspace(0, 60, 31))
     # residual (Z, A) after evaporation: two-sample chi-square over the occupied cells
-    from scipy import stats
     gk = gres["Z_final"].astype(np.int64) * 1000 + gres["A_final"].astype(np.int64)
     ok = ores["Zf"].astype(np.int64) * 1000 + ores["Af"].astype(np.int64)
     cells, inv = np.unique(np.concatenate([gk, ok]), return_inverse=True)
@@ -144,10 +154,12 @@ def observable_table(gres, gsec, ores, osec, n):
 
 
 def assert_observables(row, name):
-    """The bounds: multiplicities within 3 standard errors, chi-square p > 0.01."""
-    for k, v in row["multiplicity"].items():
-        assert abs(v["z"]) < 3.0, (name, k, v)
-    for field in ("spectra_p", "angle_p", "fig2_p"):
+    """The bounds: multiplicities and mean kinetic energies within 3 standard errors,
+    chi-square and Kolmogorov-Smirnov p > 0.01."""
+    for field in ("multiplicity", "mean_T"):
+        for k, v in row[field].items():
+            assert abs(v["z"]) < 3.0, (name, field, k, v)
+    for field in ("spectra_p", "angle_p", "fig2_p", "ks_T_p", "ks_cos_p"):
         for k, p in row[field].items():
             assert p > 0.01, (name, field, k, p)
     assert row["residual_ZA_p"] > 0.01, (name, row["residual_ZA_p"])
