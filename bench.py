@@ -90,7 +90,7 @@ def profile_values() -> dict:
     out = {}
     for k in ("cascade", "evaporation"):
         out[k] = {f: float(kv[f"{k}_{f}"]) for f in ("bytes_per_event", "issue_active_pct", "threads_per_inst",
-                                                     "fp64_pipe_pct") if f"{k}_{f}" in kv}
+                                                     "fp64_pipe_pct", "warp_inst_per_event") if f"{k}_{f}" in kv}
     return out
 
 
@@ -434,6 +434,19 @@ def main():
                          "frac": achieved / peaks["fp64_fma"],
                          "traffic": pk["bytes_per_event"] * n if "bytes_per_event" in pk else None,
                          "ncu": {k: v for k, v in pk.items() if k != "bytes_per_event"} or None}
+    # the issue-rate roofline: warp instructions per event (ncu capture of the same kernel
+    # sources) x events per second of this run, against one warp instruction per cycle on
+    # each of the 4 schedulers of every SM at the SM clock sampled during the timed region
+    sm_hz = ((clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 0) * 1e6
+    issue_peak = 4 * torch.cuda.get_device_properties(local).multi_processor_count * sm_hz
+    for name in kernels:
+        ipe = prof.get(name, {}).get("warp_inst_per_event")
+        if ipe and issue_peak > 0:
+            rate = ipe * n / (kernels[name]["ms_per_launch"] * 1e-3)
+            kernels[name]["issue"] = {"warp_inst_per_event": ipe, "achieved": rate / 1e9, "peak": issue_peak / 1e9,
+                                      "unit": "G warp-inst/s", "frac": rate / issue_peak}
+        else:
+            kernels[name]["issue"] = None
     top = max(kernels, key=lambda k: kernels[k]["ms_per_launch"])
     kt = kernels[top]
     roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"{top} kernel (FP32 mode)", "achieved": kt["achieved"],
@@ -441,6 +454,7 @@ def main():
                 "traffic_note": "DRAM bytes per launch, scaled by events from an ncu capture of 8e5 events; "
                                 "ncu: issue-slot use and active threads per instruction of the same capture",
                 "peak_source": "pnuc_measure_peaks, FP64 FMA lane-ops/s measured in this run",
+                "issue_rate": kt["issue"],
                 "timed_launches": ktimes["launches"], "kernels": kernels, "peaks_lane_ops_per_s": peaks,
                 "work_per_event": {k: v / n for k, v in counters.items() if not k.startswith("cycles")}}
     cyc = {k[7:]: counters[k] for k in counters if k.startswith("cycles_")}
