@@ -188,3 +188,12 @@ def test_overflow_inside_a_merged_launch(ctx):
         assert st["completed"] == len(reqs) and st["reruns"] >= len(reqs)
     finally:
         srv.close()
+
+
+def test_server_configuration_is_checked(ctx):
+    for bad in (dict(max_merge=0), dict(max_merge=65), dict(merge_events=0), dict(merge_events=(1 << 22) + 1),
+                dict(lane_events=0), dict(lane_events=1025), dict(streams=65), dict(sec_per_event=0)):
+        with pytest.raises(pnuc.PnucError):
+            pnuc.Server(ctx, precision="fp32", arena_bytes=64 << 20, **bad)
+    srv = pnuc.Server(ctx, precision="fp32", arena_bytes=64 << 20, max_merge=64, merge_events=1 << 22, lane_events=1024)
+    srv.close()
