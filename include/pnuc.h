@@ -285,12 +285,13 @@ pnuc_status pnuc_graph_destroy(pnuc_graph *graph);
 /* Serving loop (not in the paper: it motivates the code as a component of a GPU proton
  * transport Monte Carlo, §1 and §4.2). A transport driver submits interaction requests as
  * they arise; a scheduler thread admits queued requests in order whenever one of `streams`
- * CUDA streams is free and both the device output arena and a pinned host arena of
- * arena_bytes have room for the request's inputs, residuals and sec_per_event secondaries
- * per event (memory-based admission). Queued requests with the same seed are merged, up to
- * max_merge of them and merge_events events, into one persistent launch on a free stream, each
- * event keeping its own id; a partition kernel then gives every request a contiguous range of
- * secondaries. Launches on different streams overlap on the GPU (continuous batching). A
+ * CUDA streams is free and both a device arena (the inputs, and a merged launch's
+ * secondaries) and a pinned host arena (residuals and sec_per_event secondaries per event,
+ * written there by the kernels) of arena_bytes each have room (memory-based admission).
+ * Queued requests with the same seed are merged, up to max_merge of them and merge_events
+ * events, into one persistent launch on a free stream, each event keeping its own id; a
+ * partition kernel then gives every request a contiguous range of secondaries. Launches on
+ * different streams overlap on the GPU (continuous batching). A
  * request that produces more secondaries than reserved is run again alone, with room for
  * exactly its count; as results depend only on (seed, event id), every request's results
  * equal those of a lone pnuc_simulate call. Latency is measured from submit to results ready
@@ -317,7 +318,7 @@ typedef struct {
     double latency_p50_ms, latency_p99_ms, latency_max_ms; /* submit -> results on the host */
     double queue_p50_ms, queue_p99_ms;                     /* submit -> admission */
     double elapsed_s, events_per_s;                        /* since creation or the last reset */
-    uint64_t arena_peak_bytes;
+    uint64_t arena_peak_bytes;                             /* largest use of either arena */
     uint64_t launches;                                     /* kernel launches (merged groups and re-runs) */
 } pnuc_server_stats;
 

@@ -95,9 +95,11 @@ struct Request {
 
 auto up = [](size_t b) { return (b + 255) / 256 * 256; };
 
-// Byte offsets of one group in the arenas. Device: header, inputs, residuals, the launch's
-// secondaries, and (for more than one request) the partitioned copy; host: header,
-// residuals, the partitioned secondaries (or the launch's for a single request).
+// Byte offsets of one group in the arenas. Device: header, inputs, and (for more than one
+// request) the launch's secondaries; host: header, residuals, secondaries. The kernels write
+// the residuals, and a single request's secondaries, straight into the pinned host region
+// (mapped memory); the partition kernel writes merged requests' secondaries there too, so
+// only the counts are copied back.
 struct GroupLayout {
     // header: [0] launch count, [8 .. 8+8*kMaxSeg) per-request counts (device -> host), then
     // the segment tables (host -> device): seg_start (u32, kMaxSeg + 1), seg_first (u64,
@@ -106,19 +108,18 @@ struct GroupLayout {
                             cap_start = seg_first + 8 * kMaxSeg, header = 2304;
     static_assert(seg_start + 4 * (kMaxSeg + 1) <= seg_first && cap_start + 8 * (kMaxSeg + 1) <= header,
                   "group header fields overlap");
-    size_t e, t, r, s, p, dev_total, host_r, host_s, host_total;
+    size_t e, t, s, dev_total, host_r, host_s, host_total;
     GroupLayout(uint64_t n, uint64_t cap, int n_seg)
     {
         e = header;
         t = e + up(8 * n);
-        r = t + up(4 * n);
-        s = r + up(sizeof(pnuc_residual) * n);
-        p = s + up(sizeof(pnuc_secondary) * cap);
-        dev_total = n_seg > 1 ? p + up(sizeof(pnuc_secondary) * cap) : p;
+        s = t + up(4 * n);
+        dev_total = n_seg > 1 ? s + up(sizeof(pnuc_secondary) * cap) : s;
         host_r = header;
         host_s = host_r + up(sizeof(pnuc_residual) * n);
         host_total = host_s + up(sizeof(pnuc_secondary) * cap);
     }
+    bool fits(uint64_t arena) const { return dev_total <= arena && host_total <= arena; }
 };
 
 struct Group {
@@ -165,8 +166,9 @@ __global__ void partition_kernel(const uint4 *__restrict__ in, const unsigned lo
 struct pnuc_server {
     pnuc_ctx *ctx = nullptr;
     pnuc_server_config cfg;
-    unsigned char *dev = nullptr;   // device arena
-    unsigned char *host = nullptr;  // pinned host arena (same size)
+    unsigned char *dev = nullptr;       // device arena
+    unsigned char *host = nullptr;      // pinned host arena (same size)
+    unsigned char *host_dev = nullptr;  // the host arena's device address
     std::unique_ptr<Arena> dev_arena, host_arena;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
@@ -314,9 +316,11 @@ bool admit(pnuc_server *S)
                         GroupLayout::header - GroupLayout::seg_start, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(d + GroupLayout::seg_count, 0, 8 * kMaxSeg, s) != cudaSuccess)
         st = PNUC_ERR_CUDA;
+    unsigned char *hd = S->host_dev + hoff;  // the host region, as the kernels address it
     pnuc_batch b = {(const double *)(d + L.e), (const int32_t *)(d + L.t), n, cand[0]->seed, cand[0]->first};
-    pnuc_output o = {cap ? (pnuc_secondary *)(d + L.s) : nullptr, cap, (unsigned long long *)(d + GroupLayout::count),
-                     (pnuc_residual *)(d + L.r), nullptr};
+    pnuc_secondary *launch_sec = k > 1 ? (pnuc_secondary *)(d + L.s) : (pnuc_secondary *)(hd + L.host_s);
+    pnuc_output o = {cap ? launch_sec : nullptr, cap, (unsigned long long *)(d + GroupLayout::count),
+                     (pnuc_residual *)(hd + L.host_r), nullptr};
     Placement seg;
     {
         const uint64_t per_block = (uint64_t)S->ctx->tuning[S->cfg.precision].block_size * S->cfg.lane_events;
@@ -335,17 +339,13 @@ bool admit(pnuc_server *S)
         partition_kernel<<<grid, 256, 0, s>>>(
             (const uint4 *)(d + L.s), (const unsigned long long *)(d + GroupLayout::count), cap,
             (const uint32_t *)(d + GroupLayout::seg_start), (const unsigned long long *)(d + GroupLayout::cap_start),
-            k, (unsigned long long *)(d + GroupLayout::seg_count), (uint4 *)(d + L.p));
+            k, (unsigned long long *)(d + GroupLayout::seg_count), (uint4 *)(hd + L.host_s));
         if (cudaGetLastError() != cudaSuccess) st = PNUC_ERR_CUDA;
     }
-    // counts, residuals and the secondary reservation come back in stream order behind the
-    // kernels, so one completion event covers the whole group
-    if (st == PNUC_OK &&
-        (cudaMemcpyAsync(h, d, GroupLayout::seg_start, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         cudaMemcpyAsync(h + L.host_r, d + L.r, sizeof(pnuc_residual) * n, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         (cap && cudaMemcpyAsync(h + L.host_s, d + (k > 1 ? L.p : L.s), sizeof(pnuc_secondary) * cap,
-                                 cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
-         cudaEventRecord(S->events[si], s) != cudaSuccess))
+    // the counts come back in stream order behind the kernels (the records are already in the
+    // host region), so one completion event covers the whole group
+    if (st == PNUC_OK && (cudaMemcpyAsync(h, d, GroupLayout::seg_start, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                          cudaEventRecord(S->events[si], s) != cudaSuccess))
         st = PNUC_ERR_CUDA;
     S->launches++;
     const uint64_t gid = g->id;
@@ -392,7 +392,7 @@ void complete(pnuc_server *S, Group &g)
             leave_group(S, r);
             r.solo = true;
             r.cap = std::max<uint64_t>(r.cap, cnt);
-            if (GroupLayout(r.n, r.cap, 1).dev_total > S->cfg.arena_bytes) {
+            if (!GroupLayout(r.n, r.cap, 1).fits(S->cfg.arena_bytes)) {
                 finish(S, r, kFailed, PNUC_ERR_CAPACITY);
                 continue;
             }
@@ -533,6 +533,12 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg_in, 
         return fail(ctx, PNUC_ERR_CUDA, "server arenas of %llu bytes could not be allocated",
                     (unsigned long long)cfg.arena_bytes);
     }
+    void *hd = nullptr;
+    if (cudaHostGetDevicePointer(&hd, S->host, 0) != cudaSuccess || !hd) {
+        pnuc_server_destroy(S);
+        return fail(ctx, PNUC_ERR_CUDA, "the pinned host arena is not mapped into the device's address space");
+    }
+    S->host_dev = static_cast<unsigned char *>(hd);
     S->dev_arena.reset(new Arena(cfg.arena_bytes));
     S->host_arena.reset(new Arena(cfg.arena_bytes));
     for (int k = 0; k < cfg.streams; ++k) {
@@ -562,7 +568,7 @@ pnuc_status pnuc_server_submit(pnuc_server *S, const double *energies, const int
     if (n == 0 || n > S->cfg.max_request_events)
         return fail(S->ctx, PNUC_ERR_ARG, "request of %llu events", (unsigned long long)n);
     uint64_t cap = n * S->cfg.sec_per_event;
-    if (GroupLayout(n, cap, 1).dev_total > S->cfg.arena_bytes)
+    if (!GroupLayout(n, cap, 1).fits(S->cfg.arena_bytes))
         return fail(S->ctx, PNUC_ERR_ARG, "request of %llu events can never fit the %llu-byte arena",
                     (unsigned long long)n, (unsigned long long)S->cfg.arena_bytes);
     std::unique_ptr<Request> r(new Request());
@@ -675,7 +681,7 @@ pnuc_status pnuc_server_get_stats(pnuc_server *S, pnuc_server_stats *out)
     double secs = std::chrono::duration<double>(Clock::now() - S->t_start).count();
     out->elapsed_s = secs;
     out->events_per_s = secs > 0 ? S->events_done / secs : 0.0;
-    out->arena_peak_bytes = S->dev_arena->peak();
+    out->arena_peak_bytes = std::max(S->dev_arena->peak(), S->host_arena->peak());
     out->launches = S->launches;
     return PNUC_OK;
 }
