@@ -2,7 +2,8 @@
  * pnuc.h — C ABI of libpnuc: event-parallel Monte Carlo of non-elastic proton–nucleus
  * interactions (20–250 MeV) on one GB300 GPU, after arXiv:1309.7963.
  *
- * One event = one incident proton on one target nucleus: an intranuclear cascade
+ * One event = one incident proton (or, as an extension, a neutron: pnuc_batch.projectiles)
+ * on one target nucleus: an intranuclear cascade
  * (paper §2.3) on a 15-shell Fermi-gas nucleus (§2.2, Eq. 1), then evaporation of
  * n, p, d, t, 3He and alpha down to the residual nucleus (§2.4). Every event depends only
  * on (seed, event id): its random numbers are the stream of Philox4x64-10 with key
