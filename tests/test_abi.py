@@ -61,3 +61,39 @@ def test_binding_refuses_without_gpu():
         assert "no CPU fallback" in str(e)
     else:
         raise AssertionError("Context must fail loudly without a GPU")
+
+
+def test_python_mirrors_match_the_header(tmp_path):
+    """Every struct of pnuc.h, compiled by the host C compiler: its size and each field's
+    offset equal those of the binding's ctypes / numpy mirror."""
+    import subprocess
+    mirrors = {name: getattr(pnuc, name) for name in (
+        "pnuc_config", "pnuc_batch", "pnuc_output", "pnuc_tuning", "pnuc_target_info", "pnuc_peaks",
+        "pnuc_tally_spec", "pnuc_server_config", "pnuc_server_stats")}
+    dtypes = {"pnuc_secondary": pnuc.SECONDARY_DTYPE, "pnuc_residual": pnuc.RESIDUAL_DTYPE}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pnuc.h"', "int main(void) {"]
+    for name, cls in mirrors.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    for name, dt in dtypes.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for f in dt.names:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, val = ln.split()
+        got[(name, field)] = int(val)
+    for name, cls in mirrors.items():
+        assert got[(name, "sizeof")] == C.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
+    for name, dt in dtypes.items():
+        assert got[(name, "sizeof")] == dt.itemsize, name
+        for f in dt.names:
+            assert got[(name, f)] == dt.fields[f][1], (name, f)
