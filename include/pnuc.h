@@ -336,6 +336,12 @@ pnuc_status pnuc_server_submit(pnuc_server *server, const double *energies, cons
 /* Waits up to timeout_ms (negative: no limit) for the request; PNUC_ERR_TIMEOUT if it is not
  * done by then, else the request's status, and *n_secondaries its number of secondaries. */
 pnuc_status pnuc_server_wait(pnuc_server *server, uint64_t ticket, int32_t timeout_ms, uint64_t *n_secondaries);
+/* Waits up to timeout_ms (negative: no limit) for any request to finish that no earlier
+ * pnuc_server_wait_any returned, in the order they finished; PNUC_ERR_TIMEOUT if none does,
+ * else PNUC_OK with *ticket the finished request (done or failed: view, fetch or release it
+ * as after pnuc_server_wait). Requests released before they are returned are skipped. Lets
+ * a driver take results as they complete rather than in submission order. */
+pnuc_status pnuc_server_wait_any(pnuc_server *server, int32_t timeout_ms, uint64_t *ticket);
 /* Copies a finished request's residuals (n records) and secondaries (host buffers; capacity
  * at least its count, else PNUC_ERR_CAPACITY and nothing is released) and releases it.
  * PNUC_ERR_STATE if it is not finished; a failed request returns its error and is released.

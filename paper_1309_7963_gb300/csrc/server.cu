@@ -176,6 +176,7 @@ struct pnuc_server {
     std::mutex mu;
     std::condition_variable cv;
     std::deque<uint64_t> pending;
+    std::deque<uint64_t> finished;  // tickets in the order they finished, for wait_any
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
     std::unordered_map<uint64_t, std::unique_ptr<Group>> groups;
     uint64_t next_ticket = 1, next_group = 1;
@@ -211,6 +212,11 @@ void finish(pnuc_server *S, Request &r, State st, pnuc_status status)
     r.state = st;
     r.status = status;
     r.t_done = Clock::now();
+    S->finished.push_back(r.ticket);
+    if (S->finished.size() > 2 * S->reqs.size() + 64)  // drop released tickets (amortised)
+        S->finished.erase(std::remove_if(S->finished.begin(), S->finished.end(),
+                                         [&](uint64_t t) { return S->reqs.find(t) == S->reqs.end(); }),
+                          S->finished.end());
     if (st == kDone) {
         S->completed++;
         S->events_done += r.n;
@@ -604,6 +610,22 @@ pnuc_status pnuc_server_wait(pnuc_server *S, uint64_t ticket, int32_t timeout_ms
     else if (!S->cv.wait_for(lock, std::chrono::milliseconds(timeout_ms), done)) return PNUC_ERR_TIMEOUT;
     if (n_secondaries) *n_secondaries = r->count;
     return r->status;
+}
+
+pnuc_status pnuc_server_wait_any(pnuc_server *S, int32_t timeout_ms, uint64_t *ticket)
+{
+    if (!S || !ticket) return PNUC_ERR_ARG;
+    std::unique_lock<std::mutex> lock(S->mu);
+    auto ready = [&] {
+        while (!S->finished.empty() && S->reqs.find(S->finished.front()) == S->reqs.end())
+            S->finished.pop_front();  // released already
+        return !S->finished.empty();
+    };
+    if (timeout_ms < 0) S->cv.wait(lock, ready);
+    else if (!S->cv.wait_for(lock, std::chrono::milliseconds(timeout_ms), ready)) return PNUC_ERR_TIMEOUT;
+    *ticket = S->finished.front();
+    S->finished.pop_front();
+    return PNUC_OK;
 }
 
 pnuc_status pnuc_server_fetch(pnuc_server *S, uint64_t ticket, pnuc_secondary *secondaries, uint64_t capacity,

@@ -18,30 +18,34 @@ def run(server: Server, requests: list, target_ids: np.ndarray, seed: int, keep=
     """Plays `requests` against `server` in real time. target_ids maps the workload's target
     index to the context's target id. keep(request, secondaries, residuals) is called for
     each result if given, with views valid only during the call (copy what you keep).
-    Returns client-side latencies (ms, submit to release) and throughput."""
+    Results are taken in the order they finish (pnuc_server_wait_any), as a transport code
+    continues whichever histories are ready. Returns client-side latencies (ms, submit to
+    release) and throughput."""
     done = {}
-    order = []
+    meta = {}  # ticket -> (request, submit time)
     lock = threading.Condition()
+    finished = [False]
     t0 = time.perf_counter()
 
     def consumer():
-        k = 0
         while True:
             with lock:
-                while k >= len(order) and not finished[0]:
-                    lock.wait(0.05)
-                if k >= len(order):
+                if finished[0] and len(done) >= len(meta):
                     return
-                tk, req, t_sub = order[k]
-            k += 1
-            server.wait(tk, -1)
+            tk = server.wait_any(20)
+            if tk is None:
+                continue
+            with lock:  # the submitting thread records the ticket just after submit returns
+                while tk not in meta:
+                    lock.wait(0.001)
+                req, t_sub = meta[tk]
             sec, res = server.view(tk)  # zero-copy: the results where they landed
             if keep is not None:
                 keep(req, sec, res)
             server.release(tk)
-            done[tk] = (t_sub, time.perf_counter(), req["energies"].shape[0])
+            with lock:
+                done[tk] = (t_sub, time.perf_counter(), req["energies"].shape[0])
 
-    finished = [False]
     th = threading.Thread(target=consumer, daemon=True)
     th.start()
     for req in requests:
@@ -59,7 +63,7 @@ def run(server: Server, requests: list, target_ids: np.ndarray, seed: int, keep=
                     raise
                 time.sleep(0.001)
         with lock:
-            order.append((tk, req, time.perf_counter()))
+            meta[tk] = (req, time.perf_counter())
             lock.notify_all()
     with lock:
         finished[0] = True

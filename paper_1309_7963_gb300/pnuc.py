@@ -143,6 +143,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_server_create.argtypes = [vp, C.POINTER(pnuc_server_config), C.POINTER(vp)]
     L.pnuc_server_submit.argtypes = [vp, vp, vp, u64, u64, u64, C.POINTER(u64)]
     L.pnuc_server_wait.argtypes = [vp, u64, C.c_int32, C.POINTER(u64)]
+    L.pnuc_server_wait_any.argtypes = [vp, C.c_int32, C.POINTER(u64)]
     L.pnuc_server_fetch.argtypes = [vp, u64, vp, u64, vp]
     L.pnuc_server_view.argtypes = [vp, u64, C.POINTER(vp), C.POINTER(u64), C.POINTER(vp)]
     L.pnuc_server_release.argtypes = [vp, u64]
@@ -154,7 +155,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                  "pnuc_set_tuning",
                  "pnuc_measure_peaks", "pnuc_autotune", "pnuc_save_tuning", "pnuc_load_tuning",
                  "pnuc_graph_create", "pnuc_graph_update", "pnuc_graph_launch", "pnuc_graph_destroy",
-                 "pnuc_server_create", "pnuc_server_submit", "pnuc_server_wait", "pnuc_server_fetch",
+                 "pnuc_server_create", "pnuc_server_submit", "pnuc_server_wait", "pnuc_server_wait_any",
+                 "pnuc_server_fetch",
                  "pnuc_server_get_stats", "pnuc_server_reset_stats", "pnuc_server_destroy"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -456,6 +458,15 @@ class Server:
             return None
         self.ctx._check(st)
         return n.value
+
+    def wait_any(self, timeout_ms: int = -1):
+        """Ticket of the next request to have finished (completion order), or None on timeout."""
+        tk = C.c_uint64()
+        st = self.lib.pnuc_server_wait_any(self.handle, timeout_ms, C.byref(tk))
+        if st == self.TIMEOUT:
+            return None
+        self.ctx._check(st)
+        return tk.value
 
     def fetch(self, ticket: int, n_secondaries: int):
         sec = np.empty(max(n_secondaries, 1), SECONDARY_DTYPE)

@@ -197,3 +197,29 @@ def test_server_configuration_is_checked(ctx):
             pnuc.Server(ctx, precision="fp32", arena_bytes=64 << 20, **bad)
     srv = pnuc.Server(ctx, precision="fp32", arena_bytes=64 << 20, max_merge=64, merge_events=1 << 22, lane_events=1024)
     srv.close()
+
+
+def test_wait_any_returns_each_finished_request_once(ctx):
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(10, rate_hz=1e6, seed=17, min_batch=500, max_batch=50_000)
+    srv = pnuc.Server(ctx, precision="fp32", streams=3, arena_bytes=256 << 20, max_merge=1)
+    try:
+        tickets = [srv.submit(r["energies"], tids[r["tidx"]], 8, r["first_event_id"]) for r in reqs]
+        by_ticket = dict(zip(tickets, reqs))
+        # one request waited for and released directly: wait_any must skip it
+        srv.wait(tickets[3])
+        srv.release(tickets[3])
+        seen = []
+        while len(seen) < len(tickets) - 1:
+            tk = srv.wait_any(10_000)
+            assert tk is not None and tk not in seen and tk != tickets[3]
+            seen.append(tk)
+            sec, res = srv.view(tk)
+            ref_sec, ref_res = alone(ctx, by_ticket[tk], tids, 8)
+            assert np.array_equal(res, ref_res)
+            assert np.array_equal(pnuc.sort_secondaries(sec.copy()), ref_sec)
+            srv.release(tk)
+        assert sorted(seen) == sorted(t for t in tickets if t != tickets[3])
+        assert srv.wait_any(50) is None  # nothing left: the wait times out
+    finally:
+        srv.close()
