@@ -295,8 +295,10 @@ class Context:
                                         C.c_void_p(s)))
         return hists
 
-    def _structs(self, energies, target_ids, seed, first_event_id, out):
-        b = pnuc_batch(_ptr(energies), _ptr(target_ids), int(energies.shape[0]), seed, first_event_id)
+    def _structs(self, energies, target_ids, seed, first_event_id, out, projectiles=None, event_ids=None):
+        b = pnuc_batch(_ptr(energies), _ptr(target_ids), int(energies.shape[0]), seed, first_event_id,
+                       _ptr(projectiles) if projectiles is not None else None,
+                       _ptr(event_ids) if event_ids is not None else None)
         o = pnuc_output(_ptr(out.secondaries), out.secondaries.shape[0], _ptr(out.count), _ptr(out.residuals),
                         _ptr(out.counters))
         return b, o
@@ -320,9 +322,10 @@ class Context:
         self._check(self.lib.pnuc_load_tuning(self.handle, os.fsencode(path)))
 
     def graph(self, energies, target_ids, seed: int, out: "Result", first_event_id: int = 0,
-              precision: str = "fp32", method: str = "persistent") -> "Graph":
-        """pnuc_graph_create: a CUDA-graph plan of one launch for fixed buffers."""
-        return Graph(self, energies, target_ids, seed, out, first_event_id, precision, method)
+              precision: str = "fp32", method: str = "persistent", projectiles=None, event_ids=None) -> "Graph":
+        """pnuc_graph_create: a CUDA-graph plan of one launch for fixed buffers (optional
+        projectiles uint8 and event_ids int64 device tensors, as in simulate)."""
+        return Graph(self, energies, target_ids, seed, out, first_event_id, precision, method, projectiles, event_ids)
 
     def alloc(self, n: int, capacity: int | None = None, counters: bool = False) -> Result:
         torch = self._torch
@@ -393,18 +396,19 @@ class Context:
 class Graph:
     """A CUDA-graph launch plan (pnuc_graph_*); keeps its buffers alive."""
 
-    def __init__(self, ctx: Context, energies, target_ids, seed, out, first_event_id, precision, method):
+    def __init__(self, ctx: Context, energies, target_ids, seed, out, first_event_id, precision, method,
+                 projectiles=None, event_ids=None):
         self.ctx, self.handle = ctx, C.c_void_p()
-        self._keep = (energies, target_ids, out)
-        b, o = ctx._structs(energies, target_ids, seed, first_event_id, out)
+        self._keep = (energies, target_ids, out, projectiles, event_ids)
+        b, o = ctx._structs(energies, target_ids, seed, first_event_id, out, projectiles, event_ids)
         ctx._check(ctx.lib.pnuc_graph_create(ctx.handle, PRECISION[precision], METHOD[method], C.byref(b), C.byref(o),
                                              C.byref(self.handle)))
         self.out = out
 
-    def update(self, energies, target_ids, seed, out, first_event_id=0):
-        b, o = self.ctx._structs(energies, target_ids, seed, first_event_id, out)
+    def update(self, energies, target_ids, seed, out, first_event_id=0, projectiles=None, event_ids=None):
+        b, o = self.ctx._structs(energies, target_ids, seed, first_event_id, out, projectiles, event_ids)
         self.ctx._check(self.ctx.lib.pnuc_graph_update(self.handle, C.byref(b), C.byref(o)))
-        self._keep = (energies, target_ids, out)
+        self._keep = (energies, target_ids, out, projectiles, event_ids)
         self.out = out
 
     def launch(self, stream=None):

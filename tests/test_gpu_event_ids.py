@@ -69,3 +69,25 @@ def test_event_ids_are_checked(ctx):
         ctx.simulate(e, t, seed=1, event_ids=torch.arange(8, device="cuda", dtype=torch.int32))
     with pytest.raises(ValueError):
         ctx.simulate(e, t, seed=1, event_ids=torch.arange(7, device="cuda", dtype=torch.int64))
+
+
+def test_graph_plan_with_ids_and_projectiles(ctx):
+    """A CUDA-graph plan carries per-event ids and incident species like a direct launch."""
+    import torch
+    w = inputs.mixed(3000, seed=8)
+    tids = np.array([ctx.create_target(*za) for za in w.targets], np.int32)
+    e = torch.tensor(w.energies, device="cuda")
+    t = torch.tensor(tids[w.tidx], device="cuda")
+    rng = np.random.default_rng(9)
+    ids = torch.tensor(rng.integers(0, 1 << 40, w.n), dtype=torch.int64, device="cuda")
+    proj = torch.tensor(rng.integers(0, 2, w.n), dtype=torch.uint8, device="cuda")
+    ref = ctx.simulate(e, t, seed=w.seed, capacity=40 * w.n, projectiles=proj, event_ids=ids)
+    out = ctx.alloc(w.n, capacity=40 * w.n)
+    g = ctx.graph(e, t, seed=w.seed, out=out, projectiles=proj, event_ids=ids)
+    try:
+        g.launch()
+        torch.cuda.synchronize()
+    finally:
+        g.close()
+    assert np.array_equal(out.residuals_np(), ref.residuals_np())
+    assert np.array_equal(pnuc.sort_secondaries(out.secondaries_np()), pnuc.sort_secondaries(ref.secondaries_np()))
