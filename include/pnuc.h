@@ -333,6 +333,13 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg, pnu
  * are queued (submit again later). Thread-safe. */
 pnuc_status pnuc_server_submit(pnuc_server *server, const double *energies, const int32_t *target_ids, uint64_t n,
                                uint64_t seed, uint64_t first_event_id, uint64_t *ticket);
+/* pnuc_server_submit with the incident nucleon of each event (projectiles: host, n entries,
+ * 1 proton, 0 neutron, other values flagged PNUC_FLAG_BAD_INPUT as in pnuc_batch; NULL =
+ * protons): a transport code's secondary neutrons go through the same loop. Requests with
+ * and without species merge as usual. */
+pnuc_status pnuc_server_submit_nucleons(pnuc_server *server, const double *energies, const int32_t *target_ids,
+                                        const uint8_t *projectiles, uint64_t n, uint64_t seed,
+                                        uint64_t first_event_id, uint64_t *ticket);
 /* Waits up to timeout_ms (negative: no limit) for the request; PNUC_ERR_TIMEOUT if it is not
  * done by then, else the request's status, and *n_secondaries its number of secondaries. */
 pnuc_status pnuc_server_wait(pnuc_server *server, uint64_t ticket, int32_t timeout_ms, uint64_t *n_secondaries);

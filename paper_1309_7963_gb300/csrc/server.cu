@@ -81,6 +81,7 @@ struct Request {
     uint64_t ticket, n, seed, first;
     std::vector<double> e;
     std::vector<int32_t> t;
+    std::vector<uint8_t> proj;  // incident species per event (1 proton, 0 neutron); empty = protons
     uint64_t cap = 0;  // secondaries reserved
     bool solo = false; // run alone (after an overflow)
     State state = kPending;
@@ -108,12 +109,13 @@ struct GroupLayout {
                             cap_start = seg_first + 8 * kMaxSeg, header = 2304;
     static_assert(seg_start + 4 * (kMaxSeg + 1) <= seg_first && cap_start + 8 * (kMaxSeg + 1) <= header,
                   "group header fields overlap");
-    size_t e, t, s, dev_total, host_r, host_s, host_total;
+    size_t e, t, pj, s, dev_total, host_r, host_s, host_total;
     GroupLayout(uint64_t n, uint64_t cap, int n_seg)
     {
         e = header;
         t = e + up(8 * n);
-        s = t + up(4 * n);
+        pj = t + up(4 * n);  // incident species, when a request of the group has them
+        s = pj + up(n);
         dev_total = n_seg > 1 ? s + up(sizeof(pnuc_secondary) * cap) : s;
         host_r = header;
         host_s = host_r + up(sizeof(pnuc_residual) * n);
@@ -293,8 +295,10 @@ bool admit(pnuc_server *S)
     unsigned long long *h_first = reinterpret_cast<unsigned long long *>(h + GroupLayout::seg_first);
     unsigned long long *h_cap = reinterpret_cast<unsigned long long *>(h + GroupLayout::cap_start);
     // the residual area of the host region stages the inputs until the results overwrite it
-    // (in stream order): 12 bytes per event in a 64-byte record
+    // (in stream order): 13 bytes per event in a 64-byte record
     unsigned char *h_in = h + L.host_r;
+    bool any_proj = false;
+    for (int j = 0; j < k; ++j) any_proj = any_proj || !cand[j]->proj.empty();
     uint64_t pos = 0, cpos = 0;
     for (int j = 0; j < k; ++j) {
         Request &r = *cand[j];
@@ -303,6 +307,10 @@ bool admit(pnuc_server *S)
         h_cap[j] = cpos;
         memcpy(h_in + 8 * pos, r.e.data(), 8 * r.n);
         memcpy(h_in + 8 * n + 4 * pos, r.t.data(), 4 * r.n);
+        if (any_proj) {
+            if (r.proj.empty()) memset(h_in + 12 * n + pos, 1, r.n);
+            else memcpy(h_in + 12 * n + pos, r.proj.data(), r.n);
+        }
         pos += r.n;
         cpos += r.cap;
         r.state = kRunning;
@@ -315,15 +323,17 @@ bool admit(pnuc_server *S)
     for (int j = 0; j < k; ++j) S->pending.pop_front();
     cudaStream_t s = S->streams[si];
     pnuc_status st = PNUC_OK;
-    static_assert(sizeof(pnuc_residual) >= 12, "inputs are staged in the residual area");
+    static_assert(sizeof(pnuc_residual) >= 13, "inputs are staged in the residual area");
     if (cudaMemcpyAsync(d + L.e, h_in, 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d + L.t, h_in + 8 * n, 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        (any_proj && cudaMemcpyAsync(d + L.pj, h_in + 12 * n, n, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
         cudaMemcpyAsync(d + GroupLayout::seg_start, h + GroupLayout::seg_start,
                         GroupLayout::header - GroupLayout::seg_start, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(d + GroupLayout::seg_count, 0, 8 * kMaxSeg, s) != cudaSuccess)
         st = PNUC_ERR_CUDA;
     unsigned char *hd = S->host_dev + hoff;  // the host region, as the kernels address it
-    pnuc_batch b = {(const double *)(d + L.e), (const int32_t *)(d + L.t), n, cand[0]->seed, cand[0]->first};
+    pnuc_batch b = {(const double *)(d + L.e), (const int32_t *)(d + L.t), n, cand[0]->seed, cand[0]->first,
+                    any_proj ? (const uint8_t *)(d + L.pj) : nullptr};
     pnuc_secondary *launch_sec = k > 1 ? (pnuc_secondary *)(d + L.s) : (pnuc_secondary *)(hd + L.host_s);
     pnuc_output o = {cap ? launch_sec : nullptr, cap, (unsigned long long *)(d + GroupLayout::count),
                      (pnuc_residual *)(hd + L.host_r), nullptr};
@@ -570,6 +580,13 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg_in, 
 pnuc_status pnuc_server_submit(pnuc_server *S, const double *energies, const int32_t *target_ids, uint64_t n,
                                uint64_t seed, uint64_t first_event_id, uint64_t *ticket)
 {
+    return pnuc_server_submit_nucleons(S, energies, target_ids, nullptr, n, seed, first_event_id, ticket);
+}
+
+pnuc_status pnuc_server_submit_nucleons(pnuc_server *S, const double *energies, const int32_t *target_ids,
+                                        const uint8_t *projectiles, uint64_t n, uint64_t seed,
+                                        uint64_t first_event_id, uint64_t *ticket)
+{
     if (!S || !ticket || (n > 0 && (!energies || !target_ids))) return PNUC_ERR_ARG;
     if (n == 0 || n > S->cfg.max_request_events)
         return fail(S->ctx, PNUC_ERR_ARG, "request of %llu events", (unsigned long long)n);
@@ -585,6 +602,7 @@ pnuc_status pnuc_server_submit(pnuc_server *S, const double *energies, const int
     r->solo = n > kMaxGroupEvents;
     r->e.assign(energies, energies + n);
     r->t.assign(target_ids, target_ids + n);
+    if (projectiles) r->proj.assign(projectiles, projectiles + n);
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lock(S->mu);

@@ -142,6 +142,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_server_default_config.restype = None
     L.pnuc_server_create.argtypes = [vp, C.POINTER(pnuc_server_config), C.POINTER(vp)]
     L.pnuc_server_submit.argtypes = [vp, vp, vp, u64, u64, u64, C.POINTER(u64)]
+    L.pnuc_server_submit_nucleons.argtypes = [vp, vp, vp, vp, u64, u64, u64, C.POINTER(u64)]
     L.pnuc_server_wait.argtypes = [vp, u64, C.c_int32, C.POINTER(u64)]
     L.pnuc_server_wait_any.argtypes = [vp, C.c_int32, C.POINTER(u64)]
     L.pnuc_server_fetch.argtypes = [vp, u64, vp, u64, vp]
@@ -155,7 +156,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                  "pnuc_set_tuning",
                  "pnuc_measure_peaks", "pnuc_autotune", "pnuc_save_tuning", "pnuc_load_tuning",
                  "pnuc_graph_create", "pnuc_graph_update", "pnuc_graph_launch", "pnuc_graph_destroy",
-                 "pnuc_server_create", "pnuc_server_submit", "pnuc_server_wait", "pnuc_server_wait_any",
+                 "pnuc_server_create", "pnuc_server_submit", "pnuc_server_submit_nucleons", "pnuc_server_wait",
+                 "pnuc_server_wait_any",
                  "pnuc_server_fetch",
                  "pnuc_server_get_stats", "pnuc_server_reset_stats", "pnuc_server_destroy"):
         getattr(L, name).restype = C.c_int
@@ -444,13 +446,22 @@ class Server:
         ctx._check(self.lib.pnuc_server_create(ctx.handle, C.byref(c), C.byref(self.handle)))
         self.n_events: dict[int, int] = {}
 
-    def submit(self, energies, target_ids, seed: int, first_event_id: int = 0) -> int:
-        """Queues a request; returns its ticket. Raises PnucError (status 3) when the queue is full."""
+    def submit(self, energies, target_ids, seed: int, first_event_id: int = 0, projectiles=None) -> int:
+        """Queues a request (optional projectiles: uint8 per event, 1 proton, 0 neutron); returns
+        its ticket. Raises PnucError (status 3) when the queue is full."""
         e = np.ascontiguousarray(energies, np.float64)
         t = np.ascontiguousarray(target_ids, np.int32)
         tk = C.c_uint64()
-        self.ctx._check(self.lib.pnuc_server_submit(self.handle, e.ctypes.data, t.ctypes.data, len(e), seed,
-                                                    first_event_id, C.byref(tk)))
+        if projectiles is None:
+            self.ctx._check(self.lib.pnuc_server_submit(self.handle, e.ctypes.data, t.ctypes.data, len(e), seed,
+                                                        first_event_id, C.byref(tk)))
+        else:
+            pj = np.ascontiguousarray(projectiles, np.uint8)
+            if pj.shape[0] != len(e):
+                raise ValueError("projectiles must have one entry per event")
+            self.ctx._check(self.lib.pnuc_server_submit_nucleons(self.handle, e.ctypes.data, t.ctypes.data,
+                                                                 pj.ctypes.data, len(e), seed, first_event_id,
+                                                                 C.byref(tk)))
         self.n_events[tk.value] = len(e)
         return tk.value
 

@@ -223,3 +223,30 @@ def test_wait_any_returns_each_finished_request_once(ctx):
         assert srv.wait_any(50) is None  # nothing left: the wait times out
     finally:
         srv.close()
+
+
+def test_neutron_requests_merge_with_proton_requests(ctx):
+    """Requests with incident neutrons (a transport code's secondary neutrons) merge with
+    proton requests; each result equals its events run alone with the same species."""
+    import torch
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(12, rate_hz=1e6, seed=18, min_batch=300, max_batch=3000)
+    rng = np.random.default_rng(19)
+    species = [None if k % 3 == 0 else rng.integers(0, 2, len(r["energies"])).astype(np.uint8)
+               for k, r in enumerate(reqs)]
+    srv = pnuc.Server(ctx, precision="fp32", streams=1, arena_bytes=128 << 20)
+    try:
+        tickets = [srv.submit(r["energies"], tids[r["tidx"]], 12, r["first_event_id"], projectiles=pj)
+                   for r, pj in zip(reqs, species)]
+        for tk, r, pj in zip(tickets, reqs, species):
+            sec, res = srv.fetch(tk, srv.wait(tk))
+            proj = None if pj is None else torch.tensor(pj, device="cuda")
+            ref = ctx.simulate(torch.tensor(r["energies"], device="cuda"),
+                               torch.tensor(tids[r["tidx"]], device="cuda"), seed=12,
+                               first_event_id=r["first_event_id"], capacity=40 * len(r["energies"]), projectiles=proj)
+            torch.cuda.synchronize()
+            assert np.array_equal(res, ref.residuals_np())
+            assert np.array_equal(pnuc.sort_secondaries(sec), pnuc.sort_secondaries(ref.secondaries_np()))
+        assert srv.stats()["launches"] < len(reqs)
+    finally:
+        srv.close()
