@@ -311,7 +311,10 @@ typedef struct {
                                     most the resident limit), so that small launches leave SMs to
                                     the others and do not each wait on their slowest event with
                                     the whole GPU, 1..1024 (default 4) */
-    uint32_t reserved;
+    uint32_t max_inflight_events; /* no new launch while launches of at least this many events
+                                    are in flight (0: no limit; default 0): under heavy load
+                                    requests then wait and merge instead of splitting the GPU
+                                    among more launches */
 } pnuc_server_config;
 
 typedef struct {

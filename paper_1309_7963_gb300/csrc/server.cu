@@ -241,6 +241,14 @@ bool admit(pnuc_server *S)
             break;
         }
     if (si < 0) return false;
+    if (S->cfg.max_inflight_events) {  // the work in flight bounds new launches
+        uint64_t inflight = 0;
+        for (uint64_t gid : S->stream_owner) {
+            auto it = gid ? S->groups.find(gid) : S->groups.end();
+            if (it != S->groups.end()) inflight += it->second->n;
+        }
+        if (inflight >= S->cfg.max_inflight_events) return false;
+    }
     // the candidates: the first pending request, then followers with the same seed
     std::vector<Request *> cand;
     uint64_t n = 0, cap = 0;

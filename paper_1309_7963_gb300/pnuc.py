@@ -79,7 +79,7 @@ class pnuc_server_config(C.Structure):
     _fields_ = [("precision", C.c_int32), ("streams", C.c_int32), ("arena_bytes", C.c_uint64),
                 ("sec_per_event", C.c_uint32), ("max_pending", C.c_uint32), ("max_request_events", C.c_uint64),
                 ("max_merge", C.c_uint32), ("merge_events", C.c_uint32),
-                ("lane_events", C.c_uint32), ("reserved", C.c_uint32)]
+                ("lane_events", C.c_uint32), ("max_inflight_events", C.c_uint32)]
 
 
 class pnuc_server_stats(C.Structure):

@@ -250,3 +250,18 @@ def test_neutron_requests_merge_with_proton_requests(ctx):
         assert srv.stats()["launches"] < len(reqs)
     finally:
         srv.close()
+
+
+def test_inflight_cap_still_serves_every_request(ctx):
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(16, rate_hz=1e6, seed=20, min_batch=1000, max_batch=20_000)
+    srv = pnuc.Server(ctx, precision="fp32", streams=8, arena_bytes=256 << 20, max_inflight_events=15_000)
+    try:
+        tickets = [srv.submit(r["energies"], tids[r["tidx"]], 13, r["first_event_id"]) for r in reqs]
+        for tk, r in zip(tickets, reqs):
+            sec, res = srv.fetch(tk, srv.wait(tk))
+            ref_sec, ref_res = alone(ctx, r, tids, 13)
+            assert np.array_equal(res, ref_res) and np.array_equal(pnuc.sort_secondaries(sec), ref_sec)
+        assert srv.stats()["completed"] == len(reqs)
+    finally:
+        srv.close()
