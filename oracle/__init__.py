@@ -82,8 +82,9 @@ def lib() -> C.CDLL:
             L = C.CDLL(_SO)
             d, i32, i64, u64, vp = C.c_double, C.c_int32, C.c_int64, C.c_uint64, C.c_void_p
             L.orc_philox4x64_10.argtypes = [vp, vp, vp]
-            L.orc_uniform.argtypes = [u64]
+            L.orc_uniform.argtypes = [C.c_uint32]
             L.orc_uniform.restype = d
+            L.orc_stream_draws.argtypes = [u64, u64, C.c_int64, vp]
             L.orc_semf_mass.argtypes = [i32, i32]
             L.orc_semf_mass.restype = d
             L.orc_target_setup.argtypes = [i32, i32, vp]
@@ -137,8 +138,16 @@ def philox4x64_10(counter, key) -> np.ndarray:
     return out
 
 
-def uniform(word: int) -> float:
-    return lib().orc_uniform(int(word))
+def uniform(half: int) -> float:
+    """The uniform of one 32-bit half of a Philox word."""
+    return lib().orc_uniform(int(half))
+
+
+def stream_draws(seed: int, event: int, n: int) -> np.ndarray:
+    """The first n uniforms of an event's draw stream."""
+    out = np.zeros(n, np.float64)
+    lib().orc_stream_draws(seed, event, n, _p(out))
+    return out
 
 
 def semf_mass(Z: int, A: int) -> float:

@@ -115,11 +115,12 @@ void orc_philox4x64_10(const uint64_t ctr_in[4], const uint64_t key_in[2], uint6
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* 64-bit word -> uniform in (0,1): the top 52 bits plus one half, exact in FP64 */
-double orc_uniform(uint64_t w) { return ((double)(w >> 12) + 0.5) * 0x1p-52; }
+/* 32-bit half-word -> uniform in (0,1): h plus one half, over 2^32; exact in FP64 */
+double orc_uniform(uint32_t h) { return ((double)h + 0.5) * 0x1p-32; }
 
-/* The event's draw stream: draw d is word d%4 of Philox((d/4, event, 0, 0), (seed, 0)).
- * A test may inject the first n_inject uniforms. */
+/* The event's draw stream (reading M7): a Philox block (d/8, event, 0, 0), key (seed, 0),
+ * gives 4 words = 8 draws; draw d is half d%2 (0: the high 32 bits, 1: the low) of word
+ * (d/2)%4 of block d/8. A test may inject the first n_inject uniforms. */
 typedef struct {
     uint64_t seed, event, next, block;
     uint64_t buf[4];
@@ -145,14 +146,23 @@ static double U(orc_stream *st)
     uint64_t d = st->next++;
     if (st->cnt) st->cnt->draws++;
     if ((int64_t)d < st->n_inject) return st->inject[d];
-    uint64_t blk = d >> 2;
+    uint64_t blk = d >> 3;
     if (!st->have || st->block != blk) {
         uint64_t ctr[4] = {blk, st->event, 0, 0}, key[2] = {st->seed, 0};
         orc_philox4x64_10(ctr, key, st->buf);
         st->block = blk;
         st->have = 1;
     }
-    return orc_uniform(st->buf[d & 3]);
+    const uint64_t w = st->buf[(d >> 1) & 3];
+    return orc_uniform((d & 1) ? (uint32_t)w : (uint32_t)(w >> 32));
+}
+
+/* The first n draws of an event's stream, as the simulation consumes them. */
+void orc_stream_draws(uint64_t seed, uint64_t event, int64_t n, double *out)
+{
+    orc_stream st;
+    stream_init(&st, seed, event, NULL, 0, NULL);
+    for (int64_t i = 0; i < n; i++) out[i] = U(&st);
 }
 
 /* ------------------------------------------------------------------ small vector helpers */

@@ -64,24 +64,28 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t
     o3 = c3;
 }
 
-template <typename R> __device__ __forceinline__ R to_uniform(uint64_t w);
-template <> __device__ __forceinline__ double to_uniform<double>(uint64_t w)
+// One 32-bit half h of a Philox word -> uniform in (0, 1).
+template <typename R> __device__ __forceinline__ R to_uniform(uint32_t h);
+template <> __device__ __forceinline__ double to_uniform<double>(uint32_t h)
 {
-    return ((double)(w >> 12) + 0.5) * 0x1p-52;  // 52 bits + 1/2: exact, open interval
+    return ((double)h + 0.5) * 0x1p-32;  // 32 bits + 1/2: exact, open interval
 }
-template <> __device__ __forceinline__ float to_uniform<float>(uint64_t w)
+template <> __device__ __forceinline__ float to_uniform<float>(uint32_t h)
 {
-    // (m + 1/2) 2^-23 for the top 23 bits m, built as (1 + m 2^-23) - (1 - 2^-24): both
-    // operands and the difference are exact floats, and no int->float conversion is needed
-    return __uint_as_float(0x3f800000u | (uint32_t)(w >> 41)) - 0x1.fffffep-1f;
+    // (m + 1/2) 2^-23 for the top 23 bits m of h (the FP64 uniform on the float grid), built
+    // as (1 + m 2^-23) - (1 - 2^-24): both operands and the difference are exact floats, and
+    // no int->float conversion is needed
+    return __uint_as_float(0x3f800000u | (h >> 9)) - 0x1.fffffep-1f;
 }
 
-// The event's draw stream: draw d is word d mod 4 of Philox((d div 4, event, 0, 0),
-// (seed, 0)). Converted words wait in a 32-slot ring in shared memory (slot k of thread t
-// at buf[k * stride], stride = block size: conflict-free). Words are generated only by
+// The event's draw stream: Philox((d div 8, event, 0, 0), (seed, 0)) gives 4 words = 8
+// draws; draw d is half d mod 2 (the high 32 bits first) of word (d div 2) mod 4.
+// Converted draws wait in a 32-slot ring in shared memory (slot k of thread t at
+// buf[k * stride], stride = block size: conflict-free). Draws are generated only by
 // ensure(k), which the kernels call once per loop iteration (and the evaporation sampler
 // once per trial), so lanes generate together and the Philox code exists twice.
 constexpr int kRing = 32;
+constexpr int kDrawsPerBlock = 8;
 
 template <typename R>
 struct Stream {
@@ -98,33 +102,37 @@ struct Stream {
         left = 0;
         head = 0;
     }
-    // at least k (<= kRing - 3) words available afterwards
+    // at least k (<= kRing - kDrawsPerBlock + 1) draws available afterwards
     __device__ __forceinline__ void ensure(int k)
     {
 #pragma unroll 1
         while (left < k) {
-            uint64_t w0, w1, w2, w3;
-            philox4x64_10(block, event, seed, 0, w0, w1, w2, w3);
+            uint64_t w[4];
+            philox4x64_10(block, event, seed, 0, w[0], w[1], w[2], w[3]);
             ++block;
             const int t = head + left;
-            buf[((t + 0) & (kRing - 1)) * stride] = to_uniform<R>(w0);
-            buf[((t + 1) & (kRing - 1)) * stride] = to_uniform<R>(w1);
-            buf[((t + 2) & (kRing - 1)) * stride] = to_uniform<R>(w2);
-            buf[((t + 3) & (kRing - 1)) * stride] = to_uniform<R>(w3);
-            left += 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                buf[((t + 2 * q) & (kRing - 1)) * stride] = to_uniform<R>((uint32_t)(w[q] >> 32));
+                buf[((t + 2 * q + 1) & (kRing - 1)) * stride] = to_uniform<R>((uint32_t)w[q]);
+            }
+            left += kDrawsPerBlock;
         }
     }
     // positions the stream at draw d (the next draw returned is draw d)
     __device__ void seek(uint64_t d)
     {
-        block = (uint32_t)(d >> 2);
+        block = (uint32_t)(d / kDrawsPerBlock);
         left = 0;
         head = 0;
-        ensure(4);
-        head = (int)(d & 3);
-        left -= (int)(d & 3);
+        ensure(kDrawsPerBlock);
+        head = (int)(d % kDrawsPerBlock);
+        left -= (int)(d % kDrawsPerBlock);
     }
-    __device__ __forceinline__ uint32_t position() const { return 4u * block - (uint32_t)left; }
+    __device__ __forceinline__ uint32_t position() const
+    {
+        return (uint32_t)kDrawsPerBlock * block - (uint32_t)left;
+    }
     __device__ __forceinline__ R next()
     {
         R u = buf[head * stride];

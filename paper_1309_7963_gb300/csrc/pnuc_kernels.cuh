@@ -71,7 +71,7 @@ template <typename R, bool kCount>
 __device__ __forceinline__ void finish_event(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
 {
     write_residual(P, L);
-    C.add(PNUC_C_DRAWS, 4u * L.rng.block - (unsigned)L.rng.left);  // generated minus unused
+    C.add(PNUC_C_DRAWS, L.rng.position());  // generated minus unused
     // events whose E* was settled here (a pending one is settled by the evaporation kernel)
     if (!L.pend && !(L.flags & (PNUC_FLAG_BAD_INPUT | PNUC_FLAG_ATTEMPT_CAP))) C.add(PNUC_C_SETTLED);
 }
@@ -209,7 +209,7 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
             // only lanes holding an event touch their stream
             if (L.phase == kKinWait || L.phase == kTransport || L.phase == kEntry) {
                 int k = draws ? 8 : 0;
-                if (L.rng.left < kRing - 3 && L.rng.left + 1 > k) k = L.rng.left + 1;
+                if (L.rng.left < kRing - kDrawsPerBlock + 1 && L.rng.left + 1 > k) k = L.rng.left + 1;
                 L.rng.ensure(k);
             }
         }

@@ -64,9 +64,10 @@ def test_fp64_per_event_parity_mixed_targets_and_energies(ctx):
     assert c["max_rel_energy_same"] < 1e-6
 
 
-@pytest.mark.parametrize("za", [inputs.TI48, inputs.FE56, inputs.PB208])
-def test_fp64_per_event_parity_heavy(ctx, za):
-    w = inputs.heavy(za, 1500, seed=7)
+@pytest.mark.parametrize("za,n", [(inputs.TI48, 6000), (inputs.FE56, 6000), (inputs.PB208, 3000)])
+def test_fp64_per_event_parity_heavy(ctx, za, n):
+    # samples of thousands of events: the bar is 99.9%, and one event in 1500 is already 0.07%
+    w = inputs.heavy(za, n, seed=7)
     r = run_gpu(ctx, w, "fp64", "persistent")
     c = compare(r.residuals_np(), r.secondaries_np(), run_oracle(w), w.n)
     assert c["frac_match"] >= 0.999, c["frac_match"]

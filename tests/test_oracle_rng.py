@@ -1,5 +1,6 @@
-"""Pins of the oracle's Philox4x64-10 and uniform conversion (model: Philox keyed by
-(seed, event id, draw block), replacing the paper's CURAND states, §3.1)."""
+"""Pins of the oracle's Philox4x64-10, uniform conversion and draw order (model: Philox keyed
+by (seed, event id, draw block), each uniform one 32-bit half of a word, replacing the
+paper's CURAND states, §3.1)."""
 import numpy as np
 import pytest
 
@@ -25,10 +26,29 @@ def test_philox_matches_numpy(key, counter):
 
 
 def test_uniform_conversion_exact_open_interval():
-    assert oracle.uniform(0) == 0.5 * 2.0**-52
-    assert oracle.uniform(2**64 - 1) == 1.0 - 0.5 * 2.0**-52
-    w = 0x0123456789ABCDEF
-    assert oracle.uniform(w) == ((w >> 12) + 0.5) / 2.0**52
+    assert oracle.uniform(0) == 0.5 * 2.0**-32
+    assert oracle.uniform(2**32 - 1) == 1.0 - 0.5 * 2.0**-32
+    h = 0x89ABCDEF
+    assert oracle.uniform(h) == (h + 0.5) / 2.0**32
+
+
+@pytest.mark.parametrize("seed,event", [(0, 0), (5, 11), (2**64 - 1, 2**40 + 3)])
+def test_draw_stream_is_the_half_words_of_numpy_philox(seed, event):
+    """Draw d of an event is half d % 2 (high first) of word (d / 2) % 4 of the Philox block
+    with counter (d / 8, event, 0, 0) and key (seed, 0): numpy's Philox, whose counter is
+    incremented before each block, started one below (d / 8, event, 0, 0)."""
+    n = 40  # five blocks
+    draws = oracle.stream_draws(seed, event, n)
+    # the counter (0, event, 0, 0) minus one, borrowing across the four 64-bit words
+    start, borrow = [0, event, 0, 0], 1
+    for k in range(4):
+        start[k] -= borrow
+        borrow = 1 if start[k] < 0 else 0
+        start[k] %= 2**64
+    g = np.random.Philox(key=np.array([seed, 0], np.uint64), counter=np.array(start, np.uint64))
+    words = [int(x) for x in g.random_raw(n // 2)]
+    halves = [h for w in words for h in (w >> 32, w & 0xFFFFFFFF)]
+    assert [float(d) for d in draws] == [(h + 0.5) / 2.0**32 for h in halves]
 
 
 def test_event_streams_are_uniform_and_independent():
