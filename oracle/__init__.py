@@ -103,7 +103,7 @@ def lib() -> C.CDLL:
             L.orc_collide.argtypes = [C.c_int, vp, C.c_int, vp, d, d, d, vp, vp]
             L.orc_boundary_distance.argtypes = [vp, C.c_int, vp, vp, vp]
             L.orc_boundary_distance.restype = d
-            L.orc_refract.argtypes = [vp, vp, d, d]
+            L.orc_refract.argtypes = [vp, vp, d, d, i32]
             L.orc_refract.restype = C.c_int
             L.orc_width_integral.argtypes = [d, d, d]
             L.orc_width_integral.restype = d
@@ -206,10 +206,14 @@ def boundary_distance(tgt: np.ndarray, shell: int, r, d):
     return s, int(direction[0])
 
 
-def refract(n, p, m: float, dT: float):
+def refract(n, p, m: float, dT: float, direction: int | None = None):
+    """A boundary crossing (M11) with outward normal n; direction +1 (outward) or -1 (inward),
+    by default the way p points along n."""
     n = np.ascontiguousarray(n, np.float64)
     p = np.array(p, np.float64)
-    ok = lib().orc_refract(_p(n), _p(p), m, dT)
+    if direction is None:
+        direction = 1 if float(np.dot(n, p)) >= 0.0 else -1
+    ok = lib().orc_refract(_p(n), _p(p), m, dT, int(direction))
     return bool(ok), p
 
 

@@ -411,17 +411,24 @@ double orc_boundary_distance(const orc_target *t, int shell, const double r[3], 
 /* Potential step at a shell boundary (section 2.3, after Chen et al.): kinetic energy
  * changes by dT with the tangential momentum kept. Returns 1 if the particle refracts
  * (p updated), 0 if it reflects (normal component reversed). n is the unit normal. */
-int orc_refract(const double n[3], double p[3], double m, double dT)
+/* Reading M11: after a crossing the momentum's component along n points the way the
+ * particle now goes, back (reflection) or on (refraction), with at least GRAZE_FLOOR of |p|
+ * (1 mrad from the tangent plane); a near-tangent reflection otherwise bounces along chords
+ * of ~2R theta, one step each. dir: +1 for a crossing outward (along n), -1 inward. */
+#define GRAZE_FLOOR 1e-3
+int orc_refract(const double n[3], double p[3], double m, double dT, int dir)
 {
     double pp = dot3(p, p);
     double T = kinetic(pp, m), Tn = T + dT;
     double pn = dot3(p, n);
     double q2 = pn * pn + (Tn - T) * (Tn + T + 2.0 * m);
     if (Tn <= 0.0 || q2 <= 0.0) {
-        for (int k = 0; k < 3; k++) p[k] -= 2.0 * pn * n[k];
+        double to = pn * pn < GRAZE_FLOOR * GRAZE_FLOOR * pp ? -dir * (GRAZE_FLOOR * sqrt(pp)) : -pn;
+        for (int k = 0; k < 3; k++) p[k] += (to - pn) * n[k];
         return 0;
     }
-    double pnn = (pn >= 0.0 ? 1.0 : -1.0) * sqrt(q2);
+    double p2n = pp - pn * pn + q2; /* |p|^2 after the crossing */
+    double pnn = q2 < GRAZE_FLOOR * GRAZE_FLOOR * p2n ? dir * (GRAZE_FLOOR * sqrt(p2n)) : dir * sqrt(q2);
     for (int k = 0; k < 3; k++) p[k] += (pnn - pn) * n[k];
     return 1;
 }
@@ -649,7 +656,7 @@ static void run_event(const orc_target *t, int proj, double T0, uint32_t ev, orc
         {
             double rr = sqrt(dot3(cur.r, cur.r));
             double n[3] = {cur.r[0] / rr, cur.r[1] / rr, cur.r[2] / rr};
-            orc_refract(n, cur.p, mproj, t->V[proj][NSHELL - 1]);
+            orc_refract(n, cur.p, mproj, t->V[proj][NSHELL - 1], -1);
         }
         trace_put(o, ev, TR_ENTRY, proj, cur.shell, kinetic(dot3(cur.p, cur.p), mproj), cur.r);
         int sp = 0;      /* stack depth */
@@ -748,7 +755,7 @@ static void run_event(const orc_target *t, int proj, double T0, uint32_t ev, orc
             double rr = sqrt(dot3(cur.r, cur.r));
             double n[3] = {cur.r[0] / rr, cur.r[1] / rr, cur.r[2] / rr};
             double Tb = kinetic(pp, m1);
-            if (!orc_refract(n, cur.p, m1, dT)) {
+            if (!orc_refract(n, cur.p, m1, dT, dir)) {
                 c->reflections++;
                 trace_put(o, ev, TR_REFLECT, s1, i, Tb, cur.r);
                 continue;

@@ -243,21 +243,33 @@ __device__ R boundary_distance(const ShellTable<R> &t, int shell, const R *r, co
     return s > R(0) ? s : R(0);
 }
 
+// After a crossing the momentum's component along n points the way the particle now goes,
+// back (reflection) or on (refraction), with at least kGrazeFloor of |p| (1 mrad from the
+// tangent plane): a near-tangent reflection otherwise bounces along chords of about 2 R theta,
+// one step each, and in FP32 a tangent one can round to zero-length chords that repeat until
+// the step cap. The tests use the exact scalars already at hand; the root only when the floor
+// applies.
+constexpr double kGrazeFloor = 1e-3;
+
 // Potential step (after Chen et al.): kinetic energy changes by dT at fixed tangential
-// momentum; reflection when that is impossible. Returns true if refracted.
+// momentum; reflection when that is impossible. dir: +1 for a crossing outward (along n),
+// -1 inward. Returns true if refracted.
 template <typename R>
-__device__ bool refract(const R *n, R *p, R m, R dT)
+__device__ bool refract(const R *n, R *p, R m, R dT, int dir)
 {
+    const R floor2 = R(kGrazeFloor * kGrazeFloor);
     R pp = dot3(p, p);
     R T = kinetic(pp, m), Tn = T + dT;
     R pn = dot3(p, n);
     R q2 = pn * pn + (Tn - T) * (Tn + T + R(2) * m);
     if (Tn <= R(0) || q2 <= R(0)) {
+        const R to = pn * pn < floor2 * pp ? R(-dir) * (R(kGrazeFloor) * sqrt(pp)) : -pn;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) p[k] -= R(2) * pn * n[k];
+        for (int k = 0; k < 3; ++k) p[k] += (to - pn) * n[k];
         return false;
     }
-    R pnn = (pn >= R(0) ? R(1) : R(-1)) * sqrt(q2);
+    const R p2n = pp - pn * pn + q2;  // |p|^2 after the crossing
+    const R pnn = q2 < floor2 * p2n ? R(dir) * (R(kGrazeFloor) * sqrt(p2n)) : R(dir) * sqrt(q2);
 #pragma unroll
     for (int k = 0; k < 3; ++k) p[k] += (pnn - pn) * n[k];
     return true;
@@ -529,7 +541,7 @@ __device__ void step_entry(const SimParams &P, const ShellTable<R> &t, double Ra
     L.p[2] = sqrt(T0 * T0 + R(2) * T0 * mproj);
     R rr = sqrt(dot3(L.r, L.r));
     R n[3] = {L.r[0] / rr, L.r[1] / rr, L.r[2] / rr};
-    refract(n, L.p, mproj, t.V[L.proj][kShells - 1]);
+    refract(n, L.p, mproj, t.V[L.proj][kShells - 1], -1);
     L.s = L.proj;
     L.shell = kShells - 1;
     L.sp = 0;
@@ -717,7 +729,7 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
     R rr = sqrt(dot3(L.r, L.r));
     R n[3] = {L.r[0] / rr, L.r[1] / rr, L.r[2] / rr};
     R Tb = kinetic(pp, m1);
-    if (!refract(n, L.p, m1, dT)) {
+    if (!refract(n, L.p, m1, dT, dir)) {
         C.add(PNUC_C_REFLECTIONS);
         return;
     }
