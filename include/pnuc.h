@@ -7,8 +7,8 @@
  * (paper §2.3) on a 15-shell Fermi-gas nucleus (§2.2, Eq. 1), then evaporation of
  * n, p, d, t, 3He and alpha down to the residual nucleus (§2.4). Every event depends only
  * on (seed, event id): its random numbers are the stream of Philox4x64-10 with key
- * (seed, 0) and counters (j, event id, 0, 0), j = 0, 1, ... (the paper used CURAND
- * states, §3.1).
+ * (seed, 0) and counters (j, event id, 0, 0), j = 0, 1, ..., each 64-bit word giving two
+ * 32-bit draws, the high half first (the paper used CURAND states, §3.1).
  *
  * Conventions for every entry point:
  *  - Pointers documented "device" must point to memory of the context's device (for
