@@ -490,7 +490,7 @@ pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_met
     }
     if (!ctx->h_count) CU(ctx, cudaMalloc(&ctx->h_count, sizeof(unsigned long long)));
     if (!ctx->h_count_host) CU(ctx, cudaMallocHost(&ctx->h_count_host, sizeof(unsigned long long)));
-    pnuc_batch b = {ctx->h_energies, ctx->h_tids, n, seed, first_event_id};
+    pnuc_batch b = {ctx->h_energies, ctx->h_tids, n, seed, first_event_id, nullptr, nullptr};
     pnuc_output o = {sec_capacity ? (dsec ? dsec : ctx->h_sec) : nullptr, sec_capacity, ctx->h_count,
                      dres ? dres : ctx->h_res, nullptr};
     pnuc_status st = check_batch(ctx, precision, method, &b, &o);
@@ -586,7 +586,7 @@ pnuc_status pnuc_simulate_host_noalloc(pnuc_ctx *ctx, pnuc_precision precision, 
         CU(ctx, cudaMemcpyAsync(d_e, energies, sizeof(double) * n, cudaMemcpyHostToDevice, s));
         CU(ctx, cudaMemcpyAsync(d_t, target_ids, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     }
-    pnuc_batch b = {d_e, d_t, n, seed, first_event_id};
+    pnuc_batch b = {d_e, d_t, n, seed, first_event_id, nullptr, nullptr};
     pnuc_output o = {sec_capacity ? d_s : nullptr, sec_capacity, count, d_r, nullptr};
     pnuc_status st = check_batch(ctx, precision, method, &b, &o);
     if (st != PNUC_OK) return st;

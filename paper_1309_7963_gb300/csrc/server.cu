@@ -341,7 +341,7 @@ bool admit(pnuc_server *S)
         st = PNUC_ERR_CUDA;
     unsigned char *hd = S->host_dev + hoff;  // the host region, as the kernels address it
     pnuc_batch b = {(const double *)(d + L.e), (const int32_t *)(d + L.t), n, cand[0]->seed, cand[0]->first,
-                    any_proj ? (const uint8_t *)(d + L.pj) : nullptr};
+                    any_proj ? (const uint8_t *)(d + L.pj) : nullptr, nullptr};
     pnuc_secondary *launch_sec = k > 1 ? (pnuc_secondary *)(d + L.s) : (pnuc_secondary *)(hd + L.host_s);
     pnuc_output o = {cap ? launch_sec : nullptr, cap, (unsigned long long *)(d + GroupLayout::count),
                      (pnuc_residual *)(hd + L.host_r), nullptr};
