@@ -204,3 +204,21 @@ def test_full_size_sampled_parity(ctx, precision, need):
         assert c["frac_same"] >= need, c["frac_same"]
     else:
         assert c["frac_match"] >= need, c["frac_match"]
+
+
+def test_grazing_reflection_does_not_loop_to_the_step_cap(ctx):
+    """A p-208Pb event (id 523678 of the 1e6-event heavy batch, seed 3, 140.04 MeV) whose FP32
+    history had reached a grazing reflection that rounding turned into zero-length chords,
+    repeated until the 1e5-step cap; with the 1-mrad floor on the normal momentum after a
+    crossing (reading M11) it ends normally in both modes."""
+    import torch
+    w = inputs.heavy(inputs.PB208, 1_000_000, seed=3)
+    i = 523678
+    tid = ctx.create_target(*inputs.PB208)
+    e = torch.tensor(w.energies[i:i + 1], device="cuda")
+    t = torch.full((1,), tid, dtype=torch.int32, device="cuda")
+    for precision in ("fp32", "fp64"):
+        r = ctx.simulate(e, t, seed=w.seed, first_event_id=i, precision=precision, counters=True, capacity=256)
+        torch.cuda.synchronize()
+        assert (r.residuals_np()["flags"] & 4).sum() == 0, precision
+        assert r.counters_dict()["steps"] < 5000, precision

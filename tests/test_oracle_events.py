@@ -157,3 +157,17 @@ def test_neutron_entry_and_residual_charge_from_trace():
     # the same events as protons differ: the projectile species enters the stream of decisions
     rp = _run(za, 60.0, n, projectiles=np.ones(n, np.int32))
     assert not np.array_equal(rp["residuals"]["Zc"], res["Zc"])
+
+
+def test_heavy_target_events_never_reach_the_step_cap():
+    """Reading M11's floor on the normal momentum after a crossing: no event of a p-208Pb
+    sample (the heavy target with the most surface reflections) runs to the 1e5-step cap,
+    and the longest stays within a few thousand steps."""
+    w = inputs.heavy(inputs.PB208, 3000, seed=3)
+    r = oracle.simulate(w.targets, w.energies, w.tidx, seed=w.seed)
+    assert (r["residuals"]["flags"] & 4).sum() == 0
+    worst = 0
+    for i in range(0, 3000, 10):  # per-event step counts on every tenth event
+        c = oracle.simulate(w.targets, w.energies[i:i + 1], w.tidx[i:i + 1], seed=w.seed, first_event_id=i)
+        worst = max(worst, int(c["counters"]["steps"]))
+    assert worst < 5000
