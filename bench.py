@@ -173,7 +173,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def serving_bench(ctx, seconds: float = 1.5) -> dict:
+def serving_bench(ctx, seconds: float = 3.0) -> dict:
     """The serving loop under the synthetic transport driver: capacity from a saturating
     burst, then Poisson arrivals at 50%, 75% and 90% of it; p50/p99 from submit to results."""
     import time as _t
