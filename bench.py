@@ -39,9 +39,8 @@ WORKLOAD = "1e6 p-16O + 1e6 p-40Ca at 200 MeV, one batch of 2e6 events per step"
 
 # Algorithmic FP64 operations of the FP32-mode model per counted unit, from the operations
 # the model performs in FP64 there (Lorentz boosts, energy/momentum bookkeeping, evaporation
-# widths): add, multiply, FMA and compare count 1; a division, square root or reciprocal
-# square root 8 and an exponential 16 (Newton-Raphson and Cody-Waite/Horner instruction
-# counts). Conversions between float and double are not arithmetic (the kernels do them on
+# Q-values): add, multiply, FMA and compare count 1; a division, square root or reciprocal
+# square root 8 (Newton-Raphson instruction counts). Conversions between float and double are not arithmetic (the kernels do them on
 # the integer pipes). The units are the kernels' own counters.
 CASCADE_FP64_OPS = {
     # pair sums and energies 6, s 4, 1/sqrt(s) 8, 1/E_t 8, beta and gamma 4, gamma^2/(gamma+1)
@@ -53,10 +52,10 @@ CASCADE_FP64_OPS = {
 EVAP_FP64_OPS = {
     "settled": 18,      # E* from the energy balance (p0 with its square root, the sums)
     "evap_passes": 18,  # six Q-values and excitations X = E* - Q
-    "evap_exps": 22,    # one open channel with x >= 1: exponential 16, F and G 3, width 3
-    "evap_series": 3,   # one open channel with x < 1: the width from F and G
-    # the channel draw 20, the emission energy and E_d 13, the decay boost 46, bookkeeping 6
-    "evap_steps": 85,
+    # the widths, the channel draw, U_d and the decay with its boost are FP32 arithmetic
+    # (widths scaled by the largest exponential); the parent's mass + E*, the release, the
+    # daughter's mass, and the parent's energy and momentum bookkeeping 9
+    "evap_steps": 9,
 }
 KERNEL_FILES = ("pnuc_device.cuh", "pnuc_kernels.cuh", "kernel_fp32.cu", "pnuc_internal.h")
 

@@ -5,9 +5,9 @@
 // kernel (warps refilling finished lanes) run the same steps.
 //
 // Precision: R = double reproduces the CPU oracle event by event (compiled without FMA
-// contraction); R = float keeps transport, paths and cross sections in FP32 while the
-// Lorentz boosts, the event's energy/momentum bookkeeping and the evaporation widths stay
-// FP64.
+// contraction); R = float keeps transport, paths, cross sections and the (scaled)
+// evaporation widths in FP32 while the Lorentz boosts, the Q-values and the event's
+// energy/momentum bookkeeping stay FP64.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -966,48 +966,92 @@ __device__ void channel_params(const SimParams &P, int Z, int A, double Mparent,
     c.open = true;
 }
 
-// F(x) = e^x (x^2 - 3x + 3) + x^2/2 - 3 and G(x) = e^x (x - 1) + 1 with the exponential in
-// FP64 (it reaches e^160); the polynomials in precision R; series below x = 1.
-template <typename R>
-__device__ void width_FG_R(R x, double &F, double &G)
+// F(x) = e^x (x^2 - 3x + 3) + x^2/2 - 3 and G(x) = e^x (x - 1) + 1 (the closed-form width
+// integrals), FP64 mode: the exponential reaches e^160; series below x = 1.
+__device__ __forceinline__ void width_FG(double x, double &F, double &G)
 {
-    if (x >= R(1)) {
-        double ex = exp(to_d<R>(x));
-        F = ex * to_d<R>(x * x - R(3) * x + R(3)) + to_d<R>(R(0.5) * x * x) - 3.0;
-        G = ex * to_d<R>(x - R(1)) + 1.0;
+    if (x >= 1.0) {
+        const double ex = exp(x);
+        F = ex * (x * x - 3.0 * x + 3.0) + 0.5 * x * x - 3.0;
+        G = ex * (x - 1.0) + 1.0;
         return;
     }
-    R term = x, f = R(0), g = R(0);  // term = x^n / n!
+    double term = x, f = 0.0, g = 0.0;  // term = x^n / n!
 #pragma unroll 1
     for (int n = 2; n <= 20; ++n) {
-        term *= x / R(n);
-        g += R(n - 1) * term;
-        if (n >= 4) f += R((n - 1) * (n - 3)) * term;
+        term *= x / n;
+        g += (n - 1) * term;
+        if (n >= 4) f += ((n - 1) * (n - 3)) * term;
     }
-    F = to_d<R>(f);
-    G = to_d<R>(g);
+    F = f;
+    G = g;
 }
 
+// The type the six widths of a step are held and drawn in: FP64 in the FP64 mode (the
+// oracle's arithmetic), FP32 in the FP32 mode, where they are scaled (below).
 template <typename R>
-__device__ double channel_width(const ChanP<R> &c);
+struct WidthOf {
+    using T = double;
+};
 template <>
-__device__ double channel_width<double>(const ChanP<double> &c)
+struct WidthOf<float> {
+    using T = float;
+};
+template <typename R>
+using width_t = typename WidthOf<R>::T;
+
+// The width of one open channel. The channel draw uses only the six widths' ratios, so the
+// FP32 mode returns the width times e^-xm, xm the largest x of the parent's open channels:
+// the exponential becomes e^(x - xm) <= 1 and the whole width is FP32 arithmetic (the
+// unscaled width reaches e^160, beyond FP32's range). The FP64 mode ignores xm.
+template <typename R>
+__device__ width_t<R> channel_width(const ChanP<R> &c, R xm);
+template <>
+__device__ double channel_width<double>(const ChanP<double> &c, double)
 {
     if (!c.open) return 0.0;
     double F, G;
-    width_FG_R<double>(c.x, F, G);
+    width_FG(c.x, F, G);
     const double a = c.a;
     const double I = F / (4.0 * a * a) + c.b * G / (2.0 * a);
     return c.w0 * I;
 }
 template <>
-__device__ double channel_width<float>(const ChanP<float> &c)
+__device__ float channel_width<float>(const ChanP<float> &c, float xm)
 {
-    if (!c.open) return 0.0;
-    double F, G;
-    width_FG_R<float>(c.x, F, G);
+    if (!c.open) return 0.f;
+    // s = e^-xm underflows to 0 for xm above about 103; the terms it multiplies are then
+    // below 2^-24 of the largest width, which the FP32 sum of the six cannot resolve anyway.
+    const float x = c.x, s = expf(-xm);
+    float F, G;
+    if (x >= 1.f) {
+        const float ex = expf(x - xm);
+        F = ex * (x * x - 3.f * x + 3.f) + (0.5f * x * x - 3.f) * s;
+        G = ex * (x - 1.f) + s;
+    } else {
+        float term = x, f = 0.f, g = 0.f;  // term = x^n / n!
+#pragma unroll 1
+        for (int n = 2; n <= 20; ++n) {
+            term *= x / float(n);
+            g += float(n - 1) * term;
+            if (n >= 4) f += float((n - 1) * (n - 3)) * term;
+        }
+        F = f * s;
+        G = g * s;
+    }
     const float ia = 1.f / c.a;
-    return f2d(c.w0) * (F * f2d(0.25f * ia * ia) + G * f2d(0.5f * c.b * ia));
+    return c.w0 * (F * (0.25f * ia * ia) + G * (0.5f * c.b * ia));
+}
+
+// The scale reference of a step's widths: the largest x of the open channels (0 if none).
+template <typename R>
+__device__ __forceinline__ R widths_xm(const ChanP<R> *chans)
+{
+    R xm = R(0);
+#pragma unroll
+    for (int j = 0; j < 6; ++j)
+        if (chans[j].open && chans[j].x > xm) xm = chans[j].x;
+    return xm;
 }
 
 // Two-body decay of the parent (invariant mass W) into an ejectile of mass m1 and a
@@ -1041,59 +1085,84 @@ __device__ void decay_to_lab<double>(double W, double m1, double m2, double eps,
     u[1] = (float)(pl[1] / pln);
     u[2] = (float)(pl[2] / pln);
 }
-// FP32 mode: rest-frame momentum and angles in FP32 (the factors of p^2 are all positive,
-// so there is no cancellation); the lab boost, the lab energy and the parent's four-momentum
-// bookkeeping in FP64.
+// FP32 mode: the decay and the boost in FP32, the parent's four-momentum bookkeeping in FP64.
+// The factors of p^2 are all positive, so there is no cancellation; the parent is a recoiling
+// nucleus (|beta| of order 0.01), so gamma - 1 is taken as beta^2 gamma^2 / (gamma + 1) and
+// the lab kinetic energy as (gamma - 1) m1 + gamma (T* + beta.p*), with no difference of
+// total energies. The release is taken as at least 0: with x in FP32, a draw of t within a
+// few 1e-7 of 0 on a channel without barrier (V = 0) can put the daughter's excitation U_d an
+// FP32 rounding above E* - Q (about 5e-7 of such emissions, in emulation), which would
+// otherwise give a NaN momentum.
 template <>
 __device__ void decay_to_lab<float>(double W, double m1, double m2, double eps, float ct, float ph,
                                     const Lane<float> &L, double *pl, double &el, double &Tl, float *u)
 {
-    const float ef = d2f(eps), m1f = d2f(m1), m2f = d2f(m2), Wf = d2f(W);
+    const float ef = fmaxf(d2f(eps), 0.f), m1f = d2f(m1), m2f = d2f(m2), Wf = d2f(W);
     const float pd2 = ef * (2.f * (m1f + m2f) + ef) * (2.f * m2f + ef) * (2.f * m1f + ef) / (4.f * Wf * Wf);
     const float pd = sqrtf(pd2);
     const float tcm = pd2 / (sqrtf(pd2 + m1f * m1f) + m1f);  // rest-frame kinetic energy
     const float sn = sqrtf((1.f - ct) * (1.f + ct));
     float sph, cph;
     __sincosf(ph, &sph, &cph);
-    const double pv[3] = {f2d(pd * sn * cph), f2d(pd * sn * sph), f2d(pd * ct)};
-    const double e1 = m1 + f2d(tcm);
-    const double Pr[3] = {L.Prx, L.Pry, L.Prz};
-    const double Er = L.Er;
-    const double M2 = Er * Er - dot3(Pr, Pr);
-    const double iEr = 1.0 / Er;
-    const double gamma = Er * rsqrt(M2);
-    const double beta[3] = {Pr[0] * iEr, Pr[1] * iEr, Pr[2] * iEr};
-    const double bp = dot3(beta, pv);
-    const double f = gamma * gamma / (gamma + 1.0) * bp + gamma * e1;
+    const float pv[3] = {pd * sn * cph, pd * sn * sph, pd * ct};
+    const float iE = 1.f / d2f(L.Er);
+    const float beta[3] = {d2f(L.Prx) * iE, d2f(L.Pry) * iE, d2f(L.Prz) * iE};
+    const float b2 = beta[0] * beta[0] + beta[1] * beta[1] + beta[2] * beta[2];
+    const float g2 = 1.f / (1.f - b2);
+    const float g = sqrtf(g2);
+    const float bp = beta[0] * pv[0] + beta[1] * pv[1] + beta[2] * pv[2];
+    const float f = g2 / (g + 1.f) * bp + g * (m1f + tcm);
+    float plf[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) pl[k] = pv[k] + beta[k] * f;
-    el = gamma * (e1 + bp);
-    Tl = el - m1;
-    const float plf[3] = {d2f(pl[0]), d2f(pl[1]), d2f(pl[2])};
+    for (int k = 0; k < 3; ++k) {
+        plf[k] = pv[k] + beta[k] * f;
+        pl[k] = f2d(plf[k]);
+    }
+    const float Tf = fmaxf(b2 * g2 / (g + 1.f) * m1f + g * (tcm + bp), 0.f);
+    Tl = f2d(Tf);
+    el = m1 + Tl;
     const float r = rsqrtf(plf[0] * plf[0] + plf[1] * plf[1] + plf[2] * plf[2]);
     u[0] = plf[0] * r;
     u[1] = plf[1] * r;
     u[2] = plf[2] * r;
 }
 
+// The daughter's excitation U_d = (x - t)^2 / (4a) after an emission at t (§2.4): FP64 in the
+// FP64 mode (the oracle's operations), FP32 in the FP32 mode.
+template <typename R>
+__device__ __forceinline__ double daughter_excitation(R x, R t, R a);
+template <>
+__device__ __forceinline__ double daughter_excitation<double>(double x, double t, double a)
+{
+    const double xt = x - t;
+    return xt * xt / (4.0 * a);
+}
+template <>
+__device__ __forceinline__ double daughter_excitation<float>(float x, float t, float a)
+{
+    const float xt = x - t;
+    return f2d(xt * xt / (4.f * a));
+}
+
 // The second half of an evaporation step (§2.4), given the six channel widths G of the
 // parent (Z, A, E* in L): the channel draw, the emission energy, and the two-body decay
 // isotropic in the parent's rest frame, boosted to the lab.
 template <typename R, bool kCount>
-__device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const ChanP<R> *chans, const double *G,
-                          Counters<kCount> &C)
+__device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const ChanP<R> *chans,
+                          const width_t<R> *G, Counters<kCount> &C)
 {
+    using W = width_t<R>;
     const int Z = L.Z, A = L.A;
     const double Estar = L.Estar;
-    double S = 0.0;
+    W S = W(0);
 #pragma unroll
     for (int j = 0; j < 6; ++j) S += G[j];
-    if (!(S > 0.0)) {
+    if (!(S > W(0))) {
         L.phase = kFinish;
         return;
     }
     C.add(PNUC_C_EVAP_STEPS);
-    double us = to_d<R>(L.rng.next()) * S, cum = 0.0;
+    W us = static_cast<W>(L.rng.next()) * S, cum = W(0);
     int ch = -1;
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) {
@@ -1102,7 +1171,7 @@ __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const 
     }
     if (ch < 0)
         for (int j = 5; j >= 0; --j)
-            if (G[j] > 0.0) {
+            if (G[j] > W(0)) {
                 ch = j;
                 break;
             }
@@ -1115,8 +1184,7 @@ __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const 
         L.phase = kFinish;
         return;
     }
-    const double xt = to_d<R>(c.x) - to_d<R>(tt);
-    const double Ud = xt * xt / (4.0 * to_d<R>(c.a));
+    const double Ud = daughter_excitation<R>(c.x, tt, c.a);
     const double eps = (Estar - c.Q) - Ud;
     const R ctr = R(2) * L.rng.next() - R(1);
     const R phr = R(kTwoPi) * L.rng.next();
@@ -1146,27 +1214,54 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     }
     C.add(PNUC_C_EVAP_PASSES);
     const double Mparent = __ldg(&P.mass[L.Z * kMassA + L.A]);
-    double G[6];
+    width_t<R> G[6];
     ChanP<R> chans[6];  // kept for the chosen channel
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) {
         channel_params<R>(P, L.Z, L.A, Mparent, L.Estar, j, chans[j]);
-        G[j] = channel_width<R>(chans[j]);
         if (chans[j].open) C.add(chans[j].x >= R(1) ? PNUC_C_EVAP_EXPS : PNUC_C_EVAP_SERIES);
     }
+    const R xm = widths_xm<R>(chans);
+#pragma unroll 1
+    for (int j = 0; j < 6; ++j) G[j] = channel_width<R>(chans[j], xm);
     evap_emit<R, kCount>(P, L, Mparent, chans, G, C);
 }
 
 // ------------------------------------------------------------------ warp-wide widths
-// One width evaluation: the parameters channel_width() reads.
+// One width evaluation: the parameters channel_width() reads (the FP32 mode's with the
+// scale reference xm of the job's lane).
 template <typename R>
 struct WidthJob {
     R x, a, b, w0;
 };
+template <>
+struct WidthJob<float> {
+    float x, a, b, w0, xm;
+};
+template <typename R>
+__device__ __forceinline__ WidthJob<R> make_job(const ChanP<R> &c, R)
+{
+    return WidthJob<R>{c.x, c.a, c.b, c.w0};
+}
+template <>
+__device__ __forceinline__ WidthJob<float> make_job<float>(const ChanP<float> &c, float xm)
+{
+    return WidthJob<float>{c.x, c.a, c.b, c.w0, xm};
+}
+template <typename R>
+__device__ __forceinline__ R job_xm(const WidthJob<R> &)
+{
+    return R(0);
+}
+template <>
+__device__ __forceinline__ float job_xm<float>(const WidthJob<float> &jb)
+{
+    return jb.xm;
+}
 constexpr int kWidthSlots = 6 * 32;  // per warp: six channels of every lane
 
 template <typename R>
-__device__ __forceinline__ double job_width(const WidthJob<R> &jb)
+__device__ __forceinline__ width_t<R> job_width(const WidthJob<R> &jb)
 {
     ChanP<R> c;
     c.open = true;
@@ -1174,18 +1269,18 @@ __device__ __forceinline__ double job_width(const WidthJob<R> &jb)
     c.a = jb.a;
     c.b = jb.b;
     c.w0 = jb.w0;
-    return channel_width<R>(c);
+    return channel_width<R>(c, job_xm<R>(jb));
 }
 
 // One evaporation step of every lane of the warp with `active` set (the evaporation kernel).
 // The widths are evaluated by the whole warp: the (lane, channel) pairs of open channels
-// go to a job list in shared memory, those that need the FP64 exponential (x >= 1) from the
+// go to a job list in shared memory, those that need the exponential (x >= 1) from the
 // front and the series ones (x < 1) from the back, and the 32 lanes work through it. One
 // pass then serves up to 32 exponentials, where the per-lane loop issues one pass per channel
 // for whichever lanes have it open; each width is channel_width()'s arithmetic, bit for bit.
 // Called by all 32 lanes of the warp; jobs and wout are the warp's kWidthSlots entries.
 template <typename R, bool kCount>
-__device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, WidthJob<R> *jobs, double *wout,
+__device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, WidthJob<R> *jobs, width_t<R> *wout,
                                Counters<kCount> &C)
 {
     if (active && L.n_evap >= P.max_evap_steps) {
@@ -1206,11 +1301,15 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
             chans[j].open = false;
             chans[j].x = R(0);
         }
+    }
+    const R xm = widths_xm<R>(chans);
+#pragma unroll 1
+    for (int j = 0; j < 6; ++j) {
         const bool ex = chans[j].open && chans[j].x >= R(1);
         const bool se = chans[j].open && !(chans[j].x >= R(1));
         const unsigned me = __ballot_sync(FULL, ex), ms = __ballot_sync(FULL, se);
         slot[j] = ex ? nexp + __popc(me & below) : kWidthSlots - 1 - (nser + __popc(ms & below));
-        if (ex || se) jobs[slot[j]] = WidthJob<R>{chans[j].x, chans[j].a, chans[j].b, chans[j].w0};
+        if (ex || se) jobs[slot[j]] = make_job<R>(chans[j], xm);
         nexp += __popc(me);
         nser += __popc(ms);
     }
@@ -1226,9 +1325,9 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
     for (int k = lane; k < nexp; k += 32) wout[k] = job_width<R>(jobs[k]);
     for (int k = kWidthSlots - 1 - (int)lane; k >= kWidthSlots - nser; k -= 32) wout[k] = job_width<R>(jobs[k]);
     __syncwarp();
-    double G[6];
+    width_t<R> G[6];
 #pragma unroll
-    for (int j = 0; j < 6; ++j) G[j] = chans[j].open ? wout[slot[j]] : 0.0;
+    for (int j = 0; j < 6; ++j) G[j] = chans[j].open ? wout[slot[j]] : width_t<R>(0);
     __syncwarp();  // the list is reused by the next step
     if (active) evap_emit<R, kCount>(P, L, Mparent, chans, G, C);
 }

@@ -48,7 +48,7 @@ __host__ __device__ constexpr size_t smem_bytes(int n_targets, int block)
 template <typename R>
 __host__ __device__ constexpr size_t evap_smem_bytes(int n_targets, int block)
 {
-    return smem_bytes<R>(n_targets, block) + (size_t)(block / 32) * kWidthSlots * (sizeof(WidthJob<R>) + sizeof(double));
+    return smem_bytes<R>(n_targets, block) + (size_t)(block / 32) * kWidthSlots * (sizeof(WidthJob<R>) + sizeof(width_t<R>));
 }
 
 template <typename R>
@@ -243,7 +243,7 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
 }
 
 // Persistent evaporation kernel (after the cascade kernel on the same stream): every lane
-// evaporates, so the FP64 width exponentials and the decays run with full warps. Lanes take
+// evaporates, so the width exponentials and the FP64 decays run with full warps. Lanes take
 // event indices from the evaporation queue and skip events with nothing pending.
 template <typename R, bool kCount>
 __device__ __forceinline__ void evap_body(const SimParams &P)
@@ -267,7 +267,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     WidthJob<R> *jobs0 = reinterpret_cast<WidthJob<R> *>(smem + smem_bytes<R>(P.n_targets, blockDim.x));
     WidthJob<R> *jobs = jobs0 + warp * kWidthSlots;
-    double *wout = reinterpret_cast<double *>(jobs0 + nwarps * kWidthSlots) + warp * kWidthSlots;
+    width_t<R> *wout = reinterpret_cast<width_t<R> *>(jobs0 + nwarps * kWidthSlots) + warp * kWidthSlots;
     while (true) {
         const long long t_top = kCount ? clock64() : 0;
         if (L.phase == kFinish) {
