@@ -1148,8 +1148,7 @@ __device__ __forceinline__ double daughter_excitation<float>(float x, float t, f
 // parent (Z, A, E* in L): the channel draw, the emission energy, and the two-body decay
 // isotropic in the parent's rest frame, boosted to the lab.
 template <typename R, bool kCount>
-__device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const ChanP<R> *chans,
-                          const width_t<R> *G, Counters<kCount> &C)
+__device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const width_t<R> *G, Counters<kCount> &C)
 {
     using W = width_t<R>;
     const int Z = L.Z, A = L.A;
@@ -1175,7 +1174,8 @@ __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const 
                 ch = j;
                 break;
             }
-    const ChanP<R> c = chans[ch];
+    ChanP<R> c;  // the chosen channel's parameters, recomputed (the same function of Z, A, E*)
+    channel_params<R>(P, Z, A, Mparent, Estar, ch, c);
     int trials = 0;
     R tt = sample_t<R>(L.rng, c.a, c.x, c.b, P.max_evap_trials, trials);
     C.add(PNUC_C_EVAP_TRIALS, trials);
@@ -1215,7 +1215,7 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     C.add(PNUC_C_EVAP_PASSES);
     const double Mparent = __ldg(&P.mass[L.Z * kMassA + L.A]);
     width_t<R> G[6];
-    ChanP<R> chans[6];  // kept for the chosen channel
+    ChanP<R> chans[6];
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) {
         channel_params<R>(P, L.Z, L.A, Mparent, L.Estar, j, chans[j]);
@@ -1224,44 +1224,21 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     const R xm = widths_xm<R>(chans);
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) G[j] = channel_width<R>(chans[j], xm);
-    evap_emit<R, kCount>(P, L, Mparent, chans, G, C);
+    evap_emit<R, kCount>(P, L, Mparent, G, C);
 }
 
 // ------------------------------------------------------------------ warp-wide widths
-// One width evaluation: the parameters channel_width() reads (the FP32 mode's with the
-// scale reference xm of the job's lane).
+// One width evaluation: the parameters channel_width() reads, and where its result goes
+// (6 x lane + channel in the warp's width array).
 template <typename R>
 struct WidthJob {
     R x, a, b, w0;
+    int tag;
 };
-template <>
-struct WidthJob<float> {
-    float x, a, b, w0, xm;
-};
-template <typename R>
-__device__ __forceinline__ WidthJob<R> make_job(const ChanP<R> &c, R)
-{
-    return WidthJob<R>{c.x, c.a, c.b, c.w0};
-}
-template <>
-__device__ __forceinline__ WidthJob<float> make_job<float>(const ChanP<float> &c, float xm)
-{
-    return WidthJob<float>{c.x, c.a, c.b, c.w0, xm};
-}
-template <typename R>
-__device__ __forceinline__ R job_xm(const WidthJob<R> &)
-{
-    return R(0);
-}
-template <>
-__device__ __forceinline__ float job_xm<float>(const WidthJob<float> &jb)
-{
-    return jb.xm;
-}
 constexpr int kWidthSlots = 6 * 32;  // per warp: six channels of every lane
 
 template <typename R>
-__device__ __forceinline__ width_t<R> job_width(const WidthJob<R> &jb)
+__device__ __forceinline__ width_t<R> job_width(const WidthJob<R> &jb, R xm)
 {
     ChanP<R> c;
     c.open = true;
@@ -1269,7 +1246,7 @@ __device__ __forceinline__ width_t<R> job_width(const WidthJob<R> &jb)
     c.a = jb.a;
     c.b = jb.b;
     c.w0 = jb.w0;
-    return channel_width<R>(c, job_xm<R>(jb));
+    return channel_width<R>(c, xm);
 }
 
 // One evaporation step of every lane of the warp with `active` set (the evaporation kernel).
@@ -1278,10 +1255,13 @@ __device__ __forceinline__ width_t<R> job_width(const WidthJob<R> &jb)
 // front and the series ones (x < 1) from the back, and the 32 lanes work through it. One
 // pass then serves up to 32 exponentials, where the per-lane loop issues one pass per channel
 // for whichever lanes have it open; each width is channel_width()'s arithmetic, bit for bit.
-// Called by all 32 lanes of the warp; jobs and wout are the warp's kWidthSlots entries.
+// Each result goes to its lane's six entries of gw (closed channels are set to 0 by their
+// lane), with the lane's scale reference in xms; no per-lane channel records are kept, so
+// nothing of the step lives in local memory. Called by all 32 lanes of the warp; jobs and gw
+// are the warp's kWidthSlots entries, xms its 32.
 template <typename R, bool kCount>
-__device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, WidthJob<R> *jobs, width_t<R> *wout,
-                               Counters<kCount> &C)
+__device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, WidthJob<R> *jobs, width_t<R> *gw,
+                               R *xms, Counters<kCount> &C)
 {
     if (active && L.n_evap >= P.max_evap_steps) {
         L.flags |= PNUC_FLAG_EVAP_STEP_CAP;
@@ -1290,29 +1270,32 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
     }
     const unsigned FULL = 0xffffffffu, lane = threadIdx.x & 31, below = (1u << lane) - 1u;
     const double Mparent = active ? __ldg(&P.mass[L.Z * kMassA + L.A]) : 0.0;
-    ChanP<R> chans[6];
-    int slot[6];
+    width_t<R> *G = gw + 6 * lane;
+    R xm = R(0);
     int nexp = 0, nser = 0;
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) {
+        ChanP<R> c;
         if (active) {
-            channel_params<R>(P, L.Z, L.A, Mparent, L.Estar, j, chans[j]);
+            channel_params<R>(P, L.Z, L.A, Mparent, L.Estar, j, c);
         } else {
-            chans[j].open = false;
-            chans[j].x = R(0);
+            c.open = false;
+            c.x = R(0);
         }
-    }
-    const R xm = widths_xm<R>(chans);
-#pragma unroll 1
-    for (int j = 0; j < 6; ++j) {
-        const bool ex = chans[j].open && chans[j].x >= R(1);
-        const bool se = chans[j].open && !(chans[j].x >= R(1));
+        const bool ex = c.open && c.x >= R(1);
+        const bool se = c.open && !(c.x >= R(1));
         const unsigned me = __ballot_sync(FULL, ex), ms = __ballot_sync(FULL, se);
-        slot[j] = ex ? nexp + __popc(me & below) : kWidthSlots - 1 - (nser + __popc(ms & below));
-        if (ex || se) jobs[slot[j]] = make_job<R>(chans[j], xm);
+        if (ex || se) {
+            const int slot = ex ? nexp + __popc(me & below) : kWidthSlots - 1 - (nser + __popc(ms & below));
+            jobs[slot] = WidthJob<R>{c.x, c.a, c.b, c.w0, (int)(6 * lane) + j};
+            if (c.x > xm) xm = c.x;
+        } else {
+            G[j] = width_t<R>(0);
+        }
         nexp += __popc(me);
         nser += __popc(ms);
     }
+    xms[lane] = xm;
     if (kCount) {
         const unsigned act = __ballot_sync(FULL, active);
         if (lane == 0) {
@@ -1322,14 +1305,17 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
         }
     }
     __syncwarp();
-    for (int k = lane; k < nexp; k += 32) wout[k] = job_width<R>(jobs[k]);
-    for (int k = kWidthSlots - 1 - (int)lane; k >= kWidthSlots - nser; k -= 32) wout[k] = job_width<R>(jobs[k]);
+    for (int k = lane; k < nexp; k += 32) {
+        const WidthJob<R> jb = jobs[k];
+        gw[jb.tag] = job_width<R>(jb, xms[jb.tag / 6]);
+    }
+    for (int k = kWidthSlots - 1 - (int)lane; k >= kWidthSlots - nser; k -= 32) {
+        const WidthJob<R> jb = jobs[k];
+        gw[jb.tag] = job_width<R>(jb, xms[jb.tag / 6]);
+    }
     __syncwarp();
-    width_t<R> G[6];
-#pragma unroll
-    for (int j = 0; j < 6; ++j) G[j] = chans[j].open ? wout[slot[j]] : width_t<R>(0);
-    __syncwarp();  // the list is reused by the next step
-    if (active) evap_emit<R, kCount>(P, L, Mparent, chans, G, C);
+    if (active) evap_emit<R, kCount>(P, L, Mparent, G, C);
+    __syncwarp();  // the lists are reused by the next step
 }
 
 // Advances lane L by one step of its current phase (no batching: the plain kernel).

@@ -48,7 +48,8 @@ __host__ __device__ constexpr size_t smem_bytes(int n_targets, int block)
 template <typename R>
 __host__ __device__ constexpr size_t evap_smem_bytes(int n_targets, int block)
 {
-    return smem_bytes<R>(n_targets, block) + (size_t)(block / 32) * kWidthSlots * (sizeof(WidthJob<R>) + sizeof(width_t<R>));
+    return smem_bytes<R>(n_targets, block) +
+           (size_t)(block / 32) * (kWidthSlots * (sizeof(WidthJob<R>) + sizeof(width_t<R>)) + 32 * sizeof(R));
 }
 
 template <typename R>
@@ -267,7 +268,9 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     WidthJob<R> *jobs0 = reinterpret_cast<WidthJob<R> *>(smem + smem_bytes<R>(P.n_targets, blockDim.x));
     WidthJob<R> *jobs = jobs0 + warp * kWidthSlots;
-    width_t<R> *wout = reinterpret_cast<width_t<R> *>(jobs0 + nwarps * kWidthSlots) + warp * kWidthSlots;
+    width_t<R> *gw0 = reinterpret_cast<width_t<R> *>(jobs0 + nwarps * kWidthSlots);
+    width_t<R> *gw = gw0 + warp * kWidthSlots;
+    R *xms = reinterpret_cast<R *>(gw0 + nwarps * kWidthSlots) + warp * 32;
     while (true) {
         const long long t_top = kCount ? clock64() : 0;
         if (L.phase == kFinish) {
@@ -294,7 +297,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
         const long long t1 = kCount ? clock64() : 0;
         const bool stepping = L.phase == kEvap;
         if (stepping) L.rng.ensure(8);
-        step_evap_warp<R, kCount>(P, L, stepping, jobs, wout, C);
+        step_evap_warp<R, kCount>(P, L, stepping, jobs, gw, xms, C);
         if (kCount) {
             __syncwarp();
             if (lane == 0) {
