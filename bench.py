@@ -2,7 +2,7 @@
 
 Workload per GPU (one "step" = one launch of the whole hot path over one batch):
 1e6 proton-16O + 1e6 proton-40Ca events at 200 MeV (one batch of 2e6 events, two targets),
-FP32 bulk mode (FP64 boosts, bookkeeping and evaporation widths), persistent kernel with
+FP32 bulk mode (FP64 collision boosts and energy/momentum bookkeeping), persistent kernel with
 warp-level lane refill. The same batch is also timed with the plain one-event-per-thread
 kernel ("batched vs plain"). Inputs are synthetic (seeded) and resident in HBM when the timed
 region starts; the e2e figure goes through the host-buffer C-ABI entry point with the
@@ -471,7 +471,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_EVENTS_PER_S, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "events_per_step": n, "precision": "fp32 bulk, fp64 boosts/bookkeeping/widths",
+        "config": {"workload": WORKLOAD, "events_per_step": n, "precision": "fp32 bulk, fp64 collision boosts and bookkeeping",
                    "method": "persistent (warp refill)", "tuning": ctx.get_tuning("fp32"),
                    "l2": "256 MiB buffer written between steps (inside the timed region)",
                    "parallelism": f"{world} rank(s), event-id ranges, no collective"},
