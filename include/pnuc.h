@@ -43,8 +43,9 @@ typedef enum {
 } pnuc_status;
 
 typedef enum {
-    PNUC_FP32 = 0, /* bulk transport, path and cross-section arithmetic in FP32; Lorentz
-                      boosts, energy/momentum bookkeeping and evaporation widths in FP64 */
+    PNUC_FP32 = 0, /* bulk transport, path, cross-section and evaporation arithmetic in
+                      FP32 (the widths scaled by the largest channel's exponential); the
+                      collision boosts, Q-values and energy/momentum bookkeeping in FP64 */
     PNUC_FP64 = 1  /* everything in FP64, no fused multiply-add: reproduces the CPU
                       oracle event by event up to libm rounding */
 } pnuc_precision;
