@@ -1020,8 +1020,8 @@ template <>
 __device__ float channel_width<float>(const ChanP<float> &c, float xm)
 {
     if (!c.open) return 0.f;
-    // s = e^-xm underflows to 0 for xm above about 103; the terms it multiplies are then
-    // below 2^-24 of the largest width, which the FP32 sum of the six cannot resolve anyway.
+    // s = e^-xm is 0 for xm above about 87 (the FP32 kernels flush denormals); the terms it
+    // multiplies are then below 2^-24 of the largest width, which the FP32 sum cannot resolve.
     const float x = c.x, s = expf(-xm);
     float F, G;
     if (x >= 1.f) {
