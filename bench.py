@@ -2,8 +2,10 @@
 
 Workload per GPU (one "step" = one launch of the whole hot path over one batch):
 1e6 proton-16O + 1e6 proton-40Ca events at 200 MeV (one batch of 2e6 events, two targets),
-FP32 bulk mode (FP64 collision boosts and energy/momentum bookkeeping), persistent kernel with
-warp-level lane refill. The same batch is also timed with the plain one-event-per-thread
+FP32 bulk mode (FP64 NN collision boosts, energy/momentum bookkeeping and evaporation widths
+with their exponentials), persistent kernel with warp-level lane refill. Beside it: the scaled
+FP32 mode (evaporation widths in FP32 too), the plain kernel, the FP64 mode, and the other
+configurations' workloads (4e6 mixed targets from a graph, 1e6 per heavy target). The same batch is also timed with the plain one-event-per-thread
 kernel ("batched vs plain"). Inputs are synthetic (seeded) and resident in HBM when the timed
 region starts; the e2e figure goes through the host-buffer C-ABI entry point with the
 host<->device transfers inside the timed region (inputs copied in; outputs written by the
@@ -37,27 +39,46 @@ ENERGY = 200.0
 PAPER_EVENTS_PER_S = 2 * 2.6e6 / (6.61 + 9.77)
 WORKLOAD = "1e6 p-16O + 1e6 p-40Ca at 200 MeV, one batch of 2e6 events per step"
 
-# Algorithmic FP64 operations of the FP32-mode model per counted unit, from the operations
-# the model performs in FP64 there (Lorentz boosts, energy/momentum bookkeeping, evaporation
-# Q-values): add, multiply, FMA and compare count 1; a division, square root or reciprocal
-# square root 8 (Newton-Raphson instruction counts). Conversions between float and double are not arithmetic (the kernels do them on
-# the integer pipes). The units are the kernels' own counters.
+# Algorithmic FP64 operations of the FP32-mode model per counted unit: the operations the
+# model performs in FP64 there (the NN collision boosts, the event's energy/momentum
+# bookkeeping, the evaporation Q-values, and in the FP32 mode the evaporation widths with
+# their exponentials and the channel draw), each add, multiply, fused multiply-add, compare,
+# divide, square root, reciprocal square root or exponential counting as one operation.
+# Conversions between float and double are not arithmetic (the kernels do them on the integer
+# pipes). The units are the kernels' own counters.
 CASCADE_FP64_OPS = {
-    # pair sums and energies 6, s 4, 1/sqrt(s) 8, 1/E_t 8, beta and gamma 4, gamma^2/(gamma+1)
-    # 10, CM direction 8, p* 1, K 3, CM energies 8, back boost 10, q1 and q2 6, T1 and T2 6;
-    # the Pauli and cutoff tests 6
-    "kinematics": 86,
+    # pair sums and energies 6, s 4, 1/sqrt(s) 1, 1/E_t 1, beta and gamma 4,
+    # gamma^2/(gamma+1) 3, CM direction 8, p* 1, K 3, CM energies 8, back boost 10, q1 and q2
+    # 6, T1 and T2 6; the Pauli and cutoff tests 4
+    "kinematics": 65,
     "escapes": 5,  # energy and momentum sums of an escaping nucleon
 }
-EVAP_FP64_OPS = {
-    "settled": 18,      # E* from the energy balance (p0 with its square root, the sums)
+EVAP_FP64_OPS_COMMON = {
+    "settled": 11,      # E* from the energy balance (p0 with its square root, the sums)
     "evap_passes": 18,  # six Q-values and excitations X = E* - Q
-    # the widths, the channel draw, U_d and the decay with its boost are FP32 arithmetic
-    # (widths scaled by the largest exponential); the parent's mass + E*, the release, the
-    # daughter's mass, and the parent's energy and momentum bookkeeping 9
+    # the parent's mass + E*, the release, the daughter's mass, and the parent's energy and
+    # momentum bookkeeping
     "evap_steps": 9,
 }
-KERNEL_FILES = ("pnuc_device.cuh", "pnuc_kernels.cuh", "kernel_fp32.cu", "pnuc_internal.h")
+EVAP_FP64_OPS = {
+    "fp32": {**EVAP_FP64_OPS_COMMON,
+             # widths in FP64: the exponential 1, F 3, G 2, the width 4 per open channel with
+             # x >= 1 (the series of a channel with x < 1 runs in FP32: the width 4); the sum
+             # of the six and its test 6 per pass, the channel draw 13 per step
+             "evap_exps": 10, "evap_series": 4},
+    # the widths, the channel draw, U_d and the decay with its boost are FP32 arithmetic
+    "fp32_scaled": dict(EVAP_FP64_OPS_COMMON),
+}
+EVAP_FP64_OPS["fp32"]["evap_passes"] += 6
+EVAP_FP64_OPS["fp32"]["evap_steps"] += 13
+KERNEL_FILES = ("pnuc_device.cuh", "pnuc_kernels.cuh", "kernel_fp32.cu", "pnuc_internal.h", "fpconv.h")
+PRECISION_NOTE = {
+    "fp32": "fp32 bulk (transport, free paths, cross sections, evaporation channel parameters, emission sampler "
+            "and decay); fp64 NN collision boosts, energy/momentum bookkeeping with the Q-values, and the "
+            "evaporation widths with their exponentials and the channel draw",
+    "fp32_scaled": "as fp32, but the evaporation widths and the channel draw in fp32 (each width scaled by the "
+                   "largest channel's exponential)",
+}
 
 
 def measured_hbm_gbs():
@@ -68,11 +89,38 @@ def measured_hbm_gbs():
         return None
 
 
+def strip_c_comments(text: str) -> str:
+    """C/C++ source with its comments removed and each run of whitespace made one space:
+    what the compiler sees, so that an edit to comments or layout alone keeps the hash."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == "/" and i + 1 < n and text[i + 1] == "/":
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif c == "/" and i + 1 < n and text[i + 1] == "*":
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        elif c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_sha1() -> str:
+    """Hash of the event kernels' sources without comments or layout (a profile summary taken
+    at other sources is not used)."""
     import hashlib
     h = hashlib.sha1()
     for f in KERNEL_FILES:
-        h.update(open(os.path.join(ROOT, "paper_1309_7963_gb300", "csrc", f), "rb").read())
+        h.update(strip_c_comments(open(os.path.join(ROOT, "paper_1309_7963_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()
 
 
@@ -93,9 +141,9 @@ def profile_values() -> dict:
     return out
 
 
-def fp64_ops_per_event(counters: dict, n_events: int) -> dict:
+def fp64_ops_per_event(counters: dict, n_events: int, precision: str = "fp32") -> dict:
     cas = sum(counters[k] * v for k, v in CASCADE_FP64_OPS.items()) / n_events
-    eva = sum(counters[k] * v for k, v in EVAP_FP64_OPS.items()) / n_events
+    eva = sum(counters[k] * v for k, v in EVAP_FP64_OPS[precision].items()) / n_events
     return {"cascade": cas, "evaporation": eva}
 
 
@@ -111,6 +159,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-divergence", action="store_true")
+    ap.add_argument("--no-others", action="store_true")
     return ap.parse_args()
 
 
@@ -250,6 +299,69 @@ def divergence_bound(ctx, n: int = 1_000_000, run: int = 32, reps: int = 3) -> d
     return out
 
 
+def other_workloads(ctx, flush, reps: int = 5, warm: int = 3) -> dict:
+    """The other configurations' workloads, each timed with CUDA events on the launching
+    stream (median of `reps` launches after `warm`, L2 flushed before each): 4e6 events on the
+    mixed tissue targets at 20-250 MeV (one persistent launch with the autotuner's tuning,
+    replayed from a CUDA graph) and 1e6 events on each heavy target at 100-250 MeV (persistent
+    method), FP32 mode, each beside the plain kernel on the same batch."""
+    import torch
+
+    from paper_1309_7963_gb300 import inputs
+    stream = torch.cuda.current_stream()
+
+    def median_ms(fn, r=reps, wu=warm):
+        for _ in range(wu):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for k in range(r):
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    res = {}
+    w = inputs.mixed(4_000_000, seed=0)
+    tids = np.array([ctx.create_target(*za) for za in w.targets], np.int32)
+    e = torch.tensor(w.energies, device="cuda")
+    t = torch.tensor(tids[w.tidx], device="cuda")
+    buf = ctx.alloc(w.n, capacity=8 * w.n)
+    saved = ctx.get_tuning("fp32")
+    try:
+        best, _ = ctx.autotune(e, t, seed=w.seed, precision="fp32", reps=1)
+        g = ctx.graph(e, t, seed=w.seed, out=buf, precision="fp32")
+        ms = median_ms(g.launch)
+        g.close()
+    finally:
+        ctx.set_tuning("fp32", **saved)
+    pms = median_ms(lambda: ctx.simulate(e, t, seed=w.seed, precision="fp32", method="plain", out=buf), r=3, wu=1)
+    res["mixed_4e6_graph_autotuned"] = {
+        "workload": "4e6 events, 20-250 MeV, 60% 16O / 20% 12C / 10% 14N / 5% 40Ca / 5% 31P, one persistent "
+                    "launch replayed from a CUDA graph with the autotuned tuning",
+        "tuning": best, "ms": ms, "value": w.n / (ms * 1e-3), "plain_ms": pms, "plain_value": w.n / (pms * 1e-3),
+        "batched_vs_plain": pms / ms}
+    del buf, e, t
+    for target in (inputs.TI48, inputs.FE56, inputs.PB208):
+        w = inputs.heavy(target, 1_000_000, seed=3)
+        tids = np.array([ctx.create_target(*za) for za in w.targets], np.int32)
+        e = torch.tensor(w.energies, device="cuda")
+        t = torch.tensor(tids[w.tidx], device="cuda")
+        buf = ctx.alloc(w.n, capacity=24 * w.n)
+        ms = median_ms(lambda: ctx.simulate(e, t, seed=w.seed, precision="fp32", method="persistent", out=buf))
+        pms = median_ms(lambda: ctx.simulate(e, t, seed=w.seed, precision="fp32", method="plain", out=buf), r=3, wu=1)
+        res[f"heavy_{target[1]}_1e6"] = {
+            "workload": f"1e6 events on (Z, A) = {target}, 100-250 MeV, persistent method", "ms": ms,
+            "value": w.n / (ms * 1e-3), "plain_ms": pms, "plain_value": w.n / (pms * 1e-3),
+            "batched_vs_plain": pms / ms}
+        del buf, e, t
+    return res
+
+
 def cpu_baseline(n_each: int, threads: int | None = None) -> dict:
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle
@@ -344,12 +456,22 @@ def main():
     total_ms, kern_ms = timed("persistent", args.steps, args.warmup, per_kernel=True)
     ctx.kernel_timing(False)
     ktimes = ctx.kernel_times()
-    clk = clocks.stop()
     total_ms = pdist.max_over_ranks(total_ms, device="cuda")
     n_sec = out.n_secondaries()
     res = out.residuals_np()
     value = world * n * args.steps / (total_ms * 1e-3)
     launch_ms = float(np.mean(kern_ms))
+
+    # the same batch with the evaporation widths and the channel draw in FP32 (scaled widths)
+    s_steps = max(2, args.steps // 2)
+    s_total, _ = timed("persistent", s_steps, args.warmup, per_kernel=True, precision="fp32_scaled")
+    ctx.kernel_timing(False)
+    s_kt = ctx.kernel_times()
+    s_total = pdist.max_over_ranks(s_total, device="cuda")
+    scaled = {"value": world * n * s_steps / (s_total * 1e-3), "unit": UNIT, "ms_per_step": s_total / s_steps,
+              "steps": s_steps, "precision": PRECISION_NOTE["fp32_scaled"],
+              "cascade_ms": s_kt["cascade_ms"] / max(1, s_kt["launches"]),
+              "evaporation_ms": s_kt["evaporation_ms"] / max(1, s_kt["launches"])}
 
     plain = None
     if not args.no_plain:
@@ -366,6 +488,8 @@ def main():
         fp64 = {"persistent": world * n * 2 / (f_pers * 1e-3), "sorted": world * n * 2 / (f_sort * 1e-3),
                 "plain": world * n * 2 / (f_plain * 1e-3), "unit": UNIT,
                 "batched_vs_plain": f_plain / min(f_pers, f_sort)}
+    others = None if (args.no_others or world > 1) else other_workloads(ctx, flush)
+    clk = clocks.stop()
 
     e2e = None
     if not args.no_e2e:
@@ -421,7 +545,8 @@ def main():
     torch.cuda.synchronize()
     counters = cnt.counters_dict()
     del cnt
-    ops_ev = fp64_ops_per_event(counters, n)
+    ops_ev = fp64_ops_per_event(counters, n, "fp32")
+    ops_ev_scaled = fp64_ops_per_event(counters, n, "fp32_scaled")
     peaks = ctx.measure_peaks()
     kernels = {}
     prof = profile_values()
@@ -446,6 +571,9 @@ def main():
                                       "unit": "G warp-inst/s", "frac": rate / issue_peak}
         else:
             kernels[name]["issue"] = None
+    scaled["evaporation_fp64_ops_per_event"] = ops_ev_scaled["evaporation"]
+    scaled["evaporation_fp64_frac"] = (ops_ev_scaled["evaporation"] * n / (scaled["evaporation_ms"] * 1e-3)
+                                       / peaks["fp64_fma"]) if scaled["evaporation_ms"] > 0 else None
     top = max(kernels, key=lambda k: kernels[k]["ms_per_launch"])
     kt = kernels[top]
     roofline = {"bound": "alu", "pipe": "fp64", "kernel": f"{top} kernel (FP32 mode)", "achieved": kt["achieved"],
@@ -471,13 +599,14 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_EVENTS_PER_S, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "events_per_step": n, "precision": "fp32 bulk, fp64 collision boosts and bookkeeping",
+        "config": {"workload": WORKLOAD, "events_per_step": n, "precision": PRECISION_NOTE["fp32"],
                    "method": "persistent (warp refill)", "tuning": ctx.get_tuning("fp32"),
                    "l2": "256 MiB buffer written between steps (inside the timed region)",
                    "parallelism": f"{world} rank(s), event-id ranges, no collective"},
         "launch_ms": launch_ms, "secondaries_per_step": n_sec,
         "flags_nonzero_fraction": float(np.mean(res["flags"] != 0)),
         "plain": plain, "batched_vs_plain": (value / plain["value"]) if plain else None, "fp64_mode": fp64,
+        "fp32_scaled_mode": scaled, "other_workloads": others,
         "phase_split": phase_split,
         "p50_ms": serving["runs"][-1]["p50_ms"] if serving else None,
         "p99_ms": serving["runs"][-1]["p99_ms"] if serving else None,

@@ -43,11 +43,18 @@ typedef enum {
 } pnuc_status;
 
 typedef enum {
-    PNUC_FP32 = 0, /* bulk transport, path, cross-section and evaporation arithmetic in
-                      FP32 (the widths scaled by the largest channel's exponential); the
-                      collision boosts, Q-values and energy/momentum bookkeeping in FP64 */
-    PNUC_FP64 = 1  /* everything in FP64, no fused multiply-add: reproduces the CPU
-                      oracle event by event up to libm rounding */
+    PNUC_FP32 = 0,        /* bulk transport, path and cross-section arithmetic, the evaporation
+                             channel parameters, emission sampler and decay in FP32; the NN
+                             collision boosts to and from the pair's CM frame, the event's
+                             energy/momentum bookkeeping (with the Q-values) and the evaporation
+                             widths with their exponentials (§2.4) in FP64 */
+    PNUC_FP64 = 1,        /* everything in FP64, no fused multiply-add: reproduces the CPU
+                             oracle event by event up to libm rounding */
+    PNUC_FP32_SCALED = 2  /* PNUC_FP32 with the evaporation widths and the channel draw in FP32:
+                             each width of an evaporation step is evaluated times e^-xm, xm the
+                             largest exponent of the step's open channels (the draw needs only
+                             the widths' ratios; unscaled they reach e^160, beyond FP32). Shares
+                             PNUC_FP32's tuning */
 } pnuc_precision;
 
 typedef enum {

@@ -37,7 +37,7 @@ enum OccKind { kOccCascade = 0, kOccEvap = 1, kOccSorted = 2 };
 
 int occupancy_kind(OccKind kind, pnuc_precision prec, int block, bool count)
 {
-    static std::atomic<int> cache[3][2][4][2];
+    static std::atomic<int> cache[3][3][4][2];
     static std::once_flag once;
     std::call_once(once, [] {
         for (auto &a : cache)
@@ -46,13 +46,14 @@ int occupancy_kind(OccKind kind, pnuc_precision prec, int block, bool count)
                     for (auto &d : c) d.store(-1);
     });
     const int bi = block == 64 ? 0 : block == 128 ? 1 : block == 256 ? 2 : 3;
-    std::atomic<int> &slot = cache[kind][prec == PNUC_FP64 ? 1 : 0][bi][count ? 1 : 0];
+    std::atomic<int> &slot = cache[kind][prec == PNUC_FP64 ? 1 : prec == PNUC_FP32_SCALED ? 2 : 0][bi][count ? 1 : 0];
     int v = slot.load();
     if (v >= 0) return v;
     if (kind == kOccCascade)
         v = prec == PNUC_FP64 ? occupancy_persistent_fp64(block) : occupancy_persistent_fp32(block, count);
     else if (kind == kOccEvap)
-        v = prec == PNUC_FP64 ? occupancy_evap_fp64(block) : occupancy_evap_fp32(block, count);
+        v = prec == PNUC_FP64 ? occupancy_evap_fp64(block)
+                              : occupancy_evap_fp32(block, count, prec == PNUC_FP32_SCALED);
     else
         v = prec == PNUC_FP64 ? occupancy_sorted_fp64(block) : occupancy_sorted_fp32(block, count);
     slot.store(v);
@@ -81,7 +82,7 @@ pnuc_status check_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method met
                         const pnuc_output *out)
 {
     if (!ctx || !batch || !out) return fail(ctx, PNUC_ERR_ARG, "null argument");
-    if (precision != PNUC_FP32 && precision != PNUC_FP64) return fail(ctx, PNUC_ERR_ARG, "bad precision %d", precision);
+    if (!valid_precision(precision)) return fail(ctx, PNUC_ERR_ARG, "bad precision %d", precision);
     if (method != PNUC_PLAIN && method != PNUC_PERSISTENT && method != PNUC_SORTED)
         return fail(ctx, PNUC_ERR_ARG, "bad method %d", method);
     if (batch->n > 0xFFFFFFFFull) return fail(ctx, PNUC_ERR_ARG, "n = %llu exceeds 2^32-1", (unsigned long long)batch->n);
@@ -140,7 +141,7 @@ cudaError_t launch_evap_for(pnuc_ctx *ctx, pnuc_precision precision, const SimPa
     if (egrid > eneed) egrid = eneed;
     if (max_blocks && egrid > max_blocks) egrid = max_blocks;
     return precision == PNUC_FP64 ? launch_evap_fp64(p, (int)egrid, eblock, s)
-                                  : launch_evap_fp32(p, (int)egrid, eblock, count, s);
+                                  : launch_evap_fp32(p, (int)egrid, eblock, count, precision == PNUC_FP32_SCALED, s);
 }
 
 pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method method, const pnuc_batch *batch,
@@ -187,7 +188,7 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
     CU(ctx, e);
     if (method == PNUC_PLAIN) {
         e = precision == PNUC_FP64 ? launch_plain_fp64(p, t.block_size, s)
-                                   : launch_plain_fp32(p, t.block_size, count, s);
+                                   : launch_plain_fp32(p, t.block_size, count, precision == PNUC_FP32_SCALED, s);
         if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
         if (ev) ctx->tev_two[ctx->tev_used / 3 - 1] = 0;
     } else if (method == PNUC_SORTED) {
@@ -399,17 +400,17 @@ pnuc_status pnuc_target_table(pnuc_ctx *ctx, int32_t target_id, pnuc_target_info
 
 pnuc_status pnuc_get_tuning(const pnuc_ctx *ctx, pnuc_precision precision, pnuc_tuning *out)
 {
-    if (!ctx || !out || (precision != PNUC_FP32 && precision != PNUC_FP64)) return PNUC_ERR_ARG;
-    *out = ctx->tuning[precision];
+    if (!ctx || !out || !valid_precision(precision)) return PNUC_ERR_ARG;
+    *out = ctx->tuning[tuning_slot(precision)];
     return PNUC_OK;
 }
 
 pnuc_status pnuc_set_tuning(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_tuning *t)
 {
-    if (!ctx || !t || (precision != PNUC_FP32 && precision != PNUC_FP64)) return fail(ctx, PNUC_ERR_ARG, "bad argument");
+    if (!ctx || !t || !valid_precision(precision)) return fail(ctx, PNUC_ERR_ARG, "bad argument");
     pnuc_status st = check_tuning(ctx, t);
     if (st != PNUC_OK) return st;
-    ctx->tuning[precision] = *t;
+    ctx->tuning[tuning_slot(precision)] = *t;
     return PNUC_OK;
 }
 
@@ -418,7 +419,8 @@ pnuc_status pnuc_simulate(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method m
 {
     pnuc_status st = check_batch(ctx, precision, method, batch, out);
     if (st != PNUC_OK) return st;
-    return launch_batch(ctx, precision, method, batch, out, (cudaStream_t)stream, ctx->tuning[precision], nullptr);
+    return launch_batch(ctx, precision, method, batch, out, (cudaStream_t)stream, ctx->tuning[tuning_slot(precision)],
+                        nullptr);
 }
 
 namespace {
@@ -500,7 +502,7 @@ pnuc_status pnuc_simulate_host(pnuc_ctx *ctx, pnuc_precision precision, pnuc_met
         CU(ctx, cudaMemcpyAsync(ctx->h_energies, energies, sizeof(double) * n, cudaMemcpyHostToDevice, s));
         CU(ctx, cudaMemcpyAsync(ctx->h_tids, target_ids, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     }
-    st = launch_batch(ctx, precision, method, &b, &o, s, ctx->tuning[precision], nullptr);
+    st = launch_batch(ctx, precision, method, &b, &o, s, ctx->tuning[tuning_slot(precision)], nullptr);
     if (st != PNUC_OK) return st;
     CU(ctx, cudaMemcpyAsync(ctx->h_count_host, ctx->h_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
     if (n > 0 && !dres)
@@ -590,7 +592,7 @@ pnuc_status pnuc_simulate_host_noalloc(pnuc_ctx *ctx, pnuc_precision precision, 
     pnuc_output o = {sec_capacity ? d_s : nullptr, sec_capacity, count, d_r, nullptr};
     pnuc_status st = check_batch(ctx, precision, method, &b, &o);
     if (st != PNUC_OK) return st;
-    st = launch_batch(ctx, precision, method, &b, &o, s, ctx->tuning[precision], head);
+    st = launch_batch(ctx, precision, method, &b, &o, s, ctx->tuning[tuning_slot(precision)], head);
     if (st != PNUC_OK) return st;
     unsigned long long cnt = 0;
     CU(ctx, cudaMemcpyAsync(&cnt, count, sizeof cnt, cudaMemcpyDeviceToHost, s));

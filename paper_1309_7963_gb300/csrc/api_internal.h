@@ -12,6 +12,10 @@
 namespace pnuc {
 constexpr int kQueueSlots = 256;  // persistent launches of one context in flight at once
 constexpr int kQueueStride = 16;  // 128-byte spacing between queue heads
+inline bool valid_precision(int p) { return p == PNUC_FP32 || p == PNUC_FP64 || p == PNUC_FP32_SCALED; }
+// The context's tuning slot of a precision: the two FP32 modes run the same cascade kernel
+// and share one tuning.
+inline int tuning_slot(int p) { return p == PNUC_FP64 ? 1 : 0; }
 }  // namespace pnuc
 
 struct pnuc_ctx {
@@ -25,7 +29,7 @@ struct pnuc_ctx {
     std::vector<std::pair<int, int>> targets;
     unsigned long long *queue = nullptr;  // [kQueueSlots * kQueueStride]
     unsigned queue_next = 0;
-    pnuc_tuning tuning[2];
+    pnuc_tuning tuning[2];  // [tuning_slot(precision)]
     // staging for pnuc_simulate_host
     double *h_energies = nullptr;
     int32_t *h_tids = nullptr;

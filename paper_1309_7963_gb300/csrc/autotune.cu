@@ -170,7 +170,7 @@ pnuc_status pnuc_autotune(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_ba
     cudaEvent_t e0, e1;
     CU(ctx, cudaEventCreate(&e0));
     CU(ctx, cudaEventCreate(&e1));
-    pnuc_tuning cur = ctx->tuning[precision];
+    pnuc_tuning cur = ctx->tuning[tuning_slot(precision)];
     cur.blocks_per_sm = 32;  // the launch clamps to the kernel's occupancy
     double cur_ms = time_tuning(ctx, precision, batch, out, cur, reps, s, e0, e1);
     for (int pass = 0; pass < 2 && cur_ms > 0; ++pass) {
@@ -190,7 +190,7 @@ pnuc_status pnuc_autotune(pnuc_ctx *ctx, pnuc_precision precision, const pnuc_ba
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (!(cur_ms > 0)) return fail(ctx, PNUC_ERR_CUDA, "autotune launch failed: %s", ctx->err);
-    ctx->tuning[precision] = cur;
+    ctx->tuning[tuning_slot(precision)] = cur;
     if (best) *best = cur;
     if (best_ms) *best_ms = cur_ms;
     return PNUC_OK;

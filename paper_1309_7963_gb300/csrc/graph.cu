@@ -21,7 +21,8 @@ pnuc_status capture(pnuc_graph *g, const pnuc_batch *b, const pnuc_output *o, cu
 {
     pnuc_ctx *ctx = g->ctx;
     CU(ctx, cudaStreamBeginCapture(g->capture, cudaStreamCaptureModeThreadLocal));
-    pnuc_status st = launch_batch(ctx, g->precision, g->method, b, o, g->capture, ctx->tuning[g->precision], g->head);
+    pnuc_status st = launch_batch(ctx, g->precision, g->method, b, o, g->capture, ctx->tuning[tuning_slot(g->precision)],
+                                    g->head);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(g->capture, &graph);
     if (st != PNUC_OK) {

@@ -1,6 +1,9 @@
-// FP32 bulk mode (compiled with --use_fast_math, which affects single precision only):
-// transport, free paths and cross sections in float; collision boosts, event bookkeeping
-// and evaporation widths stay in double.
+// FP32 bulk modes (compiled with --use_fast_math, which affects single precision only):
+// transport, free paths, cross sections, channel parameters, the emission sampler and the
+// evaporation decay in float; the NN collision boosts and the event's energy/momentum
+// bookkeeping in double. PNUC_FP32 keeps the evaporation widths (their exponentials, the
+// channel draw) in double; PNUC_FP32_SCALED evaluates them in float, scaled by the largest
+// channel's exponential (the "scaled" evaporation kernels below).
 #include "pnuc_kernels.cuh"
 
 namespace pnuc {
@@ -11,12 +14,15 @@ namespace {
 // and 72 with six and seven blocks measured the same and 4% slower). The evaporation kernel
 // fits 96 without spilling (five blocks per SM instead of four; the same time).
 __global__ void __maxnreg__(96) persistent_kernel_f32(const SimParams P) { persistent_body<float, false>(P); }
-__global__ void __maxnreg__(96) evap_kernel_f32(const SimParams P) { evap_body<float, false>(P); }
+__global__ void __maxnreg__(96) evap_kernel_f32(const SimParams P) { evap_body<float, false, false>(P); }
+__global__ void __maxnreg__(96) evap_kernel_f32s(const SimParams P) { evap_body<float, false, true>(P); }
 }  // namespace
 }  // namespace dev
 
-cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, cudaStream_t s)
+cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, bool scaled, cudaStream_t s)
 {
+    if (scaled)
+        return count ? dev::launch_plain<float, true, true>(p, block, s) : dev::launch_plain<float, false, true>(p, block, s);
     return count ? dev::launch_plain<float, true>(p, block, s) : dev::launch_plain<float, false>(p, block, s);
 }
 cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s)
@@ -24,8 +30,13 @@ cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool
     if (count) return dev::launch_persistent<float, true>(p, grid, block, s);
     return dev::launch_kernel(dev::persistent_kernel_f32, dev::smem_bytes<float>(p.n_targets, block), p, grid, block, s);
 }
-cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s)
+cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count, bool scaled, cudaStream_t s)
 {
+    if (scaled) {
+        if (count) return dev::launch_evap<float, true, true>(p, grid, block, s);
+        return dev::launch_kernel(dev::evap_kernel_f32s, dev::evap_smem_bytes<float, true>(p.n_targets, block), p,
+                                  grid, block, s);
+    }
     if (count) return dev::launch_evap<float, true>(p, grid, block, s);
     return dev::launch_kernel(dev::evap_kernel_f32, dev::evap_smem_bytes<float>(p.n_targets, block), p, grid, block, s);
 }
@@ -39,8 +50,12 @@ int occupancy_sorted_fp32(int block, bool count)
     return count ? dev::occupancy_sorted<float, true>(block) : dev::occupancy_sorted<float, false>(block);
 }
 size_t sorted_stack_bytes_fp32() { return sizeof(dev::Particle<float>) * kStackCap; }
-int occupancy_evap_fp32(int block, bool count)
+int occupancy_evap_fp32(int block, bool count, bool scaled)
 {
+    if (scaled) {
+        if (count) return dev::occupancy_evap<float, true, true>(block);
+        return dev::occupancy_of(dev::evap_kernel_f32s, dev::evap_smem_bytes<float, true>(kMaxTargets, block), block);
+    }
     if (count) return dev::occupancy_evap<float, true>(block);
     return dev::occupancy_of(dev::evap_kernel_f32, dev::evap_smem_bytes<float>(kMaxTargets, block), block);
 }

@@ -5,9 +5,11 @@
 // kernel (warps refilling finished lanes) run the same steps.
 //
 // Precision: R = double reproduces the CPU oracle event by event (compiled without FMA
-// contraction); R = float keeps transport, paths, cross sections and the (scaled)
-// evaporation widths in FP32 while the Lorentz boosts, the Q-values and the event's
-// energy/momentum bookkeeping stay FP64.
+// contraction); R = float keeps transport, paths, cross sections, the channel parameters and
+// the emission sampler in FP32 while the NN collision boosts, the Q-values, the event's
+// energy/momentum bookkeeping and the evaporation widths with their exponentials stay FP64.
+// The evaporation templates' kScaled variant (FP32 only) evaluates the widths in FP32, each
+// scaled by the largest channel's exponential, and draws the channel in FP32.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -987,37 +989,80 @@ __device__ __forceinline__ void width_FG(double x, double &F, double &G)
     G = g;
 }
 
-// The type the six widths of a step are held and drawn in: FP64 in the FP64 mode (the
-// oracle's arithmetic), FP32 in the FP32 mode, where they are scaled (below).
-template <typename R>
+// The type the six widths of a step are held and drawn in: FP64 (the FP64 mode, and the
+// FP32 mode's widths with FP64 exponentials), or FP32 for the scaled FP32 widths (below).
+template <typename R, bool kScaled>
 struct WidthOf {
     using T = double;
 };
 template <>
-struct WidthOf<float> {
+struct WidthOf<float, true> {
     using T = float;
 };
-template <typename R>
-using width_t = typename WidthOf<R>::T;
+template <typename R, bool kScaled>
+using width_t = typename WidthOf<R, kScaled>::T;
 
-// The width of one open channel. The channel draw uses only the six widths' ratios, so the
-// FP32 mode returns the width times e^-xm, xm the largest x of the parent's open channels:
-// the exponential becomes e^(x - xm) <= 1 and the whole width is FP32 arithmetic (the
-// unscaled width reaches e^160, beyond FP32's range). The FP64 mode ignores xm.
-template <typename R>
-__device__ width_t<R> channel_width(const ChanP<R> &c, R xm);
-template <>
-__device__ double channel_width<double>(const ChanP<double> &c, double)
+// a draw or parameter of precision R as a width-type value (float -> double on the integer
+// pipes, fpconv.h)
+template <typename W, typename R>
+__device__ __forceinline__ W as_width(R x)
 {
-    if (!c.open) return 0.0;
-    double F, G;
-    width_FG(c.x, F, G);
-    const double a = c.a;
-    const double I = F / (4.0 * a * a) + c.b * G / (2.0 * a);
-    return c.w0 * I;
+    if constexpr (sizeof(W) == sizeof(R)) return x;
+    else return to_d<R>(x);
 }
-template <>
-__device__ float channel_width<float>(const ChanP<float> &c, float xm)
+
+// FP32 mode, widths in FP64: the channel parameters (x, a, b, w0) come in FP32; the
+// exponential e^x and the closed forms F, G are assembled in FP64 (e^x reaches e^160,
+// beyond FP32's range); the series below x = 1 needs no exponential and runs in FP32.
+__device__ __forceinline__ double channel_width_f32_d(const ChanP<float> &c)
+{
+    const float x = c.x;
+    double F, G;
+    if (x >= 1.f) {
+        const double ex = exp(f2d(x));
+        F = ex * f2d(x * x - 3.f * x + 3.f) + f2d(0.5f * x * x) - 3.0;
+        G = ex * f2d(x - 1.f) + 1.0;
+    } else {
+        float term = x, f = 0.f, g = 0.f;  // term = x^n / n!
+#pragma unroll 1
+        for (int n = 2; n <= 20; ++n) {
+            term *= x / float(n);
+            g += float(n - 1) * term;
+            if (n >= 4) f += float((n - 1) * (n - 3)) * term;
+        }
+        F = f2d(f);
+        G = f2d(g);
+    }
+    const float ia = 1.f / c.a;
+    return f2d(c.w0) * (F * f2d(0.25f * ia * ia) + G * f2d(0.5f * c.b * ia));
+}
+
+// The width of one open channel, FP64 in the FP64 mode and in the FP32 mode (the scale
+// reference xm is ignored). The channel draw uses only the six widths' ratios, so the scaled
+// FP32 variant (kScaled) returns the width times e^-xm, xm the largest x of the parent's open
+// channels: the exponential becomes e^(x - xm) <= 1 and the whole width is FP32 arithmetic
+// (the unscaled width reaches e^160, beyond FP32's range).
+__device__ float channel_width_scaled(const ChanP<float> &c, float xm);
+
+template <typename R, bool kScaled>
+__device__ width_t<R, kScaled> channel_width(const ChanP<R> &c, R xm)
+{
+    if constexpr (sizeof(R) == 8) {
+        if (!c.open) return 0.0;
+        double F, G;
+        width_FG(c.x, F, G);
+        const double a = c.a;
+        const double I = F / (4.0 * a * a) + c.b * G / (2.0 * a);
+        return c.w0 * I;
+    } else if constexpr (kScaled) {
+        return channel_width_scaled(c, xm);
+    } else {
+        if (!c.open) return 0.0;
+        return channel_width_f32_d(c);
+    }
+}
+
+__device__ float channel_width_scaled(const ChanP<float> &c, float xm)
 {
     if (!c.open) return 0.f;
     // s = e^-xm is 0 for xm above about 87 (the FP32 kernels flush denormals); the terms it
@@ -1147,10 +1192,11 @@ __device__ __forceinline__ double daughter_excitation<float>(float x, float t, f
 // The second half of an evaporation step (§2.4), given the six channel widths G of the
 // parent (Z, A, E* in L): the channel draw, the emission energy, and the two-body decay
 // isotropic in the parent's rest frame, boosted to the lab.
-template <typename R, bool kCount>
-__device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const width_t<R> *G, Counters<kCount> &C)
+template <typename R, bool kScaled, bool kCount>
+__device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const width_t<R, kScaled> *G,
+                          Counters<kCount> &C)
 {
-    using W = width_t<R>;
+    using W = width_t<R, kScaled>;
     const int Z = L.Z, A = L.A;
     const double Estar = L.Estar;
     W S = W(0);
@@ -1161,7 +1207,7 @@ __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const 
         return;
     }
     C.add(PNUC_C_EVAP_STEPS);
-    W us = static_cast<W>(L.rng.next()) * S, cum = W(0);
+    W us = as_width<W>(L.rng.next()) * S, cum = W(0);
     int ch = -1;
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) {
@@ -1204,7 +1250,7 @@ __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const 
 
 // One evaporation step of one lane (the plain kernel): widths of the six channels, then
 // evap_emit().
-template <typename R, bool kCount>
+template <typename R, bool kScaled, bool kCount>
 __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
 {
     if (L.n_evap >= P.max_evap_steps) {
@@ -1214,17 +1260,17 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     }
     C.add(PNUC_C_EVAP_PASSES);
     const double Mparent = __ldg(&P.mass[L.Z * kMassA + L.A]);
-    width_t<R> G[6];
+    width_t<R, kScaled> G[6];
     ChanP<R> chans[6];
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) {
         channel_params<R>(P, L.Z, L.A, Mparent, L.Estar, j, chans[j]);
         if (chans[j].open) C.add(chans[j].x >= R(1) ? PNUC_C_EVAP_EXPS : PNUC_C_EVAP_SERIES);
     }
-    const R xm = widths_xm<R>(chans);
+    const R xm = kScaled ? widths_xm<R>(chans) : R(0);
 #pragma unroll 1
-    for (int j = 0; j < 6; ++j) G[j] = channel_width<R>(chans[j], xm);
-    evap_emit<R, kCount>(P, L, Mparent, G, C);
+    for (int j = 0; j < 6; ++j) G[j] = channel_width<R, kScaled>(chans[j], xm);
+    evap_emit<R, kScaled, kCount>(P, L, Mparent, G, C);
 }
 
 // ------------------------------------------------------------------ warp-wide widths
@@ -1237,8 +1283,8 @@ struct WidthJob {
 };
 constexpr int kWidthSlots = 6 * 32;  // per warp: six channels of every lane
 
-template <typename R>
-__device__ __forceinline__ width_t<R> job_width(const WidthJob<R> &jb, R xm)
+template <typename R, bool kScaled>
+__device__ __forceinline__ width_t<R, kScaled> job_width(const WidthJob<R> &jb, R xm)
 {
     ChanP<R> c;
     c.open = true;
@@ -1246,7 +1292,7 @@ __device__ __forceinline__ width_t<R> job_width(const WidthJob<R> &jb, R xm)
     c.a = jb.a;
     c.b = jb.b;
     c.w0 = jb.w0;
-    return channel_width<R>(c, xm);
+    return channel_width<R, kScaled>(c, xm);
 }
 
 // One evaporation step of every lane of the warp with `active` set (the evaporation kernel).
@@ -1259,9 +1305,9 @@ __device__ __forceinline__ width_t<R> job_width(const WidthJob<R> &jb, R xm)
 // lane), with the lane's scale reference in xms; no per-lane channel records are kept, so
 // nothing of the step lives in local memory. Called by all 32 lanes of the warp; jobs and gw
 // are the warp's kWidthSlots entries, xms its 32.
-template <typename R, bool kCount>
-__device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, WidthJob<R> *jobs, width_t<R> *gw,
-                               R *xms, Counters<kCount> &C)
+template <typename R, bool kScaled, bool kCount>
+__device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, WidthJob<R> *jobs,
+                               width_t<R, kScaled> *gw, R *xms, Counters<kCount> &C)
 {
     if (active && L.n_evap >= P.max_evap_steps) {
         L.flags |= PNUC_FLAG_EVAP_STEP_CAP;
@@ -1270,7 +1316,7 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
     }
     const unsigned FULL = 0xffffffffu, lane = threadIdx.x & 31, below = (1u << lane) - 1u;
     const double Mparent = active ? __ldg(&P.mass[L.Z * kMassA + L.A]) : 0.0;
-    width_t<R> *G = gw + 6 * lane;
+    width_t<R, kScaled> *G = gw + 6 * lane;
     R xm = R(0);
     int nexp = 0, nser = 0;
 #pragma unroll 1
@@ -1290,7 +1336,7 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
             jobs[slot] = WidthJob<R>{c.x, c.a, c.b, c.w0, (int)(6 * lane) + j};
             if (c.x > xm) xm = c.x;
         } else {
-            G[j] = width_t<R>(0);
+            G[j] = width_t<R, kScaled>(0);
         }
         nexp += __popc(me);
         nser += __popc(ms);
@@ -1307,19 +1353,19 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
     __syncwarp();
     for (int k = lane; k < nexp; k += 32) {
         const WidthJob<R> jb = jobs[k];
-        gw[jb.tag] = job_width<R>(jb, xms[jb.tag / 6]);
+        gw[jb.tag] = job_width<R, kScaled>(jb, xms[jb.tag / 6]);
     }
     for (int k = kWidthSlots - 1 - (int)lane; k >= kWidthSlots - nser; k -= 32) {
         const WidthJob<R> jb = jobs[k];
-        gw[jb.tag] = job_width<R>(jb, xms[jb.tag / 6]);
+        gw[jb.tag] = job_width<R, kScaled>(jb, xms[jb.tag / 6]);
     }
     __syncwarp();
-    if (active) evap_emit<R, kCount>(P, L, Mparent, G, C);
+    if (active) evap_emit<R, kScaled, kCount>(P, L, Mparent, G, C);
     __syncwarp();  // the lists are reused by the next step
 }
 
 // Advances lane L by one step of its current phase (no batching: the plain kernel).
-template <typename R, bool kCount>
+template <typename R, bool kScaled, bool kCount>
 __device__ __forceinline__ void step(const SimParams &P, const ShellTable<R> *sh, const TargetScalars *tabs, Lane<R> &L,
                                      Particle<R> *stack, Counters<kCount> &C)
 {
@@ -1330,7 +1376,7 @@ __device__ __forceinline__ void step(const SimParams &P, const ShellTable<R> *sh
     } else if (L.phase == kEntry) {
         step_entry<R, kCount>(P, sh[L.tgt], tabs[L.tgt].R, L, C);
     } else if (L.phase == kEvap) {
-        step_evap<R, kCount>(P, L, C);
+        step_evap<R, kScaled, kCount>(P, L, C);
     }
 }
 

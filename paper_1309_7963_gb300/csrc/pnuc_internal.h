@@ -76,14 +76,16 @@ struct SimParams {
 cudaError_t launch_plain_fp64(const SimParams &p, int block, cudaStream_t s);
 cudaError_t launch_persistent_fp64(const SimParams &p, int grid, int block, cudaStream_t s);
 cudaError_t launch_evap_fp64(const SimParams &p, int grid, int block, cudaStream_t s);
-cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s);
-cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, cudaStream_t s);
+// FP32 launchers of kernels that evaporate take `scaled`: the evaporation widths in FP32,
+// scaled by the largest channel's exponential (PNUC_FP32_SCALED), instead of FP64 (PNUC_FP32).
+cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count, bool scaled, cudaStream_t s);
+cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, bool scaled, cudaStream_t s);
 cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s);
 // Resident blocks per SM of the persistent kernels at a block size.
 int occupancy_persistent_fp64(int block);
 int occupancy_persistent_fp32(int block, bool count);
 int occupancy_evap_fp64(int block);
-int occupancy_evap_fp32(int block, bool count);
+int occupancy_evap_fp32(int block, bool count, bool scaled);
 // Sorted method (cascade kernel regrouping slots by action): launchers, resident blocks per
 // SM, and the bytes of one slot's particle stack (the stacks live in a context buffer).
 cudaError_t launch_sorted_fp64(const SimParams &p, void *stacks, int grid, int block, cudaStream_t s);

@@ -45,11 +45,12 @@ __host__ __device__ constexpr size_t smem_bytes(int n_targets, int block)
 }
 
 // the evaporation kernel adds each warp's width-job list after the rings
-template <typename R>
+template <typename R, bool kScaled = false>
 __host__ __device__ constexpr size_t evap_smem_bytes(int n_targets, int block)
 {
     return smem_bytes<R>(n_targets, block) +
-           (size_t)(block / 32) * (kWidthSlots * (sizeof(WidthJob<R>) + sizeof(width_t<R>)) + 32 * sizeof(R));
+           (size_t)(block / 32) *
+               (kWidthSlots * (sizeof(WidthJob<R>) + sizeof(width_t<R, kScaled>)) + 32 * sizeof(R));
 }
 
 template <typename R>
@@ -77,7 +78,7 @@ __device__ __forceinline__ void finish_event(const SimParams &P, Lane<R> &L, Cou
     if (!L.pend && !(L.flags & (PNUC_FLAG_BAD_INPUT | PNUC_FLAG_ATTEMPT_CAP))) C.add(PNUC_C_SETTLED);
 }
 
-template <typename R, bool kCount>
+template <typename R, bool kCount, bool kScaled = false>
 __global__ void __launch_bounds__(512) plain_kernel(const SimParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(512) plain_kernel(const SimParams P)
         begin_event<R>(P, ts, L, (uint32_t)i);
         while (L.phase != kFinish) {
             L.rng.ensure(8);
-            step<R, kCount>(P, sh, ts, L, stack, C);
+            step<R, kScaled, kCount>(P, sh, ts, L, stack, C);
         }
         finish_event<R, kCount>(P, L, C);
     }
@@ -244,9 +245,9 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
 }
 
 // Persistent evaporation kernel (after the cascade kernel on the same stream): every lane
-// evaporates, so the width exponentials and the FP64 decays run with full warps. Lanes take
+// evaporates, so the width exponentials and the decays run with full warps. Lanes take
 // event indices from the evaporation queue and skip events with nothing pending.
-template <typename R, bool kCount>
+template <typename R, bool kCount, bool kScaled = false>
 __device__ __forceinline__ void evap_body(const SimParams &P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -268,8 +269,8 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     WidthJob<R> *jobs0 = reinterpret_cast<WidthJob<R> *>(smem + smem_bytes<R>(P.n_targets, blockDim.x));
     WidthJob<R> *jobs = jobs0 + warp * kWidthSlots;
-    width_t<R> *gw0 = reinterpret_cast<width_t<R> *>(jobs0 + nwarps * kWidthSlots);
-    width_t<R> *gw = gw0 + warp * kWidthSlots;
+    width_t<R, kScaled> *gw0 = reinterpret_cast<width_t<R, kScaled> *>(jobs0 + nwarps * kWidthSlots);
+    width_t<R, kScaled> *gw = gw0 + warp * kWidthSlots;
     R *xms = reinterpret_cast<R *>(gw0 + nwarps * kWidthSlots) + warp * 32;
     while (true) {
         const long long t_top = kCount ? clock64() : 0;
@@ -297,7 +298,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
         const long long t1 = kCount ? clock64() : 0;
         const bool stepping = L.phase == kEvap;
         if (stepping) L.rng.ensure(8);
-        step_evap_warp<R, kCount>(P, L, stepping, jobs, gw, xms, C);
+        step_evap_warp<R, kScaled, kCount>(P, L, stepping, jobs, gw, xms, C);
         if (kCount) {
             __syncwarp();
             if (lane == 0) {
@@ -453,32 +454,32 @@ __global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
     persistent_body<R, kCount>(P);
 }
 
-template <typename R, bool kCount>
+template <typename R, bool kCount, bool kScaled = false>
 __global__ void __launch_bounds__(512) evap_kernel(const SimParams P)
 {
-    evap_body<R, kCount>(P);
+    evap_body<R, kCount, kScaled>(P);
 }
 
-template <typename R, bool kCount>
+template <typename R, bool kCount, bool kScaled = false>
 cudaError_t launch_evap(const SimParams &p, int grid, int block, cudaStream_t s)
 {
     if (p.n == 0) return cudaSuccess;
-    size_t smem = evap_smem_bytes<R>(p.n_targets, block);
-    cudaError_t e = allow_smem(evap_kernel<R, kCount>, smem);
+    size_t smem = evap_smem_bytes<R, kScaled>(p.n_targets, block);
+    cudaError_t e = allow_smem(evap_kernel<R, kCount, kScaled>, smem);
     if (e != cudaSuccess) return e;
-    evap_kernel<R, kCount><<<grid, block, smem, s>>>(p);
+    evap_kernel<R, kCount, kScaled><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <typename R, bool kCount>
+template <typename R, bool kCount, bool kScaled = false>
 cudaError_t launch_plain(const SimParams &p, int block, cudaStream_t s)
 {
     if (p.n == 0) return cudaSuccess;
     size_t smem = smem_bytes<R>(p.n_targets, block);
-    cudaError_t e = allow_smem(plain_kernel<R, kCount>, smem);
+    cudaError_t e = allow_smem(plain_kernel<R, kCount, kScaled>, smem);
     if (e != cudaSuccess) return e;
     unsigned long long grid = (p.n + block - 1) / block;
-    plain_kernel<R, kCount><<<(unsigned)grid, block, smem, s>>>(p);
+    plain_kernel<R, kCount, kScaled><<<(unsigned)grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -529,10 +530,10 @@ int occupancy_sorted(int block)
     return occupancy_of(sorted_kernel<R, kCount>, sorted_smem_bytes<R>(kMaxTargets, block), block);
 }
 
-template <typename R, bool kCount>
+template <typename R, bool kCount, bool kScaled = false>
 int occupancy_evap(int block)
 {
-    return occupancy_of(evap_kernel<R, kCount>, evap_smem_bytes<R>(kMaxTargets, block), block);
+    return occupancy_of(evap_kernel<R, kCount, kScaled>, evap_smem_bytes<R, kScaled>(kMaxTargets, block), block);
 }
 
 template <typename R, bool kCount>

@@ -347,7 +347,7 @@ bool admit(pnuc_server *S)
                      (pnuc_residual *)(hd + L.host_r), nullptr};
     Placement seg;
     {
-        const uint64_t per_block = (uint64_t)S->ctx->tuning[S->cfg.precision].block_size * S->cfg.lane_events;
+        const uint64_t per_block = (uint64_t)S->ctx->tuning[tuning_slot(S->cfg.precision)].block_size * S->cfg.lane_events;
         seg.max_blocks = (unsigned)std::min<uint64_t>((n + per_block - 1) / per_block, 1u << 30);
     }
     if (k > 1) {
@@ -357,7 +357,7 @@ bool admit(pnuc_server *S)
     }
     if (st == PNUC_OK)
         st = launch_batch(S->ctx, (pnuc_precision)S->cfg.precision, PNUC_PERSISTENT, &b, &o, s,
-                          S->ctx->tuning[S->cfg.precision], nullptr, seg);
+                          S->ctx->tuning[tuning_slot(S->cfg.precision)], nullptr, seg);
     if (st == PNUC_OK && k > 1 && cap) {
         const int grid = std::max(1, std::min<int>((int)((cap + 255) / 256), S->ctx->sm_count * 4));
         partition_kernel<<<grid, 256, 0, s>>>(
@@ -541,7 +541,7 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg_in, 
     pnuc_server_config cfg;
     pnuc_server_default_config(&cfg);
     if (cfg_in) cfg = *cfg_in;
-    if ((cfg.precision != PNUC_FP32 && cfg.precision != PNUC_FP64) || cfg.streams < 1 || cfg.streams > 64 ||
+    if (!valid_precision(cfg.precision) || cfg.streams < 1 || cfg.streams > 64 ||
         cfg.arena_bytes < (1u << 20) || cfg.sec_per_event < 1 || cfg.sec_per_event > 256 || cfg.max_pending < 1 ||
         cfg.max_request_events < 1 || cfg.max_merge < 1 || cfg.max_merge > (uint32_t)kMaxSeg || cfg.merge_events < 1 ||
         cfg.merge_events > kMaxGroupEvents || cfg.lane_events < 1 || cfg.lane_events > 1024)

@@ -31,7 +31,9 @@ COUNTER_NAMES = ("steps", "candidates", "kinematics", "pauli_blocked", "collisio
                  "cycles_refill")
 FLAGS = dict(bad_input=1, attempt_cap=2, step_cap=4, stack_overflow=8, bad_residual=16, no_excitation=32,
              evap_trial_cap=64, evap_step_cap=128, output_overflow=256)
-PRECISION = {"fp32": 0, "fp64": 1}
+# "fp32": FP32 bulk with FP64 evaporation widths; "fp32_scaled": the widths in FP32 as well, scaled by the
+# largest channel's exponential; "fp64": the deterministic mode (per-event oracle parity)
+PRECISION = {"fp32": 0, "fp64": 1, "fp32_scaled": 2}
 METHOD = {"plain": 0, "persistent": 1, "sorted": 2}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of range", 3: "capacity exceeded", 4: "CUDA error",
           5: "timeout", 6: "invalid state"}

@@ -1,4 +1,4 @@
-"""FP32 mode stays finite. Over the bench workload and a mixed-target batch (3e6 events in
+"""The FP32 modes stay finite. Over the bench workload and a mixed-target batch (3e6 events in
 all) every secondary has a finite, non-negative kinetic energy and a unit direction, and every
 residual a finite E* after the cascade and at the end. The case this guards: the emission
 energy of an evaporation step (§2.4) is E* - Q less the daughter's excitation U_d, and for a
@@ -12,15 +12,16 @@ from paper_1309_7963_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp32_scaled"])
 @pytest.mark.parametrize("workload", ["oxygen_calcium", "mixed"])
-def test_fp32_outputs_finite(ctx, workload):
+def test_fp32_outputs_finite(ctx, workload, precision):
     import torch
     w = inputs.oxygen_calcium(500_000, seed=5) if workload == "oxygen_calcium" else inputs.mixed(2_000_000, seed=6)
     n = w.n
     tids = np.array([ctx.create_target(*za) for za in w.targets], np.int32)
     e = torch.tensor(w.energies, device="cuda")
     t = torch.tensor(tids[w.tidx], device="cuda")
-    r = ctx.simulate(e, t, seed=w.seed, first_event_id=w.first_event_id, precision="fp32", method="persistent")
+    r = ctx.simulate(e, t, seed=w.seed, first_event_id=w.first_event_id, precision=precision, method="persistent")
     sec, res = r.secondaries_np(), r.residuals_np()
     assert len(sec) > 3 * n
     u = np.stack([sec["ux"], sec["uy"], sec["uz"]], 1).astype(np.float64)

@@ -1,4 +1,6 @@
-"""FP32 mode against the FP64 oracle, observable by observable, on the same events.
+"""FP32 modes against the FP64 oracle, observable by observable, on the same events: the FP32
+mode (FP64 evaporation widths) and the scaled FP32 mode (FP32 widths scaled by the largest
+channel's exponential).
 
 For each workload: the fraction of events whose integer outcomes are identical, the mean
 multiplicity of every species (cascade and evaporation) with the difference in units of its
@@ -31,24 +33,25 @@ WORKLOADS = [
 ]
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp32_scaled"])
 @pytest.mark.parametrize("name,make", WORKLOADS, ids=[w[0] for w in WORKLOADS])
-def test_fp32_observables_against_fp64_oracle(ctx, name, make):
+def test_fp32_observables_against_fp64_oracle(ctx, name, make, precision):
     import torch
     w = make()
     tids = np.array([ctx.create_target(*za) for za in w.targets], np.int32)
     r = ctx.simulate(torch.tensor(w.energies, device="cuda"), torch.tensor(tids[w.tidx], device="cuda"), seed=w.seed,
-                     first_event_id=w.first_event_id, precision="fp32", method="persistent")
+                     first_event_id=w.first_event_id, precision=precision, method="persistent")
     torch.cuda.synchronize()
     gres, gsec = r.residuals_np(), r.secondaries_np()
     orc = oracle.simulate_parallel(w.targets, w.energies, w.tidx, seed=w.seed, first_event_id=w.first_event_id)
     ores, osec = orc["residuals"], orc["secondaries"]
     c = compare(gres, gsec, orc, w.n, rel_tol=1e-4)
     row = observable_table(gres, gsec, ores, osec, w.n)
-    row.update(workload=name, identical_integers=c["frac_same"], **{"identical_within_1e-4": c["frac_match"]})
+    row.update(workload=name, precision=precision, identical_integers=c["frac_same"], **{"identical_within_1e-4": c["frac_match"]})
     row["mean_A_final"] = {"fp32": float(gres["A_final"].mean()), "oracle": float(ores["Af"].mean())}
     assert_observables(row, name)
     assert c["frac_same"] >= 0.90, c["frac_same"]
-    record(name, row)
+    record(f"{name} [{precision}]", row)
 
 
 def record(name, row):

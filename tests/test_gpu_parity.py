@@ -56,26 +56,29 @@ def test_fp64_per_event_parity_o16_200MeV(ctx, method):
     assert c["max_dir_err"] < 2e-7
 
 
-def test_fp64_per_event_parity_mixed_targets_and_energies(ctx):
+@pytest.mark.parametrize("method", ["persistent", "sorted"])
+def test_fp64_per_event_parity_mixed_targets_and_energies(ctx, method):
+    # the sorted method (phase-regrouped cascade) is held to the oracle directly as well
     w = inputs.mixed(6000, seed=3)
-    r = run_gpu(ctx, w, "fp64", "persistent")
-    c = compare(r.residuals_np(), r.secondaries_np(), run_oracle(w), w.n)
-    assert c["frac_match"] >= 0.999, c["frac_match"]
-    assert c["max_rel_energy_same"] < 1e-6
-
-
-@pytest.mark.parametrize("za,n", [(inputs.TI48, 6000), (inputs.FE56, 6000), (inputs.PB208, 3000)])
-def test_fp64_per_event_parity_heavy(ctx, za, n):
-    # samples of thousands of events: the bar is 99.9%, and one event in 1500 is already 0.07%
-    w = inputs.heavy(za, n, seed=7)
-    r = run_gpu(ctx, w, "fp64", "persistent")
+    r = run_gpu(ctx, w, "fp64", method)
     c = compare(r.residuals_np(), r.secondaries_np(), run_oracle(w), w.n)
     assert c["frac_match"] >= 0.999, c["frac_match"]
     assert c["max_rel_energy_same"] < 1e-6
 
 
 @pytest.mark.parametrize("method", ["persistent", "sorted"])
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("za,n", [(inputs.TI48, 6000), (inputs.FE56, 6000), (inputs.PB208, 3000)])
+def test_fp64_per_event_parity_heavy(ctx, za, n, method):
+    # samples of thousands of events: the bar is 99.9%, and one event in 1500 is already 0.07%
+    w = inputs.heavy(za, n, seed=7)
+    r = run_gpu(ctx, w, "fp64", method)
+    c = compare(r.residuals_np(), r.secondaries_np(), run_oracle(w), w.n)
+    assert c["frac_match"] >= 0.999, c["frac_match"]
+    assert c["max_rel_energy_same"] < 1e-6
+
+
+@pytest.mark.parametrize("method", ["persistent", "sorted"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_scaled"])
 def test_batched_methods_equal_plain_bitwise(ctx, precision, method):
     w = inputs.mixed(20_000, seed=11)
     a = run_gpu(ctx, w, precision, "plain")
