@@ -13,7 +13,10 @@
  *
  * Where the paper is silent the reading taken is stated beside the code. Parity of
  * each function is pinned in tests/test_oracle_*.py against library routines,
- * closed forms, measured NN cross sections and conservation laws.
+ * closed forms, measured NN cross sections and angular distributions, and conservation
+ * laws. One piece has no such pin: orc_backward_a above p_lab = 0.8 GeV/c (parity
+ * unpinned: no measured np backward-to-forward peak ratio is at hand; only its continuity
+ * at 0.8 GeV/c and its decrease with momentum are tested).
  */
 #include <math.h>
 #include <stdint.h>
@@ -279,7 +282,7 @@ double orc_slope(int like, double p)
     return 4.552;
 }
 
-/* weight of the backward (u-channel) term for unlike pairs */
+/* weight of the backward (u-channel) term for unlike pairs; above 0.8 GeV/c parity unpinned */
 double orc_backward_a(double p)
 {
     if (p <= 0.8) return 1.0;
@@ -410,12 +413,9 @@ double orc_boundary_distance(const orc_target *t, int shell, const double r[3], 
 
 /* Potential step at a shell boundary (section 2.3, after Chen et al.): kinetic energy
  * changes by dT with the tangential momentum kept. Returns 1 if the particle refracts
- * (p updated), 0 if it reflects (normal component reversed). n is the unit normal. */
-/* Reading M11: after a crossing the momentum's component along n points the way the
- * particle now goes, back (reflection) or on (refraction), with at least GRAZE_FLOOR of |p|
- * (1 mrad from the tangent plane); a near-tangent reflection otherwise bounces along chords
- * of ~2R theta, one step each. dir: +1 for a crossing outward (along n), -1 inward. */
-#define GRAZE_FLOOR 1e-3
+ * (p updated), 0 if it reflects (normal component reversed). n is the unit normal.
+ * Reading M11: the refracted normal component takes the sign of the crossing, dir = +1 for
+ * a crossing outward (along n), -1 inward. */
 int orc_refract(const double n[3], double p[3], double m, double dT, int dir)
 {
     double pp = dot3(p, p);
@@ -423,12 +423,10 @@ int orc_refract(const double n[3], double p[3], double m, double dT, int dir)
     double pn = dot3(p, n);
     double q2 = pn * pn + (Tn - T) * (Tn + T + 2.0 * m);
     if (Tn <= 0.0 || q2 <= 0.0) {
-        double to = pn * pn < GRAZE_FLOOR * GRAZE_FLOOR * pp ? -dir * (GRAZE_FLOOR * sqrt(pp)) : -pn;
-        for (int k = 0; k < 3; k++) p[k] += (to - pn) * n[k];
+        for (int k = 0; k < 3; k++) p[k] -= 2.0 * pn * n[k];
         return 0;
     }
-    double p2n = pp - pn * pn + q2; /* |p|^2 after the crossing */
-    double pnn = q2 < GRAZE_FLOOR * GRAZE_FLOOR * p2n ? dir * (GRAZE_FLOOR * sqrt(p2n)) : dir * sqrt(q2);
+    double pnn = dir * sqrt(q2);
     for (int k = 0; k < 3; k++) p[k] += (pnn - pn) * n[k];
     return 1;
 }

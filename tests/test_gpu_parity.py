@@ -212,8 +212,9 @@ def test_full_size_sampled_parity(ctx, precision, need):
 def test_grazing_reflection_does_not_loop_to_the_step_cap(ctx):
     """A p-208Pb event (id 523678 of the 1e6-event heavy batch, seed 3, 140.04 MeV) whose FP32
     history had reached a grazing reflection that rounding turned into zero-length chords,
-    repeated until the 1e5-step cap; with the 1-mrad floor on the normal momentum after a
-    crossing (reading M11) it ends normally in both modes."""
+    repeated until the 1e5-step cap; with the FP32 mode's 1-mrad floor on the normal momentum
+    after a crossing (reading M11) it ends normally, and in the FP64 mode (no floor, as the
+    model) it never looped."""
     import torch
     w = inputs.heavy(inputs.PB208, 1_000_000, seed=3)
     i = 523678

@@ -160,9 +160,9 @@ def test_neutron_entry_and_residual_charge_from_trace():
 
 
 def test_heavy_target_events_never_reach_the_step_cap():
-    """Reading M11's floor on the normal momentum after a crossing: no event of a p-208Pb
-    sample (the heavy target with the most surface reflections) runs to the 1e5-step cap,
-    and the longest stays within a few thousand steps."""
+    """Specular reflections at the shell boundaries (reading M11, no floor): no event of a
+    p-208Pb sample (the heavy target with the most surface reflections) runs to the 1e5-step
+    cap, and the longest stays within a few thousand steps."""
     w = inputs.heavy(inputs.PB208, 3000, seed=3)
     r = oracle.simulate(w.targets, w.energies, w.tidx, seed=w.seed)
     assert (r["residuals"]["flags"] & 4).sum() == 0
