@@ -1,4 +1,4 @@
-"""Reading M25 (the FP32 mode's evaporation arithmetic), checked on the CPU against the
+"""Reading M25 (the scaled FP32 evaporation arithmetic, PNUC_FP32_SCALED), checked on the CPU against the
 oracle's FP64 widths (§2.4: Weisskopf–Ewing widths with closed-form integrals, channel drawn
 with probability Γ_j / ΣΓ). The FP32 mode evaluates each width times e^-xm, xm the largest x
 of the parent's open channels. An FP32 emulation of that formula (numpy float32) must give
@@ -35,33 +35,51 @@ def oracle_channels(Z, A, Estar):
     return out
 
 
-def scaled_widths_f32(chans):
-    """The FP32 mode's widths times e^-xm, in float32 arithmetic (reading M25), with the
-    exponentials' denormal results flushed to 0 as the fast-math kernels do."""
+ULP = 2.0 ** -23  # float32 relative spacing at most
+
+
+def exp_err(arg):
+    """Relative error bound of the fast-math single-precision exponential at argument arg:
+    2 + floor(|1.173 arg|) ulp (the CUDA Programming Guide's table of intrinsic functions)."""
+    return (2 + np.floor(abs(1.173 * float(arg)))) * ULP
+
+
+def scaled_widths_f32(chans, sign=None):
+    """The PNUC_FP32_SCALED widths times e^-xm, in float32 arithmetic (reading M25), with the
+    exponentials' denormal results flushed to 0 as the fast-math kernels do. With sign (a
+    function giving +1 or -1 per approximate operation), every exponential, reciprocal and
+    division is moved by its published error bound in that direction: the fast-math kernels
+    compute them approximately (expf, 1/a and x/n), the products and sums exactly rounded."""
+    if sign is None:
+        def bump(v, rel):
+            return v
+    else:
+        def bump(v, rel):
+            return f(np.float64(v) * (1.0 + sign() * rel))
     xm = f(0)
     for c in chans:
         if c is not None and f(c["x"]) > xm:
             xm = f(c["x"])
     with np.errstate(under="ignore"):
-        s = ftz(np.exp(-xm, dtype=np.float32))
+        s = ftz(bump(np.exp(-xm, dtype=np.float32), exp_err(xm)))
         w = np.zeros(6, np.float32)
         for j, c in enumerate(chans):
             if c is None:
                 continue
             x, a, b, w0 = f(c["x"]), f(c["a"]), f(c["b"]), f(c["w0"])
             if x >= f(1):
-                ex = ftz(np.exp(x - xm, dtype=np.float32))
+                ex = ftz(bump(np.exp(x - xm, dtype=np.float32), exp_err(x - xm)))
                 F = ex * (x * x - f(3) * x + f(3)) + (f(0.5) * x * x - f(3)) * s
                 G = ex * (x - f(1)) + s
             else:
                 term, fs, gs = x, f(0), f(0)
                 for n in range(2, 21):
-                    term = term * (x / f(n))
+                    term = term * bump(x / f(n), 2 * ULP)
                     gs = gs + f(n - 1) * term
                     if n >= 4:
                         fs = fs + f((n - 1) * (n - 3)) * term
                 F, G = fs * s, gs * s
-            ia = f(1) / a
+            ia = bump(f(1) / a, ULP)
             w[j] = w0 * (F * (f(0.25) * ia * ia) + G * (f(0.5) * b * ia))
     return w
 
@@ -87,6 +105,26 @@ def test_scaled_fp32_widths_give_the_oracle_channel_probabilities(za):
         seen_underflow |= max(c["x"] for c in chans if c) > 88.0
     if za == (82, 208):
         assert seen_underflow  # the range where e^-xm is flushed to 0 is covered
+
+
+@pytest.mark.parametrize("za", [(8, 16), (26, 56), (82, 208)])
+def test_scaled_widths_within_the_fast_math_error_bounds(za):
+    """The same bound with every approximate operation of the fast-math kernels (the
+    exponentials, the reciprocal of a and the series' divisions) moved by its published
+    worst-case error: all up, all down, and 16 random sign patterns per excitation."""
+    Z, A = za
+    rng = np.random.default_rng(4)
+    for Es in ESTARS:
+        chans = oracle_channels(Z, A, Es)
+        g64 = np.array([c["width"] if c else 0.0 for c in chans])
+        if not g64.sum() > 0.0:
+            continue
+        p64 = g64 / g64.sum()
+        signs = [lambda: 1.0, lambda: -1.0] + [lambda: float(rng.choice((-1.0, 1.0)))] * 16
+        for sg in signs:
+            w32 = scaled_widths_f32(chans, sign=sg)
+            p32 = w32.astype(np.float64) / float(w32.sum(dtype=np.float32))
+            assert np.abs(p32 - p64).max() < 3e-5, (za, Es, p32, p64)
 
 
 def test_fp32_rounding_can_put_U_above_the_excitation():
