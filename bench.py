@@ -362,6 +362,40 @@ def other_workloads(ctx, flush, reps: int = 5, warm: int = 3) -> dict:
     return res
 
 
+def level_density_cost(w, first, flush, steps: int = 3) -> dict:
+    """The bench batch with the constant-temperature level density below U_x (reading M26,
+    pnuc_config.level_density = 1) against the default Fermi gas: events/s of the persistent
+    method in the FP32 and FP64 modes, each in its own context, CUDA events, L2 flushed."""
+    import torch
+
+    from paper_1309_7963_gb300 import pnuc
+    stream = torch.cuda.current_stream()
+    out = {}
+    for ld in (0, 1):
+        c = pnuc.Context(torch.cuda.current_device(), level_density=ld)
+        tids = np.array([c.create_target(*za) for za in w.targets], np.int32)
+        e = torch.tensor(w.energies, dtype=torch.float64, device="cuda")
+        t = torch.tensor(tids[w.tidx], dtype=torch.int32, device="cuda")
+        buf = c.alloc(w.n, capacity=8 * w.n)
+        for prec in ("fp32", "fp64"):
+            c.simulate(e, t, seed=w.seed, first_event_id=first, precision=prec, out=buf)
+            torch.cuda.synchronize()
+            ms = []
+            for k in range(steps):
+                flush.fill_(float(k))
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                c.simulate(e, t, seed=w.seed, first_event_id=first, precision=prec, out=buf)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            out[f"{'fermi_gas' if ld == 0 else 'constant_temperature'}_{prec}"] = w.n / (float(np.median(ms)) * 1e-3)
+        del buf
+        c.close()
+    out["unit"] = UNIT
+    return out
+
+
 def cpu_baseline(n_each: int, threads: int | None = None) -> dict:
     """The CPU oracle, as it stands, on a bounded sample of the workload."""
     import oracle
@@ -489,6 +523,10 @@ def main():
                 "plain": world * n * 2 / (f_plain * 1e-3), "unit": UNIT,
                 "batched_vs_plain": f_plain / min(f_pers, f_sort)}
     others = None if (args.no_others or world > 1) else other_workloads(ctx, flush)
+    # the composite level density (reading M26, a context option) on the same batch
+    level_ct = None
+    if not (args.no_others or world > 1):
+        level_ct = level_density_cost(w, first, flush)
     clk = clocks.stop()
 
     e2e = None
@@ -606,7 +644,7 @@ def main():
         "launch_ms": launch_ms, "secondaries_per_step": n_sec,
         "flags_nonzero_fraction": float(np.mean(res["flags"] != 0)),
         "plain": plain, "batched_vs_plain": (value / plain["value"]) if plain else None, "fp64_mode": fp64,
-        "fp32_scaled_mode": scaled, "other_workloads": others,
+        "fp32_scaled_mode": scaled, "other_workloads": others, "level_density_option": level_ct,
         "phase_split": phase_split,
         "p50_ms": serving["runs"][-1]["p50_ms"] if serving else None,
         "p99_ms": serving["runs"][-1]["p99_ms"] if serving else None,

@@ -125,6 +125,11 @@ typedef struct {
     int32_t max_attempts;      /* entries per event until non-elastic (default 1000) */
     int32_t max_evap_steps;    /* evaporation steps per event (default 64) */
     int32_t max_evap_trials;   /* rejection trials per emission (default 10000) */
+    int32_t level_density;     /* the daughters' level density in the evaporation (§2.4): 0 (default) the
+                                  Fermi gas exp(2 sqrt(a U)), a = A/8; 1 the composite form of GEM after
+                                  Gilbert and Cameron, constant temperature below U_x = 2.5 + 150/A MeV,
+                                  joined to the Fermi gas in value and slope at U_x (not with
+                                  PNUC_FP32_SCALED: PNUC_ERR_ARG) */
 } pnuc_config;
 
 /* One batch of incident nucleons. */

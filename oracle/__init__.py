@@ -45,14 +45,16 @@ COUNTER_NAMES = ("steps", "candidates", "kinematics", "pauli_blocked", "collisio
                  "settled", "evap_passes", "evap_exps", "evap_series")
 COUNTERS_DTYPE = np.dtype([(n, "<u8") for n in COUNTER_NAMES])
 LIMITS_DTYPE = np.dtype([("max_steps", "<i4"), ("max_attempts", "<i4"), ("stack_cap", "<i4"),
-                         ("max_evap_steps", "<i4"), ("max_evap_trials", "<i4")])
+                         ("max_evap_steps", "<i4"), ("max_evap_trials", "<i4"), ("level_density", "<i4")])
 TRACE_DTYPE = np.dtype([("event", "<u4"), ("kind", "<i4"), ("species", "<i4"), ("shell", "<i4"),
                         ("T", "<f8"), ("x", "<f8"), ("y", "<f8"), ("z", "<f8")])
 TRACE_KINDS = {"entry": 0, "null": 1, "pauli": 2, "collision": 3, "refract": 4, "reflect": 5,
                "escape": 6, "capture": 7, "evap": 8, "product": 9}
 
+# level_density: 0 the Fermi gas of reading M20 (default), 1 the constant-temperature composite
+# of reading M26
 DEFAULT_LIMITS = dict(max_steps=100000, max_attempts=1000, stack_cap=64, max_evap_steps=64,
-                      max_evap_trials=10000)
+                      max_evap_trials=10000, level_density=0)
 
 # physical constants of the model, for tests that need them (masses in MeV)
 M_P, M_N = 938.272, 939.565
@@ -109,6 +111,14 @@ def lib() -> C.CDLL:
             L.orc_width_integral.restype = d
             L.orc_channel.argtypes = [C.c_int, C.c_int, d, C.c_int, vp, vp, vp, vp, vp, vp]
             L.orc_channel.restype = d
+            L.orc_channel_ld.argtypes = [C.c_int, C.c_int, d, C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
+            L.orc_channel_ld.restype = d
+            L.orc_level_density.argtypes = [d, d, C.c_int]
+            L.orc_level_density.restype = d
+            L.orc_width_integral_ct.argtypes = [d, d, d, vp]
+            L.orc_width_integral_ct.restype = d
+            L.orc_sample_U_ct.argtypes = [d, d, d, u64, u64, i64, vp]
+            L.orc_sample_U_ct.restype = i64
             L.orc_sample_U.argtypes = [d, d, d, u64, u64, i64, vp]
             L.orc_sample_U.restype = i64
             L.orc_sample_fermi.argtypes = [d, u64, u64, i64, vp]
@@ -221,9 +231,21 @@ def width_integral(a: float, Y: float, b: float) -> float:
     return lib().orc_width_integral(a, Y, b)
 
 
-def channel(Z: int, A: int, Estar: float, j: int) -> dict:
+def level_density(a: float, U: float, mode: int = 0) -> float:
+    """The daughter's level density: mode 0 the Fermi gas (M20), 1 the composite (M26)."""
+    return lib().orc_level_density(a, U, mode)
+
+
+def width_integral_ct(a: float, Y: float, b: float):
+    """Reading M26's width integral and its constant-temperature part."""
+    part = np.zeros(1)
+    total = lib().orc_width_integral_ct(a, Y, b, _p(part))
+    return total, float(part[0])
+
+
+def channel(Z: int, A: int, Estar: float, j: int, level_density: int = 0) -> dict:
     out = [np.zeros(1) for _ in range(6)]
-    g = lib().orc_channel(Z, A, Estar, j, *[_p(o) for o in out])
+    g = lib().orc_channel_ld(Z, A, Estar, j, level_density, *[_p(o) for o in out])
     V, b, Q, Md, a, x = (float(o[0]) for o in out)
     return dict(width=g, V=V, b=b, Q=Q, Md=Md, a=a, x=x)
 
@@ -231,6 +253,13 @@ def channel(Z: int, A: int, Estar: float, j: int) -> dict:
 def sample_U(a: float, x: float, b: float, n: int, seed: int = 0, event: int = 0):
     out = np.zeros(n)
     trials = lib().orc_sample_U(a, x, b, seed, event, n, _p(out))
+    return out, trials
+
+
+def sample_U_ct(a: float, Y: float, b: float, n: int, seed: int = 0, event: int = 0):
+    """n draws of reading M26's emission sampler (daughter excitations U) and the trials taken."""
+    out = np.zeros(n)
+    trials = lib().orc_sample_U_ct(a, Y, b, seed, event, n, _p(out))
     return out, trials
 
 

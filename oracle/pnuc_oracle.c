@@ -81,6 +81,7 @@ typedef struct {
 
 typedef struct {
     int32_t max_steps, max_attempts, stack_cap, max_evap_steps, max_evap_trials;
+    int32_t level_density; /* 0: Fermi gas (reading M20); 1: constant temperature below U_x (M26) */
 } orc_limits;
 
 /* one trace entry per model decision (for hand-traced events and invariant tests) */
@@ -462,11 +463,60 @@ double orc_width_integral(double a, double Y, double b)
     return width_F(x) / (4.0 * a * a) + b * width_G(x) / (2.0 * a);
 }
 
-/* Channel parameters of ejectile j from parent (Z, A) at excitation Estar.
- * Returns the unnormalised width; writes barrier V, offset b, Q, daughter mass Md,
- * level-density parameter a and x = 2 sqrt(a Y). Closed channels return 0. */
-double orc_channel(int Z, int A, double Estar, int j, double *V_out, double *b_out, double *Q_out,
-                   double *Md_out, double *a_out, double *x_out)
+/* Reading M26 (an option; M20's Fermi gas stays the default): the level density of GEM's
+ * evaporation after Gilbert and Cameron, a constant-temperature form below the matching
+ * energy U_x = 2.5 + 150/A_d MeV and the Fermi-gas form above it. Matched to M20's
+ * exp(2 sqrt(a U)) in value and in slope at U_x, the constant-temperature part is
+ * exp(sqrt(a U_x) + U / T) with 1/T = sqrt(a / U_x). A_d = 8a (a = A_d / 8). */
+static double ct_Ux(double a) { return 2.5 + 150.0 / (8.0 * a); }
+
+double orc_level_density(double a, double U, int mode)
+{
+    if (mode == 1) {
+        double Ux = ct_Ux(a);
+        if (U < Ux) return exp(sqrt(a * Ux) + U * sqrt(a / Ux));
+    }
+    return exp(2.0 * sqrt(a * U));
+}
+
+/* e^z - 1 - z, by series below z = 1/2 */
+static double expm1_minus(double z)
+{
+    if (z >= 0.5) return expm1(z) - z;
+    double term = z, sum = 0.0; /* term = z^n / n!, starting at n = 1 */
+    for (int n = 2; n <= 20; n++) {
+        term *= z / n;
+        sum += term;
+    }
+    return sum;
+}
+
+/* Reading M26's width integral: over U in [0, Y] of (Y + b - U) rho(U) dU with rho the
+ * composite density. The constant-temperature part over [0, L], L = min(Y, U_x), is
+ * C [(Y + b - L)(e^{kL} - 1)/k + (e^{kL} - 1 - kL)/k^2] with k = 1/T, C = e^{sqrt(a U_x)};
+ * above U_x the Fermi-gas part is M20's integral over [0, Y] less the same integrand over
+ * [0, U_x], (Y + b)/(2a) G(x_x) - H(x_x)/(8a^2), x_x = 2 sqrt(a U_x), H(x) = e^x (x^3 - 3x^2 +
+ * 6x - 6) + 6. Writes the constant-temperature part to *ct_part (if not NULL). */
+double orc_width_integral_ct(double a, double Y, double b, double *ct_part)
+{
+    double Ux = ct_Ux(a), k = sqrt(a / Ux), xx = 2.0 * sqrt(a * Ux);
+    double L = Y < Ux ? Y : Ux, kL = k * L;
+    double ict = exp(0.5 * xx) * ((Y + b - L) * expm1(kL) / k + expm1_minus(kL) / (k * k));
+    if (ct_part) *ct_part = ict;
+    if (!(Y > Ux)) return ict;
+    double ex = exp(xx);
+    double Gx = ex * (xx - 1.0) + 1.0;
+    double Hx = ex * (((xx - 3.0) * xx + 6.0) * xx - 6.0) + 6.0;
+    double below = (Y + b) * Gx / (2.0 * a) - Hx / (8.0 * a * a);
+    return ict + (orc_width_integral(a, Y, b) - below);
+}
+
+/* Channel parameters of ejectile j from parent (Z, A) at excitation Estar, with the level
+ * density of reading M20 (ld = 0) or M26 (ld = 1). Returns the unnormalised width; writes
+ * barrier V, offset b, Q, daughter mass Md, level-density parameter a and x = 2 sqrt(a Y).
+ * Closed channels return 0. */
+double orc_channel_ld(int Z, int A, double Estar, int j, int ld, double *V_out, double *b_out, double *Q_out,
+                      double *Md_out, double *a_out, double *x_out)
 {
     int Zd = Z - EJ_Z[j], Ad = A - EJ_A[j];
     *V_out = *b_out = *Q_out = *Md_out = *a_out = *x_out = 0.0;
@@ -497,7 +547,14 @@ double orc_channel(int Z, int A, double Estar, int j, double *V_out, double *b_o
     *a_out = a;
     if (!(Y > 0.0)) return 0.0;
     *x_out = 2.0 * sqrt(a * Y);
-    return EJ_G[j] * EJ_M[j] * cj * (A3 * A3) * orc_width_integral(a, Y, b);
+    double I = ld == 1 ? orc_width_integral_ct(a, Y, b, NULL) : orc_width_integral(a, Y, b);
+    return EJ_G[j] * EJ_M[j] * cj * (A3 * A3) * I;
+}
+
+double orc_channel(int Z, int A, double Estar, int j, double *V_out, double *b_out, double *Q_out,
+                   double *Md_out, double *a_out, double *x_out)
+{
+    return orc_channel_ld(Z, A, Estar, j, 0, V_out, b_out, Q_out, Md_out, a_out, x_out);
 }
 
 /* Rejection sampler for t in [0, x] with density h(t) ~ [t(2x - t)/(4a) + b](x - t) e^-t.
@@ -523,6 +580,74 @@ static double sample_t(orc_stream *st, double a, double x, double b, int max_tri
         if (ua * (W1 * t + W2) < h) return t;
     }
     return -1.0;
+}
+
+/* Reading M26's emission sampler: the daughter's excitation U in [0, Y] with density
+ * ~ (Y + b - U) rho(U), rho the composite level density. One draw picks the part, the
+ * constant-temperature one (U < L = min(Y, U_x)) with probability I_ct / I; then trials of
+ * four draws (um, u1, u2, ua) as in sample_t. Constant-temperature part: t = k (L - U) in
+ * [0, kL] has density ~ (c0 + t) e^-t, c0 = k (Y + b - L): for kL >= 2 the mixture of
+ * Exp(1) (weight c0) and Gamma(2,1) (weight 1), kept if t < kL; for kL < 2 the mixture of
+ * kL u1 (weight c0 kL) and kL max(u1, u2) (weight (kL)^2 / 2), kept with probability e^-t.
+ * Fermi-gas part: sample_t's trial on [0, x], kept if t < x - x_x (U > U_x). Returns U, or
+ * -1 after max_trials. */
+static double sample_U_ct(orc_stream *st, double a, double Y, double b, double x, int max_trials, int *trials)
+{
+    double Ux = ct_Ux(a), k = sqrt(a / Ux), xx = 2.0 * sqrt(a * Ux);
+    double ict, itot = orc_width_integral_ct(a, Y, b, &ict);
+    double up = U(st);
+    if (up * itot < ict) {
+        double L = Y < Ux ? Y : Ux, kL = k * L, c0 = k * (Y + b - L);
+        int small = kL < 2.0;
+        double pmix = small ? c0 * kL / (c0 * kL + 0.5 * kL * kL) : c0 / (c0 + 1.0);
+        for (int n = 0; n < max_trials; n++) {
+            double um = U(st), u1 = U(st), u2 = U(st), ua = U(st);
+            (*trials)++;
+            int first = um < pmix;
+            double t;
+            if (small) {
+                t = first ? kL * u1 : kL * (u1 > u2 ? u1 : u2);
+                if (!(ua < exp(-t))) continue;
+            } else {
+                t = first ? -log(u1) : -log(u1 * u2);
+                if (!(t < kL)) continue;
+            }
+            return L - t / k;
+        }
+        return -1.0;
+    }
+    double W1 = x * x / (2.0 * a), W2 = b * x;
+    int small = x < 2.0;
+    double pmix = small ? W1 * x / (W1 * x + 2.0 * W2) : W1 / (W1 + W2);
+    double tmax = x - xx;
+    for (int n = 0; n < max_trials; n++) {
+        double um = U(st), u1 = U(st), u2 = U(st), ua = U(st);
+        (*trials)++;
+        int first = um < pmix;
+        double t;
+        if (small) t = first ? x * (u1 > u2 ? u1 : u2) : x * u1;
+        else t = first ? -log(u1 * u2) : -log(u1);
+        if (t >= tmax) continue;
+        double h = (t * (2.0 * x - t) / (4.0 * a) + b) * (x - t);
+        if (small) h *= exp(-t);
+        if (ua * (W1 * t + W2) < h) return (x - t) * (x - t) / (4.0 * a);
+    }
+    return -1.0;
+}
+
+/* test entry: n samples of M26's emission sampler on a Philox stream (seed, event) */
+int64_t orc_sample_U_ct(double a, double Y, double b, uint64_t seed, uint64_t event, int64_t n, double *out)
+{
+    orc_stream st;
+    stream_init(&st, seed, event, NULL, 0, NULL);
+    int64_t trials = 0;
+    double x = 2.0 * sqrt(a * Y);
+    for (int64_t i = 0; i < n; i++) {
+        int tr = 0;
+        out[i] = sample_U_ct(&st, a, Y, b, x, 1 << 30, &tr);
+        trials += tr;
+    }
+    return trials;
 }
 
 /* test entry: the sampler on a Philox stream (seed, event), n samples of U = (x-t)^2/(4a) */
@@ -816,7 +941,7 @@ static void run_event(const orc_target *t, int proj, double T0, uint32_t ev, orc
         double G[6], V[6], bj[6], Q[6], Md[6], a[6], x[6], S = 0.0;
         c->evap_passes++;
         for (int j = 0; j < 6; j++) {
-            G[j] = orc_channel(Z, A, Estar, j, &V[j], &bj[j], &Q[j], &Md[j], &a[j], &x[j]);
+            G[j] = orc_channel_ld(Z, A, Estar, j, L->level_density, &V[j], &bj[j], &Q[j], &Md[j], &a[j], &x[j]);
             S += G[j];
             if (G[j] > 0.0) {
                 if (x[j] >= 1.0) c->evap_exps++;
@@ -841,14 +966,19 @@ static void run_event(const orc_target *t, int proj, double T0, uint32_t ev, orc
                     break;
                 }
         int trials = 0;
-        double tt = sample_t(st, a[ch], x[ch], bj[ch], L->max_evap_trials, &trials);
+        double X = Estar - Q[ch];
+        double Ud;
+        if (L->level_density == 1) {
+            Ud = sample_U_ct(st, a[ch], X - V[ch], bj[ch], x[ch], L->max_evap_trials, &trials);
+        } else {
+            double tt = sample_t(st, a[ch], x[ch], bj[ch], L->max_evap_trials, &trials);
+            Ud = tt < 0.0 ? -1.0 : (x[ch] - tt) * (x[ch] - tt) / (4.0 * a[ch]);
+        }
         c->evap_trials += trials;
-        if (tt < 0.0) {
+        if (Ud < 0.0) {
             res->flags |= F_EVAP_TRIAL_CAP;
             break;
         }
-        double Ud = (x[ch] - tt) * (x[ch] - tt) / (4.0 * a[ch]);
-        double X = Estar - Q[ch];
         double eps = X - Ud;
         /* two-body decay, isotropic in the rest frame, boosted to the lab */
         double W = orc_semf_mass(Z, A) + Estar;

@@ -35,25 +35,27 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 // depend only on the compiled kernels and the device, one device per process here).
 enum OccKind { kOccCascade = 0, kOccEvap = 1, kOccSorted = 2 };
 
-int occupancy_kind(OccKind kind, pnuc_precision prec, int block, bool count)
+int occupancy_kind(OccKind kind, pnuc_precision prec, int block, bool count, bool ct = false)
 {
-    static std::atomic<int> cache[3][3][4][2];
+    static std::atomic<int> cache[3][3][4][2][2];
     static std::once_flag once;
     std::call_once(once, [] {
         for (auto &a : cache)
             for (auto &b : a)
                 for (auto &c : b)
-                    for (auto &d : c) d.store(-1);
+                    for (auto &d : c)
+                        for (auto &e : d) e.store(-1);
     });
     const int bi = block == 64 ? 0 : block == 128 ? 1 : block == 256 ? 2 : 3;
-    std::atomic<int> &slot = cache[kind][prec == PNUC_FP64 ? 1 : prec == PNUC_FP32_SCALED ? 2 : 0][bi][count ? 1 : 0];
+    std::atomic<int> &slot =
+        cache[kind][prec == PNUC_FP64 ? 1 : prec == PNUC_FP32_SCALED ? 2 : 0][bi][count ? 1 : 0][ct ? 1 : 0];
     int v = slot.load();
     if (v >= 0) return v;
     if (kind == kOccCascade)
         v = prec == PNUC_FP64 ? occupancy_persistent_fp64(block) : occupancy_persistent_fp32(block, count);
     else if (kind == kOccEvap)
-        v = prec == PNUC_FP64 ? occupancy_evap_fp64(block)
-                              : occupancy_evap_fp32(block, count, prec == PNUC_FP32_SCALED);
+        v = prec == PNUC_FP64 ? occupancy_evap_fp64(block, ct)
+                              : occupancy_evap_fp32(block, count, prec == PNUC_FP32_SCALED, ct);
     else
         v = prec == PNUC_FP64 ? occupancy_sorted_fp64(block) : occupancy_sorted_fp32(block, count);
     slot.store(v);
@@ -83,6 +85,8 @@ pnuc_status check_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method met
 {
     if (!ctx || !batch || !out) return fail(ctx, PNUC_ERR_ARG, "null argument");
     if (!valid_precision(precision)) return fail(ctx, PNUC_ERR_ARG, "bad precision %d", precision);
+    if (precision == PNUC_FP32_SCALED && ctx->cfg.level_density != 0)
+        return fail(ctx, PNUC_ERR_ARG, "the scaled FP32 widths need the Fermi-gas level density");
     if (method != PNUC_PLAIN && method != PNUC_PERSISTENT && method != PNUC_SORTED)
         return fail(ctx, PNUC_ERR_ARG, "bad method %d", method);
     if (batch->n > 0xFFFFFFFFull) return fail(ctx, PNUC_ERR_ARG, "n = %llu exceeds 2^32-1", (unsigned long long)batch->n);
@@ -130,7 +134,7 @@ cudaError_t launch_evap_for(pnuc_ctx *ctx, pnuc_precision precision, const SimPa
                             bool count, uint64_t n, cudaStream_t s, unsigned max_blocks)
 {
     auto occ_evap = [&](int b) {
-        return occupancy_kind(kOccEvap, precision, b, count);
+        return occupancy_kind(kOccEvap, precision, b, count, p.level_density == 1);
     };
     int eblock = t.block_size, occ_e = occ_evap(eblock);
     while (occ_e < 1 && eblock > 64) occ_e = occ_evap(eblock /= 2);
@@ -175,6 +179,7 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
     p.max_attempts = ctx->cfg.max_attempts;
     p.max_evap_steps = ctx->cfg.max_evap_steps;
     p.max_evap_trials = ctx->cfg.max_evap_trials;
+    p.level_density = ctx->cfg.level_density;
     p.refill_threshold = t.refill_threshold;
     p.chunk = t.chunk;
     p.kin_batch = t.kin_batch;
@@ -257,6 +262,7 @@ void pnuc_default_config(pnuc_config *cfg)
     cfg->max_attempts = 1000;
     cfg->max_evap_steps = 64;
     cfg->max_evap_trials = 10000;
+    cfg->level_density = 0;
 }
 
 const char *pnuc_status_string(pnuc_status s)
@@ -287,7 +293,8 @@ pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
     pnuc_config cfg;
     pnuc_default_config(&cfg);
     if (cfg_in) cfg = *cfg_in;
-    if (cfg.max_steps < 1 || cfg.max_attempts < 1 || cfg.max_evap_steps < 1 || cfg.max_evap_trials < 1)
+    if (cfg.max_steps < 1 || cfg.max_attempts < 1 || cfg.max_evap_steps < 1 || cfg.max_evap_trials < 1 ||
+        (cfg.level_density != 0 && cfg.level_density != 1))
         return PNUC_ERR_ARG;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return PNUC_ERR_CUDA;

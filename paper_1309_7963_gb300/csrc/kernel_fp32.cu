@@ -16,11 +16,20 @@ namespace {
 __global__ void __maxnreg__(96) persistent_kernel_f32(const SimParams P) { persistent_body<float, false>(P); }
 __global__ void __maxnreg__(96) evap_kernel_f32(const SimParams P) { evap_body<float, false, false>(P); }
 __global__ void __maxnreg__(96) evap_kernel_f32s(const SimParams P) { evap_body<float, false, true>(P); }
+__global__ void __maxnreg__(96) evap_kernel_f32c(const SimParams P) { evap_body<float, false, false, true>(P); }
+
 }  // namespace
 }  // namespace dev
 
+
+// The kernels that evaporate come in one variant per level density (SimParams.level_density:
+// the Fermi gas, or the constant-temperature composite), so that the option's code is not in
+// the default kernels.
 cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, bool scaled, cudaStream_t s)
 {
+    if (p.level_density == 1)
+        return count ? dev::launch_plain<float, true, false, true>(p, block, s)
+                     : dev::launch_plain<float, false, false, true>(p, block, s);
     if (scaled)
         return count ? dev::launch_plain<float, true, true>(p, block, s) : dev::launch_plain<float, false, true>(p, block, s);
     return count ? dev::launch_plain<float, true>(p, block, s) : dev::launch_plain<float, false>(p, block, s);
@@ -32,6 +41,11 @@ cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool
 }
 cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count, bool scaled, cudaStream_t s)
 {
+    if (p.level_density == 1) {
+        if (count) return dev::launch_evap<float, true, false, true>(p, grid, block, s);
+        return dev::launch_kernel(dev::evap_kernel_f32c, dev::evap_smem_bytes<float>(p.n_targets, block), p, grid,
+                                  block, s);
+    }
     if (scaled) {
         if (count) return dev::launch_evap<float, true, true>(p, grid, block, s);
         return dev::launch_kernel(dev::evap_kernel_f32s, dev::evap_smem_bytes<float, true>(p.n_targets, block), p,
@@ -50,8 +64,12 @@ int occupancy_sorted_fp32(int block, bool count)
     return count ? dev::occupancy_sorted<float, true>(block) : dev::occupancy_sorted<float, false>(block);
 }
 size_t sorted_stack_bytes_fp32() { return sizeof(dev::Particle<float>) * kStackCap; }
-int occupancy_evap_fp32(int block, bool count, bool scaled)
+int occupancy_evap_fp32(int block, bool count, bool scaled, bool ct)
 {
+    if (ct) {
+        if (count) return dev::occupancy_evap<float, true, false, true>(block);
+        return dev::occupancy_of(dev::evap_kernel_f32c, dev::evap_smem_bytes<float>(kMaxTargets, block), block);
+    }
     if (scaled) {
         if (count) return dev::occupancy_evap<float, true, true>(block);
         return dev::occupancy_of(dev::evap_kernel_f32s, dev::evap_smem_bytes<float, true>(kMaxTargets, block), block);

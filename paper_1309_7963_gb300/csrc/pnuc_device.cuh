@@ -939,11 +939,70 @@ __device__ R sample_t(Stream<R> &rng, R a, R x, R b, int max_trials, int &trials
     return R(-1);
 }
 
+// Reading M26's emission sampler: the daughter's excitation U in [0, Y] with density
+// ~ (Y + b - U) rho(U), rho the composite level density. One draw picks the part, the
+// constant-temperature one (U < L = min(Y, U_x)) with probability I_ct / I (FP64); then trials
+// of four draws as in sample_t(). Constant-temperature part: t = k (L - U) on [0, kL] has
+// density ~ (c0 + t) e^-t, c0 = k (Y + b - L): for kL >= 2 the mixture of Exp(1) (weight c0)
+// and Gamma(2,1) (weight 1), kept if t < kL; for kL < 2 the mixture of kL u1 (weight c0 kL)
+// and kL max(u1, u2) (weight (kL)^2 / 2), kept with probability e^-t. Fermi-gas part:
+// sample_t()'s trial on [0, x], kept if t < x - x_x (U above U_x). Returns U, or -1 after
+// max_trials.
+__device__ double width_integral_ct(double a, double Y, double b, double *ct_part);
+
+template <typename R>
+__device__ R sample_U_ct(Stream<R> &rng, R a, R Y, R b, R x, int max_trials, int &trials)
+{
+    const R Ux = R(2.5) + R(150.0) / (R(8.0) * a), k = sqrt(a / Ux), xx = R(2) * sqrt(a * Ux);
+    double ict;
+    const double itot = width_integral_ct(to_d<R>(a), to_d<R>(Y), to_d<R>(b), &ict);
+    if (to_d<R>(rng.next()) * itot < ict) {
+        const R L = Y < Ux ? Y : Ux, kL = k * L, c0 = k * (Y + b - L);
+        const bool small = kL < R(2);
+        const R pmix = small ? c0 * kL / (c0 * kL + R(0.5) * kL * kL) : c0 / (c0 + R(1));
+        for (int n = 0; n < max_trials; ++n) {
+            rng.ensure(6);  // four for this trial, and the two decay angles if it is accepted
+            const R um = rng.next(), u1 = rng.next(), u2 = rng.next(), ua = rng.next();
+            ++trials;
+            const bool first = um < pmix;
+            R t;
+            if (small) {
+                t = first ? kL * u1 : kL * (u1 > u2 ? u1 : u2);
+                if (!(ua < exp(-t))) continue;
+            } else {
+                t = first ? -log(u1) : -log(u1 * u2);
+                if (!(t < kL)) continue;
+            }
+            return L - t / k;
+        }
+        return R(-1);
+    }
+    const R W1 = x * x / (R(2) * a), W2 = b * x;
+    const bool small = x < R(2);
+    const R pmix = small ? W1 * x / (W1 * x + R(2) * W2) : W1 / (W1 + W2);
+    const R tmax = x - xx;
+    for (int n = 0; n < max_trials; ++n) {
+        rng.ensure(6);
+        const R um = rng.next(), u1 = rng.next(), u2 = rng.next(), ua = rng.next();
+        ++trials;
+        const bool first = um < pmix;
+        R t;
+        if (small) t = first ? x * (u1 > u2 ? u1 : u2) : x * u1;
+        else t = first ? -log(u1 * u2) : -log(u1);
+        if (t >= tmax) continue;
+        R h = (t * (R(2) * x - t) / (R(4) * a) + b) * (x - t);
+        if (small) h *= exp(-t);
+        if (ua * (W1 * t + W2) < h) return (x - t) * (x - t) / (R(4) * a);
+    }
+    return R(-1);
+}
+
 // Channel parameters in precision R (Q-values and daughter masses in FP64).
 template <typename R>
 struct ChanP {
     double Q, Md;
     R V, b, a, x, w0;  // barrier, offset, level-density parameter, 2 sqrt(aY), g m c A^(2/3)
+    R Y;               // X - V: the range of the daughter's excitation
     bool open;
 };
 
@@ -976,6 +1035,7 @@ __device__ void channel_params(const SimParams &P, int Z, int A, double Mparent,
     c.V = V;
     c.b = b;
     c.a = R(Ad) / R(8);
+    c.Y = Y;
     if (!(Y > R(0))) return;
     c.x = R(2) * sqrt(c.a * Y);
     c.w0 = ej_G<R>(j) * ej_M<R>(j) * cj * (A3 * A3);
@@ -1001,6 +1061,45 @@ __device__ __forceinline__ void width_FG(double x, double &F, double &G)
     }
     F = f;
     G = g;
+}
+
+// Reading M26 (the option pnuc_config.level_density = 1): the daughter's level density is
+// constant-temperature below U_x = 2.5 + 150/A_d MeV (A_d = 8a) and M20's Fermi gas above,
+// joined in value and slope at U_x: exp(sqrt(a U_x) + U / T) with 1/T = sqrt(a / U_x).
+__device__ __forceinline__ double ct_matching_energy(double a) { return 2.5 + 150.0 / (8.0 * a); }
+
+// e^z - 1 - z, by series below z = 1/2
+__device__ double expm1_minus(double z)
+{
+    if (z >= 0.5) return expm1(z) - z;
+    double term = z, sum = 0.0;  // term = z^n / n!
+#pragma unroll 1
+    for (int n = 2; n <= 20; ++n) {
+        term *= z / n;
+        sum += term;
+    }
+    return sum;
+}
+
+// M26's width integral over U in [0, Y] of (Y + b - U) rho(U), FP64: the constant-temperature
+// part over [0, L], L = min(Y, U_x), is C [(Y + b - L)(e^{kL} - 1)/k + (e^{kL} - 1 - kL)/k^2]
+// (k = 1/T, C = e^{sqrt(a U_x)}); above U_x, M20's integral over [0, Y] less the same
+// integrand over [0, U_x], (Y + b) G(x_x)/(2a) - H(x_x)/(8a^2), x_x = 2 sqrt(a U_x),
+// H(x) = e^x (x^3 - 3x^2 + 6x - 6) + 6. The constant-temperature part goes to *ct_part.
+__device__ double width_integral_ct(double a, double Y, double b, double *ct_part)
+{
+    const double Ux = ct_matching_energy(a), k = sqrt(a / Ux), xx = 2.0 * sqrt(a * Ux);
+    const double L = Y < Ux ? Y : Ux, kL = k * L;
+    const double ict = exp(0.5 * xx) * ((Y + b - L) * expm1(kL) / k + expm1_minus(kL) / (k * k));
+    *ct_part = ict;
+    if (!(Y > Ux)) return ict;
+    const double ex = exp(xx);
+    const double Gx = ex * (xx - 1.0) + 1.0;
+    const double Hx = ex * (((xx - 3.0) * xx + 6.0) * xx - 6.0) + 6.0;
+    const double below = (Y + b) * Gx / (2.0 * a) - Hx / (8.0 * a * a);
+    double F, G;
+    width_FG(2.0 * sqrt(a * Y), F, G);
+    return ict + ((F / (4.0 * a * a) + b * G / (2.0 * a)) - below);
 }
 
 // The type the six widths of a step are held and drawn in: FP64 (the FP64 mode, and the
@@ -1058,10 +1157,15 @@ __device__ __forceinline__ double channel_width_f32_d(const ChanP<float> &c)
 // (the unscaled width reaches e^160, beyond FP32's range).
 __device__ float channel_width_scaled(const ChanP<float> &c, float xm);
 
-template <typename R, bool kScaled>
+template <typename R, bool kScaled, bool kCT = false>
 __device__ width_t<R, kScaled> channel_width(const ChanP<R> &c, R xm)
 {
-    if constexpr (sizeof(R) == 8) {
+    static_assert(!(kScaled && kCT), "the scaled FP32 widths take the Fermi-gas level density");
+    if constexpr (kCT) {  // M26, FP64 in both modes
+        if (!c.open) return 0.0;
+        double part;
+        return to_d<R>(c.w0) * width_integral_ct(to_d<R>(c.a), to_d<R>(c.Y), to_d<R>(c.b), &part);
+    } else if constexpr (sizeof(R) == 8) {
         if (!c.open) return 0.0;
         double F, G;
         width_FG(c.x, F, G);
@@ -1206,7 +1310,7 @@ __device__ __forceinline__ double daughter_excitation<float>(float x, float t, f
 // The second half of an evaporation step (§2.4), given the six channel widths G of the
 // parent (Z, A, E* in L): the channel draw, the emission energy, and the two-body decay
 // isotropic in the parent's rest frame, boosted to the lab.
-template <typename R, bool kScaled, bool kCount>
+template <typename R, bool kScaled, bool kCT, bool kCount>
 __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const width_t<R, kScaled> *G,
                           Counters<kCount> &C)
 {
@@ -1237,14 +1341,20 @@ __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const 
     ChanP<R> c;  // the chosen channel's parameters, recomputed (the same function of Z, A, E*)
     channel_params<R>(P, Z, A, Mparent, Estar, ch, c);
     int trials = 0;
-    R tt = sample_t<R>(L.rng, c.a, c.x, c.b, P.max_evap_trials, trials);
+    double Ud;
+    if constexpr (kCT) {
+        const R u = sample_U_ct<R>(L.rng, c.a, c.Y, c.b, c.x, P.max_evap_trials, trials);
+        Ud = u < R(0) ? -1.0 : to_d<R>(u);
+    } else {
+        const R tt = sample_t<R>(L.rng, c.a, c.x, c.b, P.max_evap_trials, trials);
+        Ud = tt < R(0) ? -1.0 : daughter_excitation<R>(c.x, tt, c.a);
+    }
     C.add(PNUC_C_EVAP_TRIALS, trials);
-    if (tt < R(0)) {
+    if (Ud < 0.0) {
         L.flags |= PNUC_FLAG_EVAP_TRIAL_CAP;
         L.phase = kFinish;
         return;
     }
-    const double Ud = daughter_excitation<R>(c.x, tt, c.a);
     const double eps = (Estar - c.Q) - Ud;
     const R ctr = R(2) * L.rng.next() - R(1);
     const R phr = R(kTwoPi) * L.rng.next();
@@ -1264,7 +1374,7 @@ __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const 
 
 // One evaporation step of one lane (the plain kernel): widths of the six channels, then
 // evap_emit().
-template <typename R, bool kScaled, bool kCount>
+template <typename R, bool kScaled, bool kCT, bool kCount>
 __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
 {
     if (L.n_evap >= P.max_evap_steps) {
@@ -1283,8 +1393,8 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     }
     const R xm = kScaled ? widths_xm<R>(chans) : R(0);
 #pragma unroll 1
-    for (int j = 0; j < 6; ++j) G[j] = channel_width<R, kScaled>(chans[j], xm);
-    evap_emit<R, kScaled, kCount>(P, L, Mparent, G, C);
+    for (int j = 0; j < 6; ++j) G[j] = channel_width<R, kScaled, kCT>(chans[j], xm);
+    evap_emit<R, kScaled, kCT, kCount>(P, L, Mparent, G, C);
 }
 
 // ------------------------------------------------------------------ warp-wide widths
@@ -1292,12 +1402,12 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
 // (6 x lane + channel in the warp's width array).
 template <typename R>
 struct WidthJob {
-    R x, a, b, w0;
+    R x, a, b, w0, Y;
     int tag;
 };
 constexpr int kWidthSlots = 6 * 32;  // per warp: six channels of every lane
 
-template <typename R, bool kScaled>
+template <typename R, bool kScaled, bool kCT>
 __device__ __forceinline__ width_t<R, kScaled> job_width(const WidthJob<R> &jb, R xm)
 {
     ChanP<R> c;
@@ -1306,7 +1416,8 @@ __device__ __forceinline__ width_t<R, kScaled> job_width(const WidthJob<R> &jb, 
     c.a = jb.a;
     c.b = jb.b;
     c.w0 = jb.w0;
-    return channel_width<R, kScaled>(c, xm);
+    c.Y = jb.Y;
+    return channel_width<R, kScaled, kCT>(c, xm);
 }
 
 // One evaporation step of every lane of the warp with `active` set (the evaporation kernel).
@@ -1319,7 +1430,7 @@ __device__ __forceinline__ width_t<R, kScaled> job_width(const WidthJob<R> &jb, 
 // lane), with the lane's scale reference in xms; no per-lane channel records are kept, so
 // nothing of the step lives in local memory. Called by all 32 lanes of the warp; jobs and gw
 // are the warp's kWidthSlots entries, xms its 32.
-template <typename R, bool kScaled, bool kCount>
+template <typename R, bool kScaled, bool kCT, bool kCount>
 __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, WidthJob<R> *jobs,
                                width_t<R, kScaled> *gw, R *xms, Counters<kCount> &C)
 {
@@ -1347,7 +1458,7 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
         const unsigned me = __ballot_sync(FULL, ex), ms = __ballot_sync(FULL, se);
         if (ex || se) {
             const int slot = ex ? nexp + __popc(me & below) : kWidthSlots - 1 - (nser + __popc(ms & below));
-            jobs[slot] = WidthJob<R>{c.x, c.a, c.b, c.w0, (int)(6 * lane) + j};
+            jobs[slot] = WidthJob<R>{c.x, c.a, c.b, c.w0, c.Y, (int)(6 * lane) + j};
             if (c.x > xm) xm = c.x;
         } else {
             G[j] = width_t<R, kScaled>(0);
@@ -1367,19 +1478,19 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
     __syncwarp();
     for (int k = lane; k < nexp; k += 32) {
         const WidthJob<R> jb = jobs[k];
-        gw[jb.tag] = job_width<R, kScaled>(jb, xms[jb.tag / 6]);
+        gw[jb.tag] = job_width<R, kScaled, kCT>(jb, xms[jb.tag / 6]);
     }
     for (int k = kWidthSlots - 1 - (int)lane; k >= kWidthSlots - nser; k -= 32) {
         const WidthJob<R> jb = jobs[k];
-        gw[jb.tag] = job_width<R, kScaled>(jb, xms[jb.tag / 6]);
+        gw[jb.tag] = job_width<R, kScaled, kCT>(jb, xms[jb.tag / 6]);
     }
     __syncwarp();
-    if (active) evap_emit<R, kScaled, kCount>(P, L, Mparent, G, C);
+    if (active) evap_emit<R, kScaled, kCT, kCount>(P, L, Mparent, G, C);
     __syncwarp();  // the lists are reused by the next step
 }
 
 // Advances lane L by one step of its current phase (no batching: the plain kernel).
-template <typename R, bool kScaled, bool kCount>
+template <typename R, bool kScaled, bool kCT, bool kCount>
 __device__ __forceinline__ void step(const SimParams &P, const ShellTable<R> *sh, const TargetScalars *tabs, Lane<R> &L,
                                      Particle<R> *stack, Counters<kCount> &C)
 {
@@ -1390,7 +1501,7 @@ __device__ __forceinline__ void step(const SimParams &P, const ShellTable<R> *sh
     } else if (L.phase == kEntry) {
         step_entry<R, kCount>(P, sh[L.tgt], tabs[L.tgt].R, L, C);
     } else if (L.phase == kEvap) {
-        step_evap<R, kScaled, kCount>(P, L, C);
+        step_evap<R, kScaled, kCT, kCount>(P, L, C);
     }
 }
 

@@ -68,6 +68,7 @@ struct SimParams {
     unsigned long long *evap_head;   // persistent method: next unclaimed event of the evaporation kernel
     int32_t split_evap;              // 1: persistent method (the cascade kernel leaves evaporation to evap_kernel)
     int32_t max_steps, max_attempts, max_evap_steps, max_evap_trials;
+    int32_t level_density;  // 0 Fermi gas (reading M20), 1 constant temperature below U_x (M26)
     int32_t refill_threshold, chunk;
     int32_t kin_batch;  // persistent kernel: accepted collisions a warp gathers before their kinematics
 };
@@ -84,8 +85,8 @@ cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool
 // Resident blocks per SM of the persistent kernels at a block size.
 int occupancy_persistent_fp64(int block);
 int occupancy_persistent_fp32(int block, bool count);
-int occupancy_evap_fp64(int block);
-int occupancy_evap_fp32(int block, bool count, bool scaled);
+int occupancy_evap_fp64(int block, bool ct);
+int occupancy_evap_fp32(int block, bool count, bool scaled, bool ct);
 // Sorted method (cascade kernel regrouping slots by action): launchers, resident blocks per
 // SM, and the bytes of one slot's particle stack (the stacks live in a context buffer).
 cudaError_t launch_sorted_fp64(const SimParams &p, void *stacks, int grid, int block, cudaStream_t s);

@@ -78,7 +78,7 @@ __device__ __forceinline__ void finish_event(const SimParams &P, Lane<R> &L, Cou
     if (!L.pend && !(L.flags & (PNUC_FLAG_BAD_INPUT | PNUC_FLAG_ATTEMPT_CAP))) C.add(PNUC_C_SETTLED);
 }
 
-template <typename R, bool kCount, bool kScaled = false>
+template <typename R, bool kCount, bool kScaled = false, bool kCT = false>
 __global__ void __launch_bounds__(512) plain_kernel(const SimParams P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(512) plain_kernel(const SimParams P)
         begin_event<R>(P, ts, L, (uint32_t)i);
         while (L.phase != kFinish) {
             L.rng.ensure(8);
-            step<R, kScaled, kCount>(P, sh, ts, L, stack, C);
+            step<R, kScaled, kCT, kCount>(P, sh, ts, L, stack, C);
         }
         finish_event<R, kCount>(P, L, C);
     }
@@ -247,7 +247,7 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
 // Persistent evaporation kernel (after the cascade kernel on the same stream): every lane
 // evaporates, so the width exponentials and the decays run with full warps. Lanes take
 // event indices from the evaporation queue and skip events with nothing pending.
-template <typename R, bool kCount, bool kScaled = false>
+template <typename R, bool kCount, bool kScaled = false, bool kCT = false>
 __device__ __forceinline__ void evap_body(const SimParams &P)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -298,7 +298,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
         const long long t1 = kCount ? clock64() : 0;
         const bool stepping = L.phase == kEvap;
         if (stepping) L.rng.ensure(8);
-        step_evap_warp<R, kScaled, kCount>(P, L, stepping, jobs, gw, xms, C);
+        step_evap_warp<R, kScaled, kCT, kCount>(P, L, stepping, jobs, gw, xms, C);
         if (kCount) {
             __syncwarp();
             if (lane == 0) {
@@ -454,32 +454,32 @@ __global__ void __launch_bounds__(512) persistent_kernel(const SimParams P)
     persistent_body<R, kCount>(P);
 }
 
-template <typename R, bool kCount, bool kScaled = false>
+template <typename R, bool kCount, bool kScaled = false, bool kCT = false>
 __global__ void __launch_bounds__(512) evap_kernel(const SimParams P)
 {
-    evap_body<R, kCount, kScaled>(P);
+    evap_body<R, kCount, kScaled, kCT>(P);
 }
 
-template <typename R, bool kCount, bool kScaled = false>
+template <typename R, bool kCount, bool kScaled = false, bool kCT = false>
 cudaError_t launch_evap(const SimParams &p, int grid, int block, cudaStream_t s)
 {
     if (p.n == 0) return cudaSuccess;
     size_t smem = evap_smem_bytes<R, kScaled>(p.n_targets, block);
-    cudaError_t e = allow_smem(evap_kernel<R, kCount, kScaled>, smem);
+    cudaError_t e = allow_smem(evap_kernel<R, kCount, kScaled, kCT>, smem);
     if (e != cudaSuccess) return e;
-    evap_kernel<R, kCount, kScaled><<<grid, block, smem, s>>>(p);
+    evap_kernel<R, kCount, kScaled, kCT><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
-template <typename R, bool kCount, bool kScaled = false>
+template <typename R, bool kCount, bool kScaled = false, bool kCT = false>
 cudaError_t launch_plain(const SimParams &p, int block, cudaStream_t s)
 {
     if (p.n == 0) return cudaSuccess;
     size_t smem = smem_bytes<R>(p.n_targets, block);
-    cudaError_t e = allow_smem(plain_kernel<R, kCount, kScaled>, smem);
+    cudaError_t e = allow_smem(plain_kernel<R, kCount, kScaled, kCT>, smem);
     if (e != cudaSuccess) return e;
     unsigned long long grid = (p.n + block - 1) / block;
-    plain_kernel<R, kCount, kScaled><<<(unsigned)grid, block, smem, s>>>(p);
+    plain_kernel<R, kCount, kScaled, kCT><<<(unsigned)grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -530,10 +530,11 @@ int occupancy_sorted(int block)
     return occupancy_of(sorted_kernel<R, kCount>, sorted_smem_bytes<R>(kMaxTargets, block), block);
 }
 
-template <typename R, bool kCount, bool kScaled = false>
+template <typename R, bool kCount, bool kScaled = false, bool kCT = false>
 int occupancy_evap(int block)
 {
-    return occupancy_of(evap_kernel<R, kCount, kScaled>, evap_smem_bytes<R, kScaled>(kMaxTargets, block), block);
+    return occupancy_of(evap_kernel<R, kCount, kScaled, kCT>, evap_smem_bytes<R, kScaled>(kMaxTargets, block),
+                        block);
 }
 
 template <typename R, bool kCount>

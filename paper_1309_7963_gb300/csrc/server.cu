@@ -546,6 +546,8 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg_in, 
         cfg.max_request_events < 1 || cfg.max_merge < 1 || cfg.max_merge > (uint32_t)kMaxSeg || cfg.merge_events < 1 ||
         cfg.merge_events > kMaxGroupEvents || cfg.lane_events < 1 || cfg.lane_events > 1024)
         return fail(ctx, PNUC_ERR_ARG, "bad server configuration");
+    if (cfg.precision == PNUC_FP32_SCALED && ctx->cfg.level_density != 0)
+        return fail(ctx, PNUC_ERR_ARG, "the scaled FP32 widths need the Fermi-gas level density");
     CU(ctx, cudaSetDevice(ctx->cfg.device));
     pnuc_server *S = new pnuc_server();
     S->ctx = ctx;

@@ -41,7 +41,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "out of range", 3: "capacity exceed
 
 class pnuc_config(C.Structure):
     _fields_ = [("device", C.c_int32), ("max_steps", C.c_int32), ("max_attempts", C.c_int32),
-                ("max_evap_steps", C.c_int32), ("max_evap_trials", C.c_int32)]
+                ("max_evap_steps", C.c_int32), ("max_evap_trials", C.c_int32), ("level_density", C.c_int32)]
 
 
 class pnuc_batch(C.Structure):

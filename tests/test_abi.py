@@ -31,7 +31,7 @@ def test_record_layouts():
     assert pnuc.SECONDARY_DTYPE.fields["T"][1] == 8
     assert pnuc.RESIDUAL_DTYPE.fields["Estar_cascade"][1] == 24
     assert C.sizeof(pnuc.pnuc_batch) == 56 and C.sizeof(pnuc.pnuc_output) == 40
-    assert C.sizeof(pnuc.pnuc_tuning) == 20 and C.sizeof(pnuc.pnuc_config) == 20
+    assert C.sizeof(pnuc.pnuc_tuning) == 20 and C.sizeof(pnuc.pnuc_config) == 24
 
 
 def test_host_side_status_strings_without_gpu():
