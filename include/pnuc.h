@@ -428,6 +428,13 @@ pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, const pnuc_se
 pnuc_status pnuc_kernel_timing(pnuc_ctx *ctx, int32_t enable);
 pnuc_status pnuc_kernel_times(pnuc_ctx *ctx, double *cascade_ms, double *evaporation_ms, uint64_t *launches);
 
+/* The double-precision exponential the FP32 mode's evaporation widths take (§2.4: the widths'
+ * e^x, x = 2 sqrt(a Y)), evaluated on the integer pipes by a fixed-point table method (the FP64
+ * pipe is scarce on GB300), exposed so that its accuracy can be tested: out[i] = e^x[i] for
+ * x[i] in [1, 256), -1 for other arguments. x and out: device arrays of n entries. Asynchronous
+ * on stream. The paper has no counterpart. */
+pnuc_status pnuc_width_exp(pnuc_ctx *ctx, const float *x, double *out, uint64_t n, void *stream);
+
 /* Measured throughput of the pipes the event kernels use, in lane operations per second
  * (one fused multiply-add = one operation): FP32 FMA, FP64 FMA, special-function unit
  * (reciprocal square root) and 32-bit integer multiply-add. Independent FMA chains on 8

@@ -617,6 +617,14 @@ pnuc_status pnuc_simulate_host_noalloc(pnuc_ctx *ctx, pnuc_precision precision, 
     return PNUC_OK;
 }
 
+pnuc_status pnuc_width_exp(pnuc_ctx *ctx, const float *x, double *out, uint64_t n, void *stream)
+{
+    if (!ctx || (n > 0 && (!x || !out))) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    CU(ctx, cudaSetDevice(ctx->cfg.device));
+    CU(ctx, launch_width_exp(x, out, n, ctx->sm_count, (cudaStream_t)stream));
+    return PNUC_OK;
+}
+
 pnuc_status pnuc_measure_peaks(pnuc_ctx *ctx, pnuc_peaks *out)
 {
     if (!ctx || !out) return fail(ctx, PNUC_ERR_ARG, "null argument");

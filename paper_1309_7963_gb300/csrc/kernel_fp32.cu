@@ -18,9 +18,25 @@ __global__ void __maxnreg__(96) evap_kernel_f32(const SimParams P) { evap_body<f
 __global__ void __maxnreg__(96) evap_kernel_f32s(const SimParams P) { evap_body<float, false, true>(P); }
 __global__ void __maxnreg__(96) evap_kernel_f32c(const SimParams P) { evap_body<float, false, false, true>(P); }
 
+// The FP32 mode's width exponential on n arguments (pnuc_width_exp): e^x for x in [1, 256),
+// -1 for other arguments.
+__global__ void width_exp_kernel(const float *x, double *out, uint64_t n)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        out[i] = v >= 1.f && v < 256.f ? exp_fixed(v) : -1.0;
+    }
+}
 }  // namespace
 }  // namespace dev
 
+cudaError_t launch_width_exp(const float *x, double *out, uint64_t n, int sm_count, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + 255) / 256, cap = (uint64_t)sm_count * 8;
+    dev::width_exp_kernel<<<(unsigned)(blocks < cap ? blocks : cap), 256, 0, s>>>(x, out, n);
+    return cudaGetLastError();
+}
 
 // The kernels that evaporate come in one variant per level density (SimParams.level_density:
 // the Fermi gas, or the constant-temperature composite), so that the option's code is not in

@@ -15,6 +15,7 @@
 #include <cooperative_groups.h>
 #include <cstddef>
 
+#include "expfixed.h"
 #include "fpconv.h"
 #include "pnuc_internal.h"
 
@@ -1126,13 +1127,14 @@ __device__ __forceinline__ W as_width(R x)
 
 // FP32 mode, widths in FP64: the channel parameters (x, a, b, w0) come in FP32; the
 // exponential e^x and the closed forms F, G are assembled in FP64 (e^x reaches e^160,
-// beyond FP32's range); the series below x = 1 needs no exponential and runs in FP32.
+// beyond FP32's range), the exponential on the integer pipes (expfixed.h); the series below
+// x = 1 needs no exponential and runs in FP32.
 __device__ __forceinline__ double channel_width_f32_d(const ChanP<float> &c)
 {
     const float x = c.x;
     double F, G;
     if (x >= 1.f) {
-        const double ex = exp(f2d(x));
+        const double ex = x < 256.f ? exp_fixed(x) : exp(f2d(x));
         F = ex * f2d(x * x - 3.f * x + 3.f) + f2d(0.5f * x * x) - 3.0;
         G = ex * f2d(x - 1.f) + 1.0;
     } else {

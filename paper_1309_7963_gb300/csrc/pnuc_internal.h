@@ -96,6 +96,9 @@ int occupancy_sorted_fp32(int block, bool count);
 size_t sorted_stack_bytes_fp64();
 size_t sorted_stack_bytes_fp32();
 
+// The FP32 mode's double-precision width exponential on n float arguments (kernel_fp32.cu).
+cudaError_t launch_width_exp(const float *x, double *out, uint64_t n, int sm_count, cudaStream_t s);
+
 // Pipe microbenchmarks (microbench.cu): FP32 FMA, FP64 FMA, MUFU, INT32 MAD lane ops/s.
 cudaError_t measure_peaks(int sm_count, double out[4]);
 

@@ -126,6 +126,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_simulate_host.argtypes = [vp, C.c_int, C.c_int, vp, vp, u64, u64, u64, vp, u64, C.POINTER(u64), vp, vp]
     L.pnuc_simulate_host_noalloc.argtypes = [vp, C.c_int, C.c_int, vp, vp, u64, u64, u64, vp, u64, C.POINTER(u64),
                                              vp, vp]
+    L.pnuc_width_exp.argtypes = [vp, vp, vp, u64, vp]
     L.pnuc_get_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
     L.pnuc_set_tuning.argtypes = [vp, C.c_int, C.POINTER(pnuc_tuning)]
     L.pnuc_measure_peaks.argtypes = [vp, C.POINTER(pnuc_peaks)]
@@ -260,6 +261,17 @@ class Context:
         cur.update(kw)
         t = pnuc_tuning(**cur)
         self._check(self.lib.pnuc_set_tuning(self.handle, PRECISION[precision], C.byref(t)))
+
+    def width_exp(self, x):
+        """pnuc_width_exp: the FP32 mode's double-precision width exponential of a float32 CUDA
+        tensor (e^x for x in [1, 256), -1 elsewhere), as a float64 tensor."""
+        torch = self._torch
+        x = x.contiguous()
+        assert x.dtype == torch.float32 and x.is_cuda
+        out = torch.empty(x.shape, dtype=torch.float64, device=x.device)
+        self._check(self.lib.pnuc_width_exp(self.handle, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                            x.numel(), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        return out
 
     def measure_peaks(self) -> dict:
         """Lane operations per second of the FP32 FMA, FP64 FMA, MUFU and INT32 MAD pipes."""
