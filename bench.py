@@ -242,13 +242,16 @@ def serving_bench(ctx, seconds: float = 3.0) -> dict:
             n_req = max(40, int(rate * seconds))
             reqs = inputs.serving_requests(n_req, rate_hz=rate, seed=200 + int(100 * load))
             srv.reset_stats()
+            srv.trace(True)
             r = driver.run(srv, reqs, tids, seed=7)
+            srv.trace(False)
             st = srv.stats()
+            where = driver.attribute(srv.trace_read())
             runs.append({"load": load, "offered_events_per_s": rate * mean_events, "requests": r["requests"],
                          "events_per_s": r["events_per_s"], "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"],
                          "max_ms": r["max_ms"], "server_p50_ms": st["latency_p50_ms"],
                          "server_p99_ms": st["latency_p99_ms"], "queue_p99_ms": st["queue_p99_ms"],
-                         "reruns": st["reruns"]})
+                         "reruns": st["reruns"], "latency_phases": where})
         return {"capacity_events_per_s": capacity, "mean_request_events": mean_events,
                 "config": "Poisson arrivals, 1e3-1e5 events log-uniform, 20-250 MeV, 12C/16O/40Ca/48Ti/56Fe, "
                           "16 streams, 2 GiB arenas, FP32; capacity from a burst of 256 requests; same-seed "

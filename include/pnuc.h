@@ -385,6 +385,29 @@ pnuc_status pnuc_server_reset_stats(pnuc_server *server);
 /* Drops queued requests, waits for those in flight, frees everything. Safe on NULL. */
 pnuc_status pnuc_server_destroy(pnuc_server *server);
 
+/* Per-request trace of the serving loop (measurement support; the paper has no counterpart),
+ * to attribute latency to the queue, the host, the GPU or the client. pnuc_server_trace(S, 1)
+ * clears the record and records one entry per request released from then on (up to 2^20);
+ * pnuc_server_trace(S, 0) stops and keeps the record. Times are milliseconds on the host's
+ * steady clock from the trace's start; the GPU times (CUDA events on the request's stream,
+ * at the start of its launch's first copy and after its last one) are put on that clock by an
+ * event the device records when the trace starts (aligned to a few tens of microseconds).
+ * A request that ran more than once (an overflow re-run) carries its last launch. */
+typedef struct {
+    uint64_t ticket, events, launch; /* launch: the server's launch number of the request's run */
+    int32_t stream, group_requests;  /* its stream and the requests merged into that launch */
+    int32_t reruns, status;
+    double t_submit, t_admit;        /* submitted; admitted into a launch (first admission) */
+    double t_launched;               /* the launch's copies and kernels enqueued (host) */
+    double t_gpu_start, t_gpu_end;   /* the launch ran on the GPU from .. to */
+    double t_complete;               /* the server saw the launch complete */
+    double t_release;                /* the client released or fetched the request */
+} pnuc_server_trace_entry;
+pnuc_status pnuc_server_trace(pnuc_server *server, int32_t enable);
+/* Copies up to capacity entries (in release order) to out and their total to *count. */
+pnuc_status pnuc_server_trace_read(pnuc_server *server, pnuc_server_trace_entry *out, uint64_t capacity,
+                                   uint64_t *count);
+
 /* Yield tallies of a batch (paper §4.1, Figs. 1-2: secondary yields per energy and angle;
  * §4.2: yields of positron emitters, i.e. of residual nuclei, per incident energy). One pass
  * over the output records on the device, accumulated (+=) into caller-owned device

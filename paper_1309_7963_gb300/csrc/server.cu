@@ -92,6 +92,7 @@ struct Request {
     const pnuc_secondary *sec_view = nullptr;
     int reruns = 0;
     Clock::time_point t_submit, t_admit, t_done;
+    pnuc_server_trace_entry tr{};  // the trace fields of its last run
 };
 
 auto up = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -126,6 +127,9 @@ struct GroupLayout {
 
 struct Group {
     uint64_t id;
+    uint64_t launch = 0;            // the server's launch number
+    bool traced = false;            // its stream's timing events were recorded around it
+    Clock::time_point t_launched;   // copies and kernels enqueued
     std::vector<uint64_t> tickets;  // segment order
     uint64_t n = 0, cap = 0;
     size_t dev_off = 0, host_off = 0, dev_bytes = 0, host_bytes = 0;
@@ -188,9 +192,46 @@ struct pnuc_server {
     std::vector<double> latencies_ms, queue_ms;
     uint64_t completed = 0, events_done = 0, failed = 0, reruns = 0, launches = 0;
     Clock::time_point t_start;
+    // pnuc_server_trace: timing events per stream (start and end of its launch), the epoch
+    // event, its host time, and the entries
+    bool tracing = false;
+    std::vector<cudaEvent_t> ev_start, ev_end;
+    cudaEvent_t epoch = nullptr;
+    Clock::time_point t_epoch;
+    std::vector<pnuc_server_trace_entry> trace;
 };
 
 namespace {
+
+// Trace times: milliseconds from the trace's start on the host clock; a GPU event's time from
+// its distance to the epoch event.
+double trace_ms(const pnuc_server *S, Clock::time_point t)
+{
+    return std::chrono::duration<double, std::milli>(t - S->t_epoch).count();
+}
+
+double gpu_ms(const pnuc_server *S, cudaEvent_t e)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, S->epoch, e) != cudaSuccess) return -1.0;
+    return ms;
+}
+
+// A request leaves the server: its trace entry (if tracing) goes to the record.
+void record_release(pnuc_server *S, Request &r)
+{
+    if (!S->tracing || S->trace.size() >= (1u << 20) || r.tr.launch == 0) return;
+    pnuc_server_trace_entry e = r.tr;
+    e.ticket = r.ticket;
+    e.events = r.n;
+    e.reruns = r.reruns;
+    e.status = r.status;
+    e.t_submit = trace_ms(S, r.t_submit);
+    e.t_admit = trace_ms(S, r.t_admit);
+    e.t_complete = trace_ms(S, r.t_done);
+    e.t_release = trace_ms(S, Clock::now());
+    S->trace.push_back(e);
+}
 
 // Drops a request's claim on its group; frees the group's host region when none is left.
 void leave_group(pnuc_server *S, Request &r)
@@ -331,8 +372,10 @@ bool admit(pnuc_server *S)
     for (int j = 0; j < k; ++j) S->pending.pop_front();
     cudaStream_t s = S->streams[si];
     pnuc_status st = PNUC_OK;
+    const bool traced = S->tracing;
+    if (traced && cudaEventRecord(S->ev_start[si], s) != cudaSuccess) st = PNUC_ERR_CUDA;
     static_assert(sizeof(pnuc_residual) >= 13, "inputs are staged in the residual area");
-    if (cudaMemcpyAsync(d + L.e, h_in, 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+    if (st != PNUC_OK || cudaMemcpyAsync(d + L.e, h_in, 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d + L.t, h_in + 8 * n, 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         (any_proj && cudaMemcpyAsync(d + L.pj, h_in + 12 * n, n, cudaMemcpyHostToDevice, s) != cudaSuccess) ||
         cudaMemcpyAsync(d + GroupLayout::seg_start, h + GroupLayout::seg_start,
@@ -369,9 +412,13 @@ bool admit(pnuc_server *S)
     // the counts come back in stream order behind the kernels (the records are already in the
     // host region), so one completion event covers the whole group
     if (st == PNUC_OK && (cudaMemcpyAsync(h, d, GroupLayout::seg_start, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                          (traced && cudaEventRecord(S->ev_end[si], s) != cudaSuccess) ||
                           cudaEventRecord(S->events[si], s) != cudaSuccess))
         st = PNUC_ERR_CUDA;
     S->launches++;
+    g->launch = S->launches;
+    g->traced = traced;
+    g->t_launched = Clock::now();
     const uint64_t gid = g->id;
     S->groups[gid] = std::move(g);
     if (st != PNUC_OK) {
@@ -429,6 +476,14 @@ void complete(pnuc_server *S, Group &g)
         r.count = cnt;
         r.res_view = (const pnuc_residual *)(h + L.host_r) + seg_start[j];
         r.sec_view = (const pnuc_secondary *)(h + L.host_s) + cap_start[j];
+        if (S->tracing && g.traced) {
+            r.tr.launch = g.launch;
+            r.tr.stream = g.stream;
+            r.tr.group_requests = (int32_t)tickets.size();
+            r.tr.t_launched = trace_ms(S, g.t_launched);
+            r.tr.t_gpu_start = gpu_ms(S, S->ev_start[g.stream]);
+            r.tr.t_gpu_end = gpu_ms(S, S->ev_end[g.stream]);
+        }
         finish(S, r, kDone, PNUC_OK);
     }
     for (auto it = again.rbegin(); it != again.rend(); ++it) S->pending.push_front(*it);
@@ -528,6 +583,9 @@ pnuc_status pnuc_server_destroy(pnuc_server *S)
     for (auto s : S->streams) cudaStreamSynchronize(s);
     for (auto s : S->streams) cudaStreamDestroy(s);
     for (auto e : S->events) cudaEventDestroy(e);
+    for (auto e : S->ev_start) cudaEventDestroy(e);
+    for (auto e : S->ev_end) cudaEventDestroy(e);
+    if (S->epoch) cudaEventDestroy(S->epoch);
     cudaFree(S->dev);
     cudaFreeHost(S->host);
     delete S;
@@ -575,11 +633,15 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg_in, 
             return fail(ctx, PNUC_ERR_CUDA, "stream creation failed");
         }
         S->streams.push_back(s);
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+            cudaEventCreate(&e1) != cudaSuccess) {
             pnuc_server_destroy(S);
             return fail(ctx, PNUC_ERR_CUDA, "event creation failed");
         }
         S->events.push_back(e);
+        S->ev_start.push_back(e0);
+        S->ev_end.push_back(e1);
         S->stream_owner.push_back(0);
     }
     S->worker = std::thread(scheduler, S);
@@ -673,6 +735,7 @@ pnuc_status pnuc_server_fetch(pnuc_server *S, uint64_t ticket, pnuc_secondary *s
     if (!residuals || (r->count > 0 && (!secondaries || capacity < r->count))) return PNUC_ERR_CAPACITY;
     memcpy(residuals, r->res_view, sizeof(pnuc_residual) * r->n);
     if (r->count) memcpy(secondaries, r->sec_view, sizeof(pnuc_secondary) * r->count);
+    record_release(S, *r);
     leave_group(S, *r);
     S->reqs.erase(it);
     S->cv.notify_all();
@@ -707,6 +770,7 @@ pnuc_status pnuc_server_release(pnuc_server *S, uint64_t ticket)
     if (it == S->reqs.end()) return PNUC_ERR_ARG;
     Request *r = it->second.get();
     if (r->state != kDone && r->state != kFailed) return PNUC_ERR_STATE;
+    record_release(S, *r);
     leave_group(S, *r);
     S->reqs.erase(it);
     S->cv.notify_all();
@@ -733,6 +797,35 @@ pnuc_status pnuc_server_get_stats(pnuc_server *S, pnuc_server_stats *out)
     out->events_per_s = secs > 0 ? S->events_done / secs : 0.0;
     out->arena_peak_bytes = std::max(S->dev_arena->peak(), S->host_arena->peak());
     out->launches = S->launches;
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_server_trace(pnuc_server *S, int32_t enable)
+{
+    if (!S) return PNUC_ERR_ARG;
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (!enable) {
+        S->tracing = false;
+        return PNUC_OK;
+    }
+    CU(S->ctx, cudaSetDevice(S->ctx->cfg.device));
+    if (!S->epoch) CU(S->ctx, cudaEventCreate(&S->epoch));
+    // the epoch: an event the device passes now, and the host time it was passed
+    CU(S->ctx, cudaEventRecord(S->epoch, S->streams[0]));
+    CU(S->ctx, cudaEventSynchronize(S->epoch));
+    S->t_epoch = Clock::now();
+    S->trace.clear();
+    S->tracing = true;
+    return PNUC_OK;
+}
+
+pnuc_status pnuc_server_trace_read(pnuc_server *S, pnuc_server_trace_entry *out, uint64_t capacity, uint64_t *count)
+{
+    if (!S || !count || (capacity && !out)) return PNUC_ERR_ARG;
+    std::lock_guard<std::mutex> lock(S->mu);
+    const uint64_t n = std::min<uint64_t>(capacity, S->trace.size());
+    if (n) memcpy(out, S->trace.data(), n * sizeof(pnuc_server_trace_entry));
+    *count = S->trace.size();
     return PNUC_OK;
 }
 

@@ -79,5 +79,39 @@ def run(server: Server, requests: list, target_ids: np.ndarray, seed: int, keep=
                 max_ms=float(lat.max()))
 
 
+PHASES = ("queue", "host_launch", "gpu_wait", "gpu_run", "detect", "client")
+
+
+def phase_times(trace: np.ndarray) -> dict:
+    """Per request (pnuc_server_trace entries), the milliseconds of each phase of its latency:
+    queue (submit to admission), host_launch (admission to its launch enqueued), gpu_wait (to
+    the GPU starting it), gpu_run (the launch on the GPU), detect (to the server seeing it
+    complete), client (to the client's release)."""
+    t = trace
+    return {"queue": t["t_admit"] - t["t_submit"], "host_launch": t["t_launched"] - t["t_admit"],
+            "gpu_wait": t["t_gpu_start"] - t["t_launched"], "gpu_run": t["t_gpu_end"] - t["t_gpu_start"],
+            "detect": t["t_complete"] - t["t_gpu_end"], "client": t["t_release"] - t["t_complete"]}
+
+
+def attribute(trace: np.ndarray, slow_ms: float = 20.0) -> dict:
+    """Where the latency of the slow requests (submit to release above slow_ms) went: for each
+    phase, how many slow requests it dominated and its mean over them; and each phase's p50 and
+    p99 over all requests."""
+    if len(trace) == 0:
+        return {}
+    ph = phase_times(trace)
+    total = trace["t_release"] - trace["t_submit"]
+    slow = total > slow_ms
+    stack = np.stack([ph[k] for k in PHASES], 1)
+    dom = np.argmax(stack, 1)
+    out = {"requests": int(len(trace)), "slow_ms": slow_ms, "slow": int(slow.sum()),
+           "dominant": {k: int(((dom == i) & slow).sum()) for i, k in enumerate(PHASES)},
+           "mean_in_slow_ms": {k: float(ph[k][slow].mean()) if slow.any() else 0.0 for k in PHASES},
+           "p50_ms": {k: float(np.percentile(ph[k], 50)) for k in PHASES},
+           "p99_ms": {k: float(np.percentile(ph[k], 99)) for k in PHASES},
+           "max_ms": {k: float(ph[k].max()) for k in PHASES}}
+    return out
+
+
 def make_requests(n_requests: int, rate_hz: float, seed: int = 0):
     return inputs.serving_requests(n_requests, rate_hz, seed=seed)

@@ -55,6 +55,12 @@ class pnuc_output(C.Structure):
                 ("residuals", C.c_void_p), ("counters", C.c_void_p)]
 
 
+TRACE_DTYPE = np.dtype([("ticket", "<u8"), ("events", "<u8"), ("launch", "<u8"), ("stream", "<i4"),
+                        ("group_requests", "<i4"), ("reruns", "<i4"), ("status", "<i4"), ("t_submit", "<f8"),
+                        ("t_admit", "<f8"), ("t_launched", "<f8"), ("t_gpu_start", "<f8"), ("t_gpu_end", "<f8"),
+                        ("t_complete", "<f8"), ("t_release", "<f8")])
+
+
 class pnuc_tuning(C.Structure):
     _fields_ = [("block_size", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_threshold", C.c_int32),
                 ("chunk", C.c_int32), ("kin_batch", C.c_int32)]
@@ -151,6 +157,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_server_fetch.argtypes = [vp, u64, vp, u64, vp]
     L.pnuc_server_view.argtypes = [vp, u64, C.POINTER(vp), C.POINTER(u64), C.POINTER(vp)]
     L.pnuc_server_release.argtypes = [vp, u64]
+    L.pnuc_server_trace.argtypes = [vp, i32]
+    L.pnuc_server_trace_read.argtypes = [vp, vp, u64, C.POINTER(u64)]
     L.pnuc_server_get_stats.argtypes = [vp, C.POINTER(pnuc_server_stats)]
     L.pnuc_server_reset_stats.argtypes = [vp]
     L.pnuc_server_destroy.argtypes = [vp]
@@ -520,6 +528,20 @@ class Server:
     def release(self, ticket: int):
         self.ctx._check(self.lib.pnuc_server_release(self.handle, ticket))
         self.n_events.pop(ticket, None)
+
+    def trace(self, enable: bool) -> None:
+        """pnuc_server_trace: start (clearing) or stop the per-request trace."""
+        self.ctx._check(self.lib.pnuc_server_trace(self.handle, 1 if enable else 0))
+
+    def trace_read(self) -> np.ndarray:
+        """The trace entries (TRACE_DTYPE), in release order."""
+        n = C.c_uint64(0)
+        self.ctx._check(self.lib.pnuc_server_trace_read(self.handle, None, 0, C.byref(n)))
+        out = np.zeros(n.value, TRACE_DTYPE)
+        if n.value:
+            self.ctx._check(self.lib.pnuc_server_trace_read(self.handle, C.c_void_p(out.ctypes.data), n.value,
+                                                            C.byref(n)))
+        return out
 
     def stats(self) -> dict:
         st = pnuc_server_stats()

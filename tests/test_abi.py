@@ -70,7 +70,8 @@ def test_python_mirrors_match_the_header(tmp_path):
     mirrors = {name: getattr(pnuc, name) for name in (
         "pnuc_config", "pnuc_batch", "pnuc_output", "pnuc_tuning", "pnuc_target_info", "pnuc_peaks",
         "pnuc_tally_spec", "pnuc_server_config", "pnuc_server_stats")}
-    dtypes = {"pnuc_secondary": pnuc.SECONDARY_DTYPE, "pnuc_residual": pnuc.RESIDUAL_DTYPE}
+    dtypes = {"pnuc_secondary": pnuc.SECONDARY_DTYPE, "pnuc_residual": pnuc.RESIDUAL_DTYPE,
+              "pnuc_server_trace_entry": pnuc.TRACE_DTYPE}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pnuc.h"', "int main(void) {"]
     for name, cls in mirrors.items():
         lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')

@@ -265,3 +265,32 @@ def test_inflight_cap_still_serves_every_request(ctx):
         assert srv.stats()["completed"] == len(reqs)
     finally:
         srv.close()
+
+
+def test_trace_orders_each_requests_phases(ctx):
+    """pnuc_server_trace: one entry per released request, whose times follow the request
+    through the server (submit, admission, launch enqueued, GPU start and end, completion seen,
+    release; the GPU times aligned to the host clock within a fraction of a millisecond), and
+    whose phases add up to its latency."""
+    tids = serving_tids(ctx)
+    reqs = inputs.serving_requests(40, rate_hz=2000.0, seed=12, min_batch=1000, max_batch=30_000)
+    srv = pnuc.Server(ctx, precision="fp32", streams=4, arena_bytes=512 << 20)
+    try:
+        srv.trace(True)
+        driver.run(srv, reqs, tids, seed=5)
+        srv.trace(False)
+        tr = srv.trace_read()
+    finally:
+        srv.close()
+    assert len(tr) == len(reqs) and np.all(tr["status"] == 0) and np.all(tr["launch"] > 0)
+    slack = 0.5  # ms: alignment of the device clock to the host's
+    assert np.all(tr["t_submit"] <= tr["t_admit"]) and np.all(tr["t_admit"] <= tr["t_launched"])
+    assert np.all(tr["t_gpu_start"] <= tr["t_gpu_end"])
+    assert np.all(tr["t_gpu_start"] >= tr["t_admit"] - slack)
+    assert np.all(tr["t_gpu_end"] <= tr["t_complete"] + slack)
+    assert np.all(tr["t_complete"] <= tr["t_release"])
+    ph = driver.phase_times(tr)
+    total = sum(ph[k] for k in driver.PHASES)
+    assert np.allclose(total, tr["t_release"] - tr["t_submit"], atol=1e-6)
+    where = driver.attribute(tr, slow_ms=0.0)
+    assert where["slow"] == len(tr) and sum(where["dominant"].values()) == len(tr)
