@@ -175,6 +175,7 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
     p.n_targets = (int32_t)ctx->targets.size();
     p.mass = ctx->mass;
     p.cbrtA = ctx->cbrtA;
+    p.ct_table = ctx->ct_table;
     p.max_steps = ctx->cfg.max_steps;
     p.max_attempts = ctx->cfg.max_attempts;
     p.max_evap_steps = ctx->cfg.max_evap_steps;
@@ -311,11 +312,13 @@ pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
         if (cudaMalloc(&ctx->mass, sizeof(double) * kMassZ * kMassA) != cudaSuccess ||
             cudaMalloc(&ctx->cbrtA, sizeof(double) * kMassA) != cudaSuccess ||
             cudaMalloc(&ctx->tables, sizeof(TargetTable) * kMaxTargets) != cudaSuccess ||
-            cudaMalloc(&ctx->queue, sizeof(unsigned long long) * kQueueSlots * kQueueStride) != cudaSuccess) {
+            cudaMalloc(&ctx->queue, sizeof(unsigned long long) * kQueueSlots * kQueueStride) != cudaSuccess ||
+            cudaMalloc(&ctx->ct_table, sizeof(double) * kMassA * kCtStride) != cudaSuccess) {
             st = PNUC_ERR_CUDA;
             break;
         }
-        if (launch_mass_table(ctx->mass, ctx->cbrtA, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        if (launch_mass_table(ctx->mass, ctx->cbrtA, 0) != cudaSuccess || launch_ct_table(ctx->ct_table, 0) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess) {
             st = PNUC_ERR_CUDA;
             break;
         }
@@ -343,6 +346,7 @@ pnuc_status pnuc_destroy(pnuc_ctx *ctx)
     cudaSetDevice(ctx->cfg.device);
     cudaFree(ctx->mass);
     cudaFree(ctx->cbrtA);
+    cudaFree(ctx->ct_table);
     cudaFree(ctx->tables);
     cudaFree(ctx->queue);
     cudaFree(ctx->h_energies);

@@ -25,6 +25,7 @@ struct pnuc_ctx {
     char err[512] = {0};
     double *mass = nullptr;              // [kMassZ * kMassA]
     double *cbrtA = nullptr;             // [kMassA]
+    double *ct_table = nullptr;          // [kMassA * kCtStride] reading M26's constants
     pnuc::TargetTable *tables = nullptr;  // [kMaxTargets]
     std::vector<std::pair<int, int>> targets;
     unsigned long long *queue = nullptr;  // [kQueueSlots * kQueueStride]

@@ -949,14 +949,15 @@ __device__ R sample_t(Stream<R> &rng, R a, R x, R b, int max_trials, int &trials
 // and kL max(u1, u2) (weight (kL)^2 / 2), kept with probability e^-t. Fermi-gas part:
 // sample_t()'s trial on [0, x], kept if t < x - x_x (U above U_x). Returns U, or -1 after
 // max_trials.
-__device__ double width_integral_ct(double a, double Y, double b, double *ct_part);
+__device__ double width_integral_ct(const double *T, double a, double Y, double b, double *ct_part);
 
+// T: the daughter's row of M26's constant table (SimParams.ct_table)
 template <typename R>
-__device__ R sample_U_ct(Stream<R> &rng, R a, R Y, R b, R x, int max_trials, int &trials)
+__device__ R sample_U_ct(Stream<R> &rng, const double *T, R a, R Y, R b, R x, int max_trials, int &trials)
 {
-    const R Ux = R(2.5) + R(150.0) / (R(8.0) * a), k = sqrt(a / Ux), xx = R(2) * sqrt(a * Ux);
+    const R Ux = to_R<R>(__ldg(&T[0])), k = to_R<R>(__ldg(&T[1])), xx = R(2) * sqrt(a * Ux);
     double ict;
-    const double itot = width_integral_ct(to_d<R>(a), to_d<R>(Y), to_d<R>(b), &ict);
+    const double itot = width_integral_ct(T, to_d<R>(a), to_d<R>(Y), to_d<R>(b), &ict);
     if (to_d<R>(rng.next()) * itot < ict) {
         const R L = Y < Ux ? Y : Ux, kL = k * L, c0 = k * (Y + b - L);
         const bool small = kL < R(2);
@@ -1067,7 +1068,12 @@ __device__ __forceinline__ void width_FG(double x, double &F, double &G)
 // Reading M26 (the option pnuc_config.level_density = 1): the daughter's level density is
 // constant-temperature below U_x = 2.5 + 150/A_d MeV (A_d = 8a) and M20's Fermi gas above,
 // joined in value and slope at U_x: exp(sqrt(a U_x) + U / T) with 1/T = sqrt(a / U_x).
-__device__ __forceinline__ double ct_matching_energy(double a) { return 2.5 + 150.0 / (8.0 * a); }
+// The daughter's row of the constant table (tables.cu, built with the context): U_x, k = 1/T,
+// C = e^{sqrt(a U_x)}, e^{k U_x} - 1, e^{k U_x} - 1 - k U_x, G(x_x), H(x_x); a = A_d / 8.
+__device__ __forceinline__ const double *ct_row(const double *table, double a)
+{
+    return table + kCtStride * (int)(8.0 * a + 0.5);
+}
 
 // e^z - 1 - z, by series below z = 1/2
 __device__ double expm1_minus(double z)
@@ -1086,18 +1092,22 @@ __device__ double expm1_minus(double z)
 // part over [0, L], L = min(Y, U_x), is C [(Y + b - L)(e^{kL} - 1)/k + (e^{kL} - 1 - kL)/k^2]
 // (k = 1/T, C = e^{sqrt(a U_x)}); above U_x, M20's integral over [0, Y] less the same
 // integrand over [0, U_x], (Y + b) G(x_x)/(2a) - H(x_x)/(8a^2), x_x = 2 sqrt(a U_x),
-// H(x) = e^x (x^3 - 3x^2 + 6x - 6) + 6. The constant-temperature part goes to *ct_part.
-__device__ double width_integral_ct(double a, double Y, double b, double *ct_part)
+// H(x) = e^x (x^3 - 3x^2 + 6x - 6) + 6. The constant-temperature part goes to *ct_part. What
+// depends only on the daughter comes from its row T of the constant table, so that a width
+// takes one exponential at most (e^{kY} below U_x, M20's e^x above).
+__device__ double width_integral_ct(const double *T, double a, double Y, double b, double *ct_part)
 {
-    const double Ux = ct_matching_energy(a), k = sqrt(a / Ux), xx = 2.0 * sqrt(a * Ux);
-    const double L = Y < Ux ? Y : Ux, kL = k * L;
-    const double ict = exp(0.5 * xx) * ((Y + b - L) * expm1(kL) / k + expm1_minus(kL) / (k * k));
+    const double Ux = __ldg(&T[0]), k = __ldg(&T[1]), C = __ldg(&T[2]);
+    double ict;
+    if (Y < Ux) {
+        const double kL = k * Y;
+        ict = C * ((Y + b - Y) * expm1(kL) / k + expm1_minus(kL) / (k * k));
+    } else {
+        ict = C * ((Y + b - Ux) * __ldg(&T[3]) / k + __ldg(&T[4]) / (k * k));
+    }
     *ct_part = ict;
     if (!(Y > Ux)) return ict;
-    const double ex = exp(xx);
-    const double Gx = ex * (xx - 1.0) + 1.0;
-    const double Hx = ex * (((xx - 3.0) * xx + 6.0) * xx - 6.0) + 6.0;
-    const double below = (Y + b) * Gx / (2.0 * a) - Hx / (8.0 * a * a);
+    const double below = (Y + b) * __ldg(&T[5]) / (2.0 * a) - __ldg(&T[6]) / (8.0 * a * a);
     double F, G;
     width_FG(2.0 * sqrt(a * Y), F, G);
     return ict + ((F / (4.0 * a * a) + b * G / (2.0 * a)) - below);
@@ -1125,19 +1135,24 @@ __device__ __forceinline__ W as_width(R x)
     else return to_d<R>(x);
 }
 
-// FP32 mode, widths in FP64: the channel parameters (x, a, b, w0) come in FP32; the
-// exponential e^x and the closed forms F, G are assembled in FP64 (e^x reaches e^160,
-// beyond FP32's range), the exponential on the integer pipes (expfixed.h); the series below
-// x = 1 needs no exponential and runs in FP32.
+// FP32 mode, widths in FP64: the channel parameters (x, a, b, w0) come in FP32, and so do the
+// factors of the closed forms: with F = e^x (x^2 - 3x + 3) + x^2/2 - 3 and G = e^x (x - 1) + 1,
+// the width w0 (F/(4a^2) + b G/(2a)) is w0 (e^x A1 + A0) with A1 = (x^2 - 3x + 3)/(4a^2) +
+// b (x - 1)/(2a) and A0 = (x^2/2 - 3)/(4a^2) + b/(2a), both FP32; the exponential (up to e^160,
+// beyond FP32's range, and computed on the integer pipes, expfixed.h) and the two products
+// that carry it are FP64. The series below x = 1 needs no exponential and runs in FP32.
 __device__ __forceinline__ double channel_width_f32_d(const ChanP<float> &c)
 {
     const float x = c.x;
-    double F, G;
     if (x >= 1.f) {
         const double ex = x < 256.f ? exp_fixed(x) : exp(f2d(x));
-        F = ex * f2d(x * x - 3.f * x + 3.f) + f2d(0.5f * x * x) - 3.0;
-        G = ex * f2d(x - 1.f) + 1.0;
-    } else {
+        const float ia = 1.f / c.a, q = 0.25f * ia * ia, h = 0.5f * c.b * ia;
+        const float A1 = (x * x - 3.f * x + 3.f) * q + (x - 1.f) * h;
+        const float A0 = (0.5f * x * x - 3.f) * q + h;
+        return f2d(c.w0) * (ex * f2d(A1) + f2d(A0));
+    }
+    double F, G;
+    {
         float term = x, f = 0.f, g = 0.f;  // term = x^n / n!
 #pragma unroll 1
         for (int n = 2; n <= 20; ++n) {
@@ -1160,13 +1175,14 @@ __device__ __forceinline__ double channel_width_f32_d(const ChanP<float> &c)
 __device__ float channel_width_scaled(const ChanP<float> &c, float xm);
 
 template <typename R, bool kScaled, bool kCT = false>
-__device__ width_t<R, kScaled> channel_width(const ChanP<R> &c, R xm)
+__device__ width_t<R, kScaled> channel_width(const ChanP<R> &c, R xm, const double *ct_table)
 {
     static_assert(!(kScaled && kCT), "the scaled FP32 widths take the Fermi-gas level density");
     if constexpr (kCT) {  // M26, FP64 in both modes
         if (!c.open) return 0.0;
         double part;
-        return to_d<R>(c.w0) * width_integral_ct(to_d<R>(c.a), to_d<R>(c.Y), to_d<R>(c.b), &part);
+        const double a = to_d<R>(c.a);
+        return to_d<R>(c.w0) * width_integral_ct(ct_row(ct_table, a), a, to_d<R>(c.Y), to_d<R>(c.b), &part);
     } else if constexpr (sizeof(R) == 8) {
         if (!c.open) return 0.0;
         double F, G;
@@ -1345,7 +1361,8 @@ __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const 
     int trials = 0;
     double Ud;
     if constexpr (kCT) {
-        const R u = sample_U_ct<R>(L.rng, c.a, c.Y, c.b, c.x, P.max_evap_trials, trials);
+        const R u = sample_U_ct<R>(L.rng, ct_row(P.ct_table, to_d<R>(c.a)), c.a, c.Y, c.b, c.x, P.max_evap_trials,
+                                   trials);
         Ud = u < R(0) ? -1.0 : to_d<R>(u);
     } else {
         const R tt = sample_t<R>(L.rng, c.a, c.x, c.b, P.max_evap_trials, trials);
@@ -1395,7 +1412,7 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
     }
     const R xm = kScaled ? widths_xm<R>(chans) : R(0);
 #pragma unroll 1
-    for (int j = 0; j < 6; ++j) G[j] = channel_width<R, kScaled, kCT>(chans[j], xm);
+    for (int j = 0; j < 6; ++j) G[j] = channel_width<R, kScaled, kCT>(chans[j], xm, P.ct_table);
     evap_emit<R, kScaled, kCT, kCount>(P, L, Mparent, G, C);
 }
 
@@ -1410,7 +1427,7 @@ struct WidthJob {
 constexpr int kWidthSlots = 6 * 32;  // per warp: six channels of every lane
 
 template <typename R, bool kScaled, bool kCT>
-__device__ __forceinline__ width_t<R, kScaled> job_width(const WidthJob<R> &jb, R xm)
+__device__ __forceinline__ width_t<R, kScaled> job_width(const WidthJob<R> &jb, R xm, const double *ct_table)
 {
     ChanP<R> c;
     c.open = true;
@@ -1419,7 +1436,7 @@ __device__ __forceinline__ width_t<R, kScaled> job_width(const WidthJob<R> &jb, 
     c.b = jb.b;
     c.w0 = jb.w0;
     c.Y = jb.Y;
-    return channel_width<R, kScaled, kCT>(c, xm);
+    return channel_width<R, kScaled, kCT>(c, xm, ct_table);
 }
 
 // One evaporation step of every lane of the warp with `active` set (the evaporation kernel).
@@ -1480,11 +1497,11 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
     __syncwarp();
     for (int k = lane; k < nexp; k += 32) {
         const WidthJob<R> jb = jobs[k];
-        gw[jb.tag] = job_width<R, kScaled, kCT>(jb, xms[jb.tag / 6]);
+        gw[jb.tag] = job_width<R, kScaled, kCT>(jb, xms[jb.tag / 6], P.ct_table);
     }
     for (int k = kWidthSlots - 1 - (int)lane; k >= kWidthSlots - nser; k -= 32) {
         const WidthJob<R> jb = jobs[k];
-        gw[jb.tag] = job_width<R, kScaled, kCT>(jb, xms[jb.tag / 6]);
+        gw[jb.tag] = job_width<R, kScaled, kCT>(jb, xms[jb.tag / 6], P.ct_table);
     }
     __syncwarp();
     if (active) evap_emit<R, kScaled, kCT, kCount>(P, L, Mparent, G, C);

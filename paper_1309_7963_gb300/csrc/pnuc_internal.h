@@ -14,6 +14,7 @@ constexpr int kMaxTargets = 16;  // targets per context
 constexpr int kStackCap = 64;    // particles waiting in one event's cascade
 constexpr int kMassZ = 102;      // nuclide table covers Z in [0, 101]
 constexpr int kMassA = 252;      //                     and A in [0, 251]
+constexpr int kCtStride = 8;     // doubles per daughter in the table of reading M26's constants
 
 // One target's shell table in precision R (paper §2.2). Index [0] = neutrons, [1] = protons.
 template <typename R>
@@ -64,6 +65,7 @@ struct SimParams {
     int32_t n_targets;
     const double *mass;            // [kMassZ * kMassA] SEMF masses, MeV (0 where undefined)
     const double *cbrtA;           // [kMassA] A^(1/3)
+    const double *ct_table;        // [kMassA * kCtStride] reading M26's constants per daughter A
     unsigned long long *queue_head;  // persistent method: next unclaimed event of the cascade kernel
     unsigned long long *evap_head;   // persistent method: next unclaimed event of the evaporation kernel
     int32_t split_evap;              // 1: persistent method (the cascade kernel leaves evaporation to evap_kernel)
@@ -104,6 +106,7 @@ cudaError_t measure_peaks(int sm_count, double out[4]);
 
 // Table builders (tables.cu).
 cudaError_t launch_mass_table(double *mass, double *cbrtA, cudaStream_t s);
+cudaError_t launch_ct_table(double *tab, cudaStream_t s);
 cudaError_t launch_target_table(TargetTable *dst, int Z, int A, const double *mass, cudaStream_t s);
 
 }  // namespace pnuc

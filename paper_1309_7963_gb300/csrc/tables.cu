@@ -32,6 +32,30 @@ __global__ void mass_table_kernel(double *mass, double *cbrtA)
     mass[idx] = (A >= 1 && Z <= A) ? semf(Z, A) : 0.0;
 }
 
+// Reading M26's constants of a daughter of mass number A (a = A/8; the level density is
+// constant-temperature below the matching energy U_x = 2.5 + 150/A MeV): U_x, k = 1/T =
+// sqrt(a / U_x), C = e^{sqrt(a U_x)}, e^{k U_x} - 1, e^{k U_x} - 1 - k U_x (k U_x >= 4.3 for
+// A >= 5, so no series is needed), and with x_x = 2 sqrt(a U_x) the Fermi-gas integrals below
+// U_x, G(x_x) = e^x_x (x_x - 1) + 1 and H(x_x) = e^x_x (x_x^3 - 3 x_x^2 + 6 x_x - 6) + 6.
+__global__ void ct_table_kernel(double *tab)
+{
+    const int A = blockIdx.x * blockDim.x + threadIdx.x;
+    if (A >= kMassA) return;
+    double *t = tab + kCtStride * A;
+    for (int k = 0; k < kCtStride; ++k) t[k] = 0.0;
+    if (A < 5) return;
+    const double a = A / 8.0;
+    const double Ux = 2.5 + 150.0 / (8.0 * a), k = sqrt(a / Ux), xx = 2.0 * sqrt(a * Ux), kU = k * Ux;
+    const double ex = exp(xx);
+    t[0] = Ux;
+    t[1] = k;
+    t[2] = exp(0.5 * xx);
+    t[3] = expm1(kU);
+    t[4] = expm1(kU) - kU;
+    t[5] = ex * (xx - 1.0) + 1.0;
+    t[6] = ex * (((xx - 3.0) * xx + 6.0) * xx - 6.0) + 6.0;
+}
+
 __device__ double fermi_density(double r, double c) { return 1.0 / (1.0 + exp((r - c) / 0.545)); }
 
 // One block of 15 warps: warp i integrates r^2 f(r) over shell i, each lane one 1/32 of it
@@ -108,6 +132,12 @@ __global__ void target_table_kernel(TargetTable *dst, int Z, int A, const double
 }
 
 }  // namespace
+
+cudaError_t launch_ct_table(double *tab, cudaStream_t s)
+{
+    ct_table_kernel<<<1, 256, 0, s>>>(tab);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mass_table(double *mass, double *cbrtA, cudaStream_t s)
 {
