@@ -389,10 +389,12 @@ pnuc_status pnuc_server_destroy(pnuc_server *server);
  * to attribute latency to the queue, the host, the GPU or the client. pnuc_server_trace(S, 1)
  * clears the record and records one entry per request released from then on (up to 2^20);
  * pnuc_server_trace(S, 0) stops and keeps the record. Times are milliseconds on the host's
- * steady clock from the trace's start; the GPU times (CUDA events on the request's stream,
- * at the start of its launch's first copy and after its last one) are put on that clock by an
- * event the device records when the trace starts (aligned to a few tens of microseconds).
- * A request that ran more than once (an overflow re-run) carries its last launch. */
+ * steady clock from the trace's start; the GPU times (the GPU's global timer, stamped by a
+ * one-warp kernel on the request's stream before its launch's first copy and after its last
+ * one) are put on that clock by a stamp taken when the trace starts (aligned to a few tens of
+ * microseconds). The stamps are plain kernels, so tracing leaves the streams' concurrency as
+ * it is (CUDA events with timing enabled did not: they raised the median latency 3-fold). A
+ * request that ran more than once (an overflow re-run) carries its last launch. */
 typedef struct {
     uint64_t ticket, events, launch; /* launch: the server's launch number of the request's run */
     int32_t stream, group_requests;  /* its stream and the requests merged into that launch */

@@ -106,9 +106,11 @@ struct GroupLayout {
     // header: [0] launch count, [8 .. 8+8*kMaxSeg) per-request counts (device -> host), then
     // the segment tables (host -> device): seg_start (u32, kMaxSeg + 1), seg_first (u64,
     // kMaxSeg), cap_start (u64, kMaxSeg + 1)
+    // the trace's GPU time stamps of the launch (start, end; nanoseconds of the GPU's global
+    // timer, written by stamp_kernel into the host region)
     static constexpr size_t count = 0, seg_count = 8, seg_start = 8 + 8 * kMaxSeg, seg_first = 1024,
-                            cap_start = seg_first + 8 * kMaxSeg, header = 2304;
-    static_assert(seg_start + 4 * (kMaxSeg + 1) <= seg_first && cap_start + 8 * (kMaxSeg + 1) <= header,
+                            cap_start = seg_first + 8 * kMaxSeg, stamps = 2288, header = 2304;
+    static_assert(seg_start + 4 * (kMaxSeg + 1) <= seg_first && cap_start + 8 * (kMaxSeg + 1) <= stamps,
                   "group header fields overlap");
     size_t e, t, pj, s, dev_total, host_r, host_s, host_total;
     GroupLayout(uint64_t n, uint64_t cap, int n_seg)
@@ -137,6 +139,16 @@ struct Group {
     int stream = -1;
     int live = 0;  // requests not yet released: the host region is freed at 0
 };
+
+// The trace's GPU time stamp: the GPU's global timer (nanoseconds) when the stream reaches it.
+__global__ void stamp_kernel(unsigned long long *dst)
+{
+    if (threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        *dst = t;
+    }
+}
 
 // Partition of a merged launch's secondaries: record i of event e (segment k) goes to
 // out[cap_start[k] + (its rank in segment k)], with its event renumbered e - seg_start[k].
@@ -192,29 +204,27 @@ struct pnuc_server {
     std::vector<double> latencies_ms, queue_ms;
     uint64_t completed = 0, events_done = 0, failed = 0, reruns = 0, launches = 0;
     Clock::time_point t_start;
-    // pnuc_server_trace: timing events per stream (start and end of its launch), the epoch
-    // event, its host time, and the entries
+    // pnuc_server_trace: the epoch (its host time and GPU global timer, read through a pinned
+    // word), and the entries
     bool tracing = false;
-    std::vector<cudaEvent_t> ev_start, ev_end;
-    cudaEvent_t epoch = nullptr;
     Clock::time_point t_epoch;
+    unsigned long long gpu_epoch_ns = 0;
+    unsigned long long *epoch_word = nullptr;  // pinned, mapped
     std::vector<pnuc_server_trace_entry> trace;
 };
 
 namespace {
 
-// Trace times: milliseconds from the trace's start on the host clock; a GPU event's time from
-// its distance to the epoch event.
+// Trace times: milliseconds from the trace's start on the host clock; a GPU stamp's time from
+// its distance to the epoch's stamp.
 double trace_ms(const pnuc_server *S, Clock::time_point t)
 {
     return std::chrono::duration<double, std::milli>(t - S->t_epoch).count();
 }
 
-double gpu_ms(const pnuc_server *S, cudaEvent_t e)
+double gpu_ms(const pnuc_server *S, unsigned long long ns)
 {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, S->epoch, e) != cudaSuccess) return -1.0;
-    return ms;
+    return 1e-6 * (double)(long long)(ns - S->gpu_epoch_ns);
 }
 
 // A request leaves the server: its trace entry (if tracing) goes to the record.
@@ -373,7 +383,11 @@ bool admit(pnuc_server *S)
     cudaStream_t s = S->streams[si];
     pnuc_status st = PNUC_OK;
     const bool traced = S->tracing;
-    if (traced && cudaEventRecord(S->ev_start[si], s) != cudaSuccess) st = PNUC_ERR_CUDA;
+    unsigned char *hd = S->host_dev + hoff;  // the host region, as the kernels address it
+    if (traced) {
+        stamp_kernel<<<1, 32, 0, s>>>((unsigned long long *)(hd + GroupLayout::stamps));
+        if (cudaGetLastError() != cudaSuccess) st = PNUC_ERR_CUDA;
+    }
     static_assert(sizeof(pnuc_residual) >= 13, "inputs are staged in the residual area");
     if (st != PNUC_OK || cudaMemcpyAsync(d + L.e, h_in, 8 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemcpyAsync(d + L.t, h_in + 8 * n, 4 * n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
@@ -382,7 +396,6 @@ bool admit(pnuc_server *S)
                         GroupLayout::header - GroupLayout::seg_start, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(d + GroupLayout::seg_count, 0, 8 * kMaxSeg, s) != cudaSuccess)
         st = PNUC_ERR_CUDA;
-    unsigned char *hd = S->host_dev + hoff;  // the host region, as the kernels address it
     pnuc_batch b = {(const double *)(d + L.e), (const int32_t *)(d + L.t), n, cand[0]->seed, cand[0]->first,
                     any_proj ? (const uint8_t *)(d + L.pj) : nullptr, nullptr};
     pnuc_secondary *launch_sec = k > 1 ? (pnuc_secondary *)(d + L.s) : (pnuc_secondary *)(hd + L.host_s);
@@ -411,10 +424,13 @@ bool admit(pnuc_server *S)
     }
     // the counts come back in stream order behind the kernels (the records are already in the
     // host region), so one completion event covers the whole group
-    if (st == PNUC_OK && (cudaMemcpyAsync(h, d, GroupLayout::seg_start, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-                          (traced && cudaEventRecord(S->ev_end[si], s) != cudaSuccess) ||
-                          cudaEventRecord(S->events[si], s) != cudaSuccess))
+    if (st == PNUC_OK && cudaMemcpyAsync(h, d, GroupLayout::seg_start, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         st = PNUC_ERR_CUDA;
+    if (st == PNUC_OK && traced) {
+        stamp_kernel<<<1, 32, 0, s>>>((unsigned long long *)(hd + GroupLayout::stamps + 8));
+        if (cudaGetLastError() != cudaSuccess) st = PNUC_ERR_CUDA;
+    }
+    if (st == PNUC_OK && cudaEventRecord(S->events[si], s) != cudaSuccess) st = PNUC_ERR_CUDA;
     S->launches++;
     g->launch = S->launches;
     g->traced = traced;
@@ -481,8 +497,9 @@ void complete(pnuc_server *S, Group &g)
             r.tr.stream = g.stream;
             r.tr.group_requests = (int32_t)tickets.size();
             r.tr.t_launched = trace_ms(S, g.t_launched);
-            r.tr.t_gpu_start = gpu_ms(S, S->ev_start[g.stream]);
-            r.tr.t_gpu_end = gpu_ms(S, S->ev_end[g.stream]);
+            const volatile unsigned long long *ts = (const volatile unsigned long long *)(h + GroupLayout::stamps);
+            r.tr.t_gpu_start = gpu_ms(S, ts[0]);
+            r.tr.t_gpu_end = gpu_ms(S, ts[1]);
         }
         finish(S, r, kDone, PNUC_OK);
     }
@@ -583,9 +600,7 @@ pnuc_status pnuc_server_destroy(pnuc_server *S)
     for (auto s : S->streams) cudaStreamSynchronize(s);
     for (auto s : S->streams) cudaStreamDestroy(s);
     for (auto e : S->events) cudaEventDestroy(e);
-    for (auto e : S->ev_start) cudaEventDestroy(e);
-    for (auto e : S->ev_end) cudaEventDestroy(e);
-    if (S->epoch) cudaEventDestroy(S->epoch);
+    if (S->epoch_word) cudaFreeHost(S->epoch_word);
     cudaFree(S->dev);
     cudaFreeHost(S->host);
     delete S;
@@ -633,15 +648,11 @@ pnuc_status pnuc_server_create(pnuc_ctx *ctx, const pnuc_server_config *cfg_in, 
             return fail(ctx, PNUC_ERR_CUDA, "stream creation failed");
         }
         S->streams.push_back(s);
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
-            cudaEventCreate(&e1) != cudaSuccess) {
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
             pnuc_server_destroy(S);
             return fail(ctx, PNUC_ERR_CUDA, "event creation failed");
         }
         S->events.push_back(e);
-        S->ev_start.push_back(e0);
-        S->ev_end.push_back(e1);
         S->stream_owner.push_back(0);
     }
     S->worker = std::thread(scheduler, S);
@@ -809,11 +820,21 @@ pnuc_status pnuc_server_trace(pnuc_server *S, int32_t enable)
         return PNUC_OK;
     }
     CU(S->ctx, cudaSetDevice(S->ctx->cfg.device));
-    if (!S->epoch) CU(S->ctx, cudaEventCreate(&S->epoch));
-    // the epoch: an event the device passes now, and the host time it was passed
-    CU(S->ctx, cudaEventRecord(S->epoch, S->streams[0]));
-    CU(S->ctx, cudaEventSynchronize(S->epoch));
-    S->t_epoch = Clock::now();
+    if (!S->epoch_word)
+        CU(S->ctx, cudaHostAlloc((void **)&S->epoch_word, 64, cudaHostAllocMapped));
+    unsigned long long *word_dev = nullptr;
+    CU(S->ctx, cudaHostGetDevicePointer((void **)&word_dev, S->epoch_word, 0));
+    // the epoch: a stamp of the GPU's global timer on a stream with nothing before it, and the
+    // host time halfway through its launch and synchronisation
+    cudaStream_t s0 = S->streams[0];
+    CU(S->ctx, cudaStreamSynchronize(s0));
+    const Clock::time_point before = Clock::now();
+    stamp_kernel<<<1, 32, 0, s0>>>(word_dev);
+    CU(S->ctx, cudaGetLastError());
+    CU(S->ctx, cudaStreamSynchronize(s0));
+    const Clock::time_point after = Clock::now();
+    S->gpu_epoch_ns = *(volatile unsigned long long *)S->epoch_word;
+    S->t_epoch = before + (after - before) / 2;
     S->trace.clear();
     S->tracing = true;
     return PNUC_OK;

@@ -5,6 +5,7 @@ result, reads it in place (zero-copy views of the server's pinned arena) and rel
 a transport code would before it continues its histories."""
 from __future__ import annotations
 
+import gc
 import threading
 import time
 
@@ -14,13 +15,16 @@ from . import inputs
 from .pnuc import PnucError, Server
 
 
-def run(server: Server, requests: list, target_ids: np.ndarray, seed: int, keep=None, time_limit_s: float = 120.0):
+def run(server: Server, requests: list, target_ids: np.ndarray, seed: int, keep=None, time_limit_s: float = 120.0,
+        pause_gc: bool = True):
     """Plays `requests` against `server` in real time. target_ids maps the workload's target
     index to the context's target id. keep(request, secondaries, residuals) is called for
     each result if given, with views valid only during the call (copy what you keep).
     Results are taken in the order they finish (pnuc_server_wait_any), as a transport code
-    continues whichever histories are ready. Returns client-side latencies (ms, submit to
-    release) and throughput."""
+    continues whichever histories are ready. Python's cyclic garbage collector is paused while
+    the requests play (pause_gc): a full collection in a process that has loaded torch holds
+    every thread for tens of milliseconds, which the trace showed as 30-36 ms client stalls.
+    Returns client-side latencies (ms, submit to release) and throughput."""
     done = {}
     meta = {}  # ticket -> (request, submit time)
     lock = threading.Condition()
@@ -46,6 +50,9 @@ def run(server: Server, requests: list, target_ids: np.ndarray, seed: int, keep=
             with lock:
                 done[tk] = (t_sub, time.perf_counter(), req["energies"].shape[0])
 
+    gc_was_on = gc.isenabled()
+    if pause_gc:
+        gc.disable()
     th = threading.Thread(target=consumer, daemon=True)
     th.start()
     for req in requests:
@@ -70,6 +77,8 @@ def run(server: Server, requests: list, target_ids: np.ndarray, seed: int, keep=
         lock.notify_all()
     th.join()
     wall = time.perf_counter() - t0
+    if pause_gc and gc_was_on:
+        gc.enable()
     lat = np.array([(b - a) * 1e3 for a, b, _ in done.values()])
     events = sum(n for _, _, n in done.values())
     first = min(a for a, _, _ in done.values())
