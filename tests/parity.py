@@ -150,7 +150,67 @@ def observable_table(gres, gsec, ores, osec, n):
     good = (ores["flags"] & 48) == 0
     row["mean_Estar_cascade"] = {"fp32": float(gres["Estar_cascade"][good].mean()),
                                  "oracle": float(ores["Estar_c"][good].mean())}
+    row["paired"] = paired_table(gsec, osec, n)
     return row
+
+
+def paired_table(gsec, osec, n):
+    """Paired comparison of the same events: FP32 and FP64 draw the same random numbers, so an
+    event's records match one to one unless rounding changed a decision. Per species and origin:
+    the fraction of events whose count of it differs, the two-sided sign-test p-value of those
+    differences (rounding flips decisions either way; a bias moves counts one way) with the net
+    relative difference of the totals (the bias's size), and over
+    the events whose ordered (species, origin) lists are identical, the median relative
+    difference of the matched records' kinetic energies (FP32 rounding leaves it near 1e-7; a
+    bias shifts it)."""
+    from scipy import stats
+    gs = pnuc.sort_secondaries(gsec) if gsec.dtype == pnuc.SECONDARY_DTYPE else gsec
+    os_ = osec[np.lexsort((osec["index"], osec["event"]))]
+    cg_all = np.bincount(gs["event"], minlength=n)
+    co_all = np.bincount(os_["event"], minlength=n)
+    eq = cg_all == co_all
+    # events with equal record counts: their records line up one to one in (event, index) order
+    ag, ao = gs[eq[gs["event"]]], os_[eq[os_["event"]]]
+    differ = (ag["species"].astype(np.int64) != ao["species"]) | (ag["origin"].astype(np.int64) != ao["origin"])
+    same = eq & (np.bincount(ag["event"][differ], minlength=n) == 0)
+    out = {"same_signature": float(same.mean()), "count_mismatch": {}, "count_sign_p": {}, "count_bias": {},
+           "median_rel_T": {}}
+    keep = same[ag["event"]]
+    mg, mo = ag[keep], ao[keep]
+    for origin, label in ((0, "cascade"), (1, "evaporated")):
+        for sp, sname in enumerate(SPECIES):
+            og = (os_["species"] == sp) & (os_["origin"] == origin)
+            if og.sum() < 50:
+                continue
+            gg = (gs["species"] == sp) & (gs["origin"] == origin)
+            cg = np.bincount(gs["event"][gg], minlength=n)
+            co = np.bincount(os_["event"][og], minlength=n)
+            key = f"{label} {sname}"
+            out["count_mismatch"][key] = float(np.mean(cg != co))
+            more, fewer = int(np.sum(cg > co)), int(np.sum(cg < co))
+            out["count_sign_p"][key] = float(stats.binomtest(more, more + fewer).pvalue) if more + fewer else 1.0
+            out["count_bias"][key] = float((cg.sum() - co.sum()) / co.sum())
+            sel = (mo["species"] == sp) & (mo["origin"] == origin)
+            tg, to = mg["T"][sel].astype(np.float64), mo["T"][sel].astype(np.float64)
+            rel = (tg - to) / np.maximum(np.abs(to), 1e-3)
+            out["median_rel_T"][key] = float(np.median(rel)) if len(rel) else 0.0
+    return out
+
+
+def assert_paired(p, name):
+    """The paired bounds: 99% of events with identical (species, origin) lists; each species'
+    count different in at most 0.2% of events, and no multiplicity bias that is both significant
+    (one-sided differences, sign test p < 1e-3) and above 0.1% of the total; the median relative
+    energy difference of the matched records below 1e-4. (Over millions of events the sign test
+    resolves the FP32 mode's own rounding bias, about 1e-4 of a multiplicity, which the 0.1%
+    bound admits.)"""
+    assert p["same_signature"] >= 0.99, (name, p["same_signature"])
+    for k, v in p["count_mismatch"].items():
+        assert v <= 0.002, (name, "count_mismatch", k, v)
+    for k, v in p["count_sign_p"].items():
+        assert v > 1e-3 or abs(p["count_bias"][k]) <= 1e-3, (name, "count bias", k, v, p["count_bias"][k])
+    for k, v in p["median_rel_T"].items():
+        assert abs(v) < 1e-4, (name, "median_rel_T", k, v)
 
 
 def assert_observables(row, name):
@@ -163,3 +223,4 @@ def assert_observables(row, name):
         for k, p in row[field].items():
             assert p > 0.01, (name, field, k, p)
     assert row["residual_ZA_p"] > 0.01, (name, row["residual_ZA_p"])
+    assert_paired(row["paired"], name)

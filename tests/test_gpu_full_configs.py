@@ -95,6 +95,7 @@ def test_plain_fp32_o16_ca40_2e6_against_the_oracle(ctx):
     assert ok.mean() > 0.995 and good[ok].all()
     orc = oracle.simulate_parallel(w.targets, w.energies, w.tidx, seed=w.seed)
     row = observable_table(res, sec, orc["residuals"], orc["secondaries"], w.n)
+    record("full size: p-16O + p-40Ca 200 MeV, 2e6 events, plain FP32 kernel", row)
     assert_observables(row, "plain fp32 2e6")
     assert row["residual_ZA_identical"] > 0.99
 

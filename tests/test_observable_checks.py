@@ -1,9 +1,10 @@
 """The statistical checks the FP32-mode tests apply (tests/parity.py: multiplicities and mean
-kinetic energies within 3 standard errors, chi-square and Kolmogorov-Smirnov p > 0.01) have
-the power to see plausible mistakes: on the CPU, oracle results recast as the library's
-records pass against themselves (kinetic energies and directions rounded as the FP32 records
-store them) and fail once a mistake is planted in the copy: a 2% energy scale, a mirrored
-angular distribution, lost emissions."""
+kinetic energies within 3 standard errors, chi-square and Kolmogorov-Smirnov p > 0.01, and the
+paired comparison of the same events' records) have the power to see plausible mistakes: on
+the CPU, oracle results recast as the library's records pass against themselves (kinetic
+energies and directions rounded as the FP32 records store them) and fail once a mistake is
+planted in the copy: a 2% or a 0.5% energy scale, a mirrored angular distribution, lost
+emissions, and one in five of the rare tritons or 3He dropped."""
 import numpy as np
 import pytest
 
@@ -49,13 +50,21 @@ def planted(ca40, how):
     elif how == "mirrored angles":
         sel = (gsec["species"] == 0) & (gsec["origin"] == 0)  # cascade neutrons backwards
         gsec["uz"][sel] = -gsec["uz"][sel]
+    elif how == "half-percent energy scale":
+        sel = (gsec["species"] == 1) & (gsec["origin"] == 1)  # evaporated protons 0.5% hot
+        gsec["T"][sel] *= 1.005
     elif how == "lost emissions":
         alpha = np.flatnonzero((gsec["species"] == 5) & (gsec["origin"] == 1))
         gsec = np.delete(gsec, alpha[::5])  # every fifth evaporated alpha dropped
+    elif how in ("lost tritons", "lost 3He"):
+        sp = 3 if how == "lost tritons" else 4
+        rare = np.flatnonzero((gsec["species"] == sp) & (gsec["origin"] == 1))
+        gsec = np.delete(gsec, rare[::5])  # every fifth evaporated t (3He) dropped
     return observable_table(gres, gsec, res, sec, n)
 
 
-@pytest.mark.parametrize("how", ["energy scale", "mirrored angles", "lost emissions"])
+@pytest.mark.parametrize("how", ["energy scale", "half-percent energy scale", "mirrored angles", "lost emissions",
+                                 "lost tritons", "lost 3He"])
 def test_planted_mistakes_fail(ca40, how):
     with pytest.raises(AssertionError):
         assert_observables(planted(ca40, how), how)
