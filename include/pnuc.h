@@ -170,7 +170,8 @@ typedef struct {
     int32_t refill_threshold; /* a warp refills when at least this many lanes are idle (1..32) */
     int32_t chunk;            /* most events a warp takes from the queue per atomic (32 .. 2^20); claims
                                  shrink towards 32 as the queue drains */
-    int32_t kin_batch;        /* accepted collisions a warp gathers before their FP64 kinematics (1..32) */
+    int32_t kin_batch;        /* accepted collisions a warp gathers before their FP64 kinematics (1..32);
+                                 a batch also runs once as many lanes wait as would run transport */
 } pnuc_tuning;
 
 typedef struct pnuc_ctx pnuc_ctx;

@@ -176,6 +176,7 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
     p.mass = ctx->mass;
     p.cbrtA = ctx->cbrtA;
     p.ct_table = ctx->ct_table;
+    p.qval = ctx->qval;
     p.max_steps = ctx->cfg.max_steps;
     p.max_attempts = ctx->cfg.max_attempts;
     p.max_evap_steps = ctx->cfg.max_evap_steps;
@@ -313,12 +314,13 @@ pnuc_status pnuc_create(const pnuc_config *cfg_in, pnuc_ctx **out)
             cudaMalloc(&ctx->cbrtA, sizeof(double) * kMassA) != cudaSuccess ||
             cudaMalloc(&ctx->tables, sizeof(TargetTable) * kMaxTargets) != cudaSuccess ||
             cudaMalloc(&ctx->queue, sizeof(unsigned long long) * kQueueSlots * kQueueStride) != cudaSuccess ||
-            cudaMalloc(&ctx->ct_table, sizeof(double) * kMassA * kCtStride) != cudaSuccess) {
+            cudaMalloc(&ctx->ct_table, sizeof(double) * kMassA * kCtStride) != cudaSuccess ||
+            cudaMalloc(&ctx->qval, sizeof(double) * kMassZ * kMassA * kQStride) != cudaSuccess) {
             st = PNUC_ERR_CUDA;
             break;
         }
         if (launch_mass_table(ctx->mass, ctx->cbrtA, 0) != cudaSuccess || launch_ct_table(ctx->ct_table, 0) != cudaSuccess ||
-            cudaDeviceSynchronize() != cudaSuccess) {
+            launch_q_table(ctx->qval, ctx->mass, 0) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
             st = PNUC_ERR_CUDA;
             break;
         }
@@ -347,6 +349,7 @@ pnuc_status pnuc_destroy(pnuc_ctx *ctx)
     cudaFree(ctx->mass);
     cudaFree(ctx->cbrtA);
     cudaFree(ctx->ct_table);
+    cudaFree(ctx->qval);
     cudaFree(ctx->tables);
     cudaFree(ctx->queue);
     cudaFree(ctx->h_energies);

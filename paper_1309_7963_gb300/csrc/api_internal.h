@@ -26,6 +26,7 @@ struct pnuc_ctx {
     double *mass = nullptr;              // [kMassZ * kMassA]
     double *cbrtA = nullptr;             // [kMassA]
     double *ct_table = nullptr;          // [kMassA * kCtStride] reading M26's constants
+    double *qval = nullptr;              // [kMassZ * kMassA * kQStride] evaporation Q-values
     pnuc::TargetTable *tables = nullptr;  // [kMaxTargets]
     std::vector<std::pair<int, int>> targets;
     unsigned long long *queue = nullptr;  // [kQueueSlots * kQueueStride]

@@ -53,7 +53,8 @@ cudaError_t launch_plain_fp32(const SimParams &p, int block, bool count, bool sc
 cudaError_t launch_persistent_fp32(const SimParams &p, int grid, int block, bool count, cudaStream_t s)
 {
     if (count) return dev::launch_persistent<float, true>(p, grid, block, s);
-    return dev::launch_kernel(dev::persistent_kernel_f32, dev::smem_bytes<float>(p.n_targets, block), p, grid, block, s);
+    return dev::launch_kernel(dev::persistent_kernel_f32, dev::persistent_smem_bytes<float>(p.n_targets, block), p, grid,
+                              block, s);
 }
 cudaError_t launch_evap_fp32(const SimParams &p, int grid, int block, bool count, bool scaled, cudaStream_t s)
 {
@@ -96,7 +97,7 @@ int occupancy_evap_fp32(int block, bool count, bool scaled, bool ct)
 int occupancy_persistent_fp32(int block, bool count)
 {
     if (count) return dev::occupancy_persistent<float, true>(block);
-    return dev::occupancy_of(dev::persistent_kernel_f32, dev::smem_bytes<float>(kMaxTargets, block), block);
+    return dev::occupancy_of(dev::persistent_kernel_f32, dev::persistent_smem_bytes<float>(kMaxTargets, block), block);
 }
 
 }  // namespace pnuc

@@ -30,12 +30,13 @@ constexpr double kMp = 938.272, kMn = 939.565;
 constexpr double kTwoPi = 6.283185307179586;
 
 // ejectiles n, p, d, t, 3He, alpha (§2.4: He and lighter)
-__constant__ double cEjM[6] = {939.565, 938.272, 1875.613, 2808.921, 2808.391, 3727.379};
+__constant__ double cEjM[6] = {kEjectileMass[0], kEjectileMass[1], kEjectileMass[2],
+                               kEjectileMass[3], kEjectileMass[4], kEjectileMass[5]};
 __constant__ double cEjG[6] = {2.0, 2.0, 3.0, 2.0, 2.0, 1.0};
 __constant__ float cEjMf[6] = {939.565f, 938.272f, 1875.613f, 2808.921f, 2808.391f, 3727.379f};
 __constant__ float cEjGf[6] = {2.f, 2.f, 3.f, 2.f, 2.f, 1.f};
-__constant__ int cEjZ[6] = {0, 1, 1, 1, 2, 2};
-__constant__ int cEjA[6] = {1, 1, 2, 3, 3, 4};
+__constant__ int cEjZ[6] = {kEjectileZ[0], kEjectileZ[1], kEjectileZ[2], kEjectileZ[3], kEjectileZ[4], kEjectileZ[5]};
+__constant__ int cEjA[6] = {kEjectileA[0], kEjectileA[1], kEjectileA[2], kEjectileA[3], kEjectileA[4], kEjectileA[5]};
 
 // kKinWait: an accepted candidate waits for its collision kinematics (batched per warp).
 enum Phase : int { kIdle = 0, kEntry = 1, kTransport = 2, kEvap = 3, kFinish = 4, kExhausted = 5, kKinWait = 6 };
@@ -151,6 +152,10 @@ template <typename R> __device__ __forceinline__ R dot3(const R *a, const R *b) 
 template <typename R> __device__ __forceinline__ R kinetic(R p2, R m) { return p2 / (sqrt(p2 + m * m) + m); }
 __device__ __forceinline__ double nucleon_mass(int s) { return s ? kMp : kMn; }
 template <typename R> __device__ __forceinline__ R nucleon_mass_R(int s) { return s ? R(kMp) : R(kMn); }
+// u^(1/3) for a uniform u in (0, 1): cbrt in FP64; in FP32 2^(log2(u) / 3) from the hardware
+// base-2 logarithm and exponential (relative error of order 1e-7), in place of the library cbrtf
+template <typename R> __device__ __forceinline__ R cbrt_uniform(R u) { return cbrt(u); }
+template <> __device__ __forceinline__ float cbrt_uniform<float>(float u) { return exp2f(log2f(u) * (1.f / 3.f)); }
 
 // Conversions: in FP32 mode on the integer pipes (fpconv.h), in FP64 mode plain casts.
 template <typename R> __device__ __forceinline__ R to_R(double x) { return (R)x; }
@@ -409,6 +414,16 @@ struct Counters {
     }
 };
 
+// The 32-byte secondary record (pnuc_secondary) as two 16-byte halves.
+__device__ __forceinline__ void pack_secondary(uint32_t ev, int species, int origin, int index, double T, float ux,
+                                               float uy, float uz, uint4 &a, uint4 &b)
+{
+    const unsigned long long tbits = (unsigned long long)__double_as_longlong(T);
+    a = make_uint4(ev, (uint32_t)species | ((uint32_t)origin << 8) | ((uint32_t)index << 16), (uint32_t)tbits,
+                   (uint32_t)(tbits >> 32));
+    b = make_uint4(__float_as_uint(ux), __float_as_uint(uy), __float_as_uint(uz), 0u);
+}
+
 // Warp-aggregated reservation of one output slot per calling lane: one atomic per
 // converged group, then 2 x 16-byte stores of the 32-byte record.
 __device__ __forceinline__ void emit_secondary(const SimParams &P, uint32_t ev, int species, int origin, int index,
@@ -423,14 +438,65 @@ __device__ __forceinline__ void emit_secondary(const SimParams &P, uint32_t ev, 
         flags |= PNUC_FLAG_OUTPUT_OVERFLOW;
         return;
     }
-    unsigned long long tbits = (unsigned long long)__double_as_longlong(T);
-    uint4 a = make_uint4(ev, (uint32_t)species | ((uint32_t)origin << 8) | ((uint32_t)index << 16),
-                         (uint32_t)tbits, (uint32_t)(tbits >> 32));
-    uint4 b = make_uint4(__float_as_uint(ux), __float_as_uint(uy), __float_as_uint(uz), 0u);
+    uint4 a, b;
+    pack_secondary(ev, species, origin, index, T, ux, uy, uz, a, b);
     uint4 *dst = reinterpret_cast<uint4 *>(P.sec + slot);
     dst[0] = a;
     dst[1] = b;
 }
+
+// Emission as the record is made (the plain and sorted methods).
+struct EmitNow {
+    __device__ __forceinline__ void emit(const SimParams &P, uint32_t ev, int species, int origin, int index, double T,
+                                         float ux, float uy, float uz, uint32_t &flags)
+    {
+        emit_secondary(P, ev, species, origin, index, T, ux, uy, uz, flags);
+    }
+};
+
+// Emission in the persistent evaporation kernel, whose lanes emit at most one record per loop
+// iteration. The converged group reserves its slots with one atomic when the record is made,
+// the record waits in the thread's staging slot in shared memory, and store(), at the top of
+// the next iteration, writes it: no warp waits for the atomic's result in the middle of a step
+// (a global atomic on one counter returns after hundreds of cycles; an iteration later it
+// has). A record past the output's capacity flags the lane's event there, before the event's
+// residual is written. The slots are the same dense range [0, count) as with EmitNow.
+struct DeferredEmit {
+    uint4 *stage;             // the thread's two 16-byte halves: stage[0] and stage[stride]
+    int stride;
+    unsigned long long base;  // the group's first slot (held by the group's first lane)
+    uint32_t tag = 0;         // 0: nothing staged; else 1 | first lane << 1 | rank << 6
+    __device__ __forceinline__ void emit(const SimParams &P, uint32_t ev, int species, int origin, int index, double T,
+                                         float ux, float uy, float uz, uint32_t &)
+    {
+        const unsigned m = __activemask(), lane = threadIdx.x & 31;
+        const unsigned first = (unsigned)__ffs(m) - 1u, rank = __popc(m & ((1u << lane) - 1u));
+        if (lane == first) base = atomicAdd(P.sec_count, (unsigned long long)__popc(m));
+        uint4 a, b;
+        pack_secondary(ev, species, origin, index, T, ux, uy, uz, a, b);
+        stage[0] = a;
+        stage[stride] = b;
+        tag = 1u | (first << 1) | (rank << 6);
+    }
+    // called by all 32 lanes of the warp
+    __device__ __forceinline__ void store(const SimParams &P, uint32_t &flags)
+    {
+        const unsigned FULL = 0xffffffffu;
+        if (!__any_sync(FULL, tag != 0)) return;
+        const unsigned long long b = __shfl_sync(FULL, base, (tag >> 1) & 31u);
+        if (tag) {
+            const unsigned long long slot = b + (tag >> 6);
+            if (slot < P.sec_cap) {
+                uint4 *dst = reinterpret_cast<uint4 *>(P.sec + slot);
+                dst[0] = stage[0];
+                dst[1] = stage[stride];
+            } else {
+                flags |= PNUC_FLAG_OUTPUT_OVERFLOW;
+            }
+            tag = 0;
+        }
+    }
+};
 
 // A residual record with a pending evaporation (persistent method, between its two kernels)
 // carries the escape sums at full precision: Esum in Estar_cascade, Pz in Estar_final, Px and
@@ -681,9 +747,9 @@ __device__ __forceinline__ void next_particle(const SimParams &P, const TargetSc
 // One transport step of the particle in flight (§2.3): a path from the majorant rate,
 // then a candidate collision or a boundary crossing. An accepted candidate leaves the
 // lane in kKinWait with its partner stored; finish_collision() completes it.
-template <typename R, bool kCount, bool kSplit>
+template <typename R, bool kCount, bool kSplit, typename Em>
 __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const TargetScalars &tab, Lane<R> &L,
-                               Particle<R> *stack, Counters<kCount> &C)
+                               Particle<R> *stack, Counters<kCount> &C, Em &em)
 {
     if (L.steps >= P.max_steps) {
         // step cap: the particles in flight stay in the nucleus and the event goes on to
@@ -712,7 +778,7 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
         C.add(PNUC_C_CANDIDATES);
         int s2 = (L.rng.next() < t.ZoverA) ? 1 : 0;
         R m2 = nucleon_mass_R<R>(s2);
-        R q = t.pF[s2][i] * cbrt(L.rng.next());
+        R q = t.pF[s2][i] * cbrt_uniform(L.rng.next());
         R ct = R(2) * L.rng.next() - R(1);
         R sn = sqrt((R(1) - ct) * (R(1) + ct));
         R ph = R(kTwoPi) * L.rng.next();
@@ -758,8 +824,8 @@ __device__ void step_transport(const SimParams &P, const ShellTable<R> &t, const
         C.add(PNUC_C_ESCAPES);
         R pn = sqrt(dot3(L.p, L.p));
         const double Toutd = to_d<R>(Tout);
-        emit_secondary(P, L.ev, s1, 0, L.n_index++, Toutd, (float)(L.p[0] / pn), (float)(L.p[1] / pn),
-                       (float)(L.p[2] / pn), L.flags);
+        em.emit(P, L.ev, s1, 0, L.n_index++, Toutd, (float)(L.p[0] / pn), (float)(L.p[1] / pn),
+                (float)(L.p[2] / pn), L.flags);
         L.Esum += Toutd + nucleon_mass(s1);
         L.Px += to_d<R>(L.p[0]);
         L.Py += to_d<R>(L.p[1]);
@@ -789,6 +855,11 @@ __device__ float slope_f(bool like, float p)
 // boost of the pair into its CM frame and back and the products' energies in FP64. The
 // boost is built from E = m + T and the pair's own s = E_t^2 - P^2, so it is an exact
 // Lorentz transformation and conserves the pair's energy and momentum to FP64 rounding.
+// It is written with beta = P / E_t and gamma = E_t / sqrt(s) substituted, so that one
+// reciprocal, D = 1 / (E_t + sqrt(s)), stands for both 1 / E_t and gamma^2 / (gamma + 1):
+//   p_cm  = p + P/sqrt(s) (D P.p - E)          (into the CM frame)
+//   q_lab = k + P/sqrt(s) (D P.k + e)          (back to the lab)
+//   T_lab = (E_t e + P.k) / sqrt(s) - m
 __device__ void collide_mixed(int s1, const float *p1, int s2, const float *p2, float ut, float uphi, float uf,
                               float *q1, float *q2, double &T1n, double &T2n)
 {
@@ -804,12 +875,10 @@ __device__ void collide_mixed(int s1, const float *p1, int s2, const float *p2, 
     const double E1 = m1 + f2d(T1), Et = E1 + (m2 + f2d(T2));
     const double s = Et * Et - dot3(P, P);
     const double irs = rsqrt(s);
-    const double iEt = 1.0 / Et;
-    const double beta[3] = {P[0] * iEt, P[1] * iEt, P[2] * iEt};
-    const double gamma = Et * irs;
-    const double g2 = gamma * gamma / (gamma + 1.0);
-    const double f = g2 * dot3(beta, P1) - gamma * E1;
-    float n[3] = {d2f(P1[0] + beta[0] * f), d2f(P1[1] + beta[1] * f), d2f(P1[2] + beta[2] * f)};
+    const double rs = s * irs;
+    const double D = 1.0 / (Et + rs);
+    const double f = (D * dot3(P, P1) - E1) * irs;
+    float n[3] = {d2f(P1[0] + P[0] * f), d2f(P1[1] + P[1] * f), d2f(P1[2] + P[2] * f)};
     const float rn = rsqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
     n[0] *= rn;
     n[1] *= rn;
@@ -840,17 +909,19 @@ __device__ void collide_mixed(int s1, const float *p1, int s2, const float *p2, 
         d[2] = (n[2] >= 0.f ? 1.f : -1.f) * ct;
     }
     const double K[3] = {pst * f2d(d[0]), pst * f2d(d[1]), pst * f2d(d[2])};
-    const double hs = 0.5 * irs;
-    const double e1 = (s + m1 * m1 - m2 * m2) * hs, e2 = (s + m2 * m2 - m1 * m1) * hs;  // CM energies
-    const double bk = dot3(beta, K);
-    const double f1 = g2 * bk + gamma * e1, f2 = -g2 * bk + gamma * e2;
+    // CM energies: e1 = (s + m1^2 - m2^2) / (2 sqrt(s)), e2 = sqrt(s) - e1
+    constexpr double kDm2 = kMp * kMp - kMn * kMn;
+    const double dm2 = like ? 0.0 : (s1 ? kDm2 : -kDm2);
+    const double e1 = (s + dm2) * (0.5 * irs), e2 = rs - e1;
+    const double PK = dot3(P, K), DPK = D * PK;
+    const double f1 = (DPK + e1) * irs, f2 = (e2 - DPK) * irs;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        q1[c] = d2f(K[c] + beta[c] * f1);
-        q2[c] = d2f(-K[c] + beta[c] * f2);
+        q1[c] = d2f(K[c] + P[c] * f1);
+        q2[c] = d2f(P[c] * f2 - K[c]);
     }
-    T1n = gamma * (e1 + bk) - m1;
-    T2n = gamma * (e2 - bk) - m2;
+    T1n = (Et * e1 + PK) * irs - m1;
+    T2n = (Et * e2 - PK) * irs - m2;
 }
 
 template <typename R>
@@ -999,24 +1070,24 @@ __device__ R sample_U_ct(Stream<R> &rng, const double *T, R a, R Y, R b, R x, in
     return R(-1);
 }
 
-// Channel parameters in precision R (Q-values and daughter masses in FP64).
+// Channel parameters in precision R (the Q-value in FP64).
 template <typename R>
 struct ChanP {
-    double Q, Md;
+    double Q;
     R V, b, a, x, w0;  // barrier, offset, level-density parameter, 2 sqrt(aY), g m c A^(2/3)
     R Y;               // X - V: the range of the daughter's excitation
     bool open;
 };
 
 template <typename R>
-__device__ void channel_params(const SimParams &P, int Z, int A, double Mparent, double Estar, int j, ChanP<R> &c)
+__device__ void channel_params(const SimParams &P, int Z, int A, double Estar, int j, ChanP<R> &c)
 {
     c.open = false;
     c.x = R(0);
     const int Zd = Z - cEjZ[j], Ad = A - cEjA[j];
     if (Zd < 1 || Ad - Zd < 1 || Ad < 5) return;
-    const double Md = __ldg(&P.mass[Zd * kMassA + Ad]);
-    const double Q = Md + cEjM[j] - Mparent;
+    // (M_d + m_j) - M_parent, tabulated per parent with the context (the same FP64 sum)
+    const double Q = __ldg(&P.qval[(size_t)kQStride * (Z * kMassA + A) + j]);
     const R A3 = to_R<R>(__ldg(&P.cbrtA[Ad]));
     R V, b, cj;
     if (cEjZ[j] == 0) {
@@ -1033,7 +1104,6 @@ __device__ void channel_params(const SimParams &P, int Z, int A, double Mparent,
     const R X = to_R<R>(Estar - Q);
     const R Y = X - V;
     c.Q = Q;
-    c.Md = Md;
     c.V = V;
     c.b = b;
     c.a = R(Ad) / R(8);
@@ -1328,9 +1398,9 @@ __device__ __forceinline__ double daughter_excitation<float>(float x, float t, f
 // The second half of an evaporation step (§2.4), given the six channel widths G of the
 // parent (Z, A, E* in L): the channel draw, the emission energy, and the two-body decay
 // isotropic in the parent's rest frame, boosted to the lab.
-template <typename R, bool kScaled, bool kCT, bool kCount>
-__device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const width_t<R, kScaled> *G,
-                          Counters<kCount> &C)
+template <typename R, bool kScaled, bool kCT, bool kCount, typename Em>
+__device__ void evap_emit(const SimParams &P, Lane<R> &L, const width_t<R, kScaled> *G,
+                          Counters<kCount> &C, Em &em)
 {
     using W = width_t<R, kScaled>;
     const int Z = L.Z, A = L.A;
@@ -1357,7 +1427,7 @@ __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const 
                 break;
             }
     ChanP<R> c;  // the chosen channel's parameters, recomputed (the same function of Z, A, E*)
-    channel_params<R>(P, Z, A, Mparent, Estar, ch, c);
+    channel_params<R>(P, Z, A, Estar, ch, c);
     int trials = 0;
     double Ud;
     if constexpr (kCT) {
@@ -1379,8 +1449,10 @@ __device__ void evap_emit(const SimParams &P, Lane<R> &L, double Mparent, const 
     const R phr = R(kTwoPi) * L.rng.next();
     double pl[3], el, Tl;
     float u[3];
-    decay_to_lab(Mparent + Estar, cEjM[ch], c.Md + Ud, eps, ctr, phr, L, pl, el, Tl, u);
-    emit_secondary(P, L.ev, ch, 1, L.n_index++, Tl, u[0], u[1], u[2], L.flags);
+    const double Mparent = __ldg(&P.mass[Z * kMassA + A]);
+    const double Md = __ldg(&P.mass[(Z - cEjZ[ch]) * kMassA + (A - cEjA[ch])]);
+    decay_to_lab(Mparent + Estar, cEjM[ch], Md + Ud, eps, ctr, phr, L, pl, el, Tl, u);
+    em.emit(P, L.ev, ch, 1, L.n_index++, Tl, u[0], u[1], u[2], L.flags);
     ++L.n_evap;
     L.Er -= el;
     L.Prx -= pl[0];
@@ -1402,18 +1474,18 @@ __device__ void step_evap(const SimParams &P, Lane<R> &L, Counters<kCount> &C)
         return;
     }
     C.add(PNUC_C_EVAP_PASSES);
-    const double Mparent = __ldg(&P.mass[L.Z * kMassA + L.A]);
     width_t<R, kScaled> G[6];
     ChanP<R> chans[6];
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) {
-        channel_params<R>(P, L.Z, L.A, Mparent, L.Estar, j, chans[j]);
+        channel_params<R>(P, L.Z, L.A, L.Estar, j, chans[j]);
         if (chans[j].open) C.add(chans[j].x >= R(1) ? PNUC_C_EVAP_EXPS : PNUC_C_EVAP_SERIES);
     }
     const R xm = kScaled ? widths_xm<R>(chans) : R(0);
 #pragma unroll 1
     for (int j = 0; j < 6; ++j) G[j] = channel_width<R, kScaled, kCT>(chans[j], xm, P.ct_table);
-    evap_emit<R, kScaled, kCT, kCount>(P, L, Mparent, G, C);
+    EmitNow em;
+    evap_emit<R, kScaled, kCT, kCount>(P, L, G, C, em);
 }
 
 // ------------------------------------------------------------------ warp-wide widths
@@ -1449,9 +1521,9 @@ __device__ __forceinline__ width_t<R, kScaled> job_width(const WidthJob<R> &jb, 
 // lane), with the lane's scale reference in xms; no per-lane channel records are kept, so
 // nothing of the step lives in local memory. Called by all 32 lanes of the warp; jobs and gw
 // are the warp's kWidthSlots entries, xms its 32.
-template <typename R, bool kScaled, bool kCT, bool kCount>
+template <typename R, bool kScaled, bool kCT, bool kCount, typename Em>
 __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, WidthJob<R> *jobs,
-                               width_t<R, kScaled> *gw, R *xms, Counters<kCount> &C)
+                               width_t<R, kScaled> *gw, R *xms, Counters<kCount> &C, Em &em)
 {
     if (active && L.n_evap >= P.max_evap_steps) {
         L.flags |= PNUC_FLAG_EVAP_STEP_CAP;
@@ -1459,7 +1531,6 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
         active = false;
     }
     const unsigned FULL = 0xffffffffu, lane = threadIdx.x & 31, below = (1u << lane) - 1u;
-    const double Mparent = active ? __ldg(&P.mass[L.Z * kMassA + L.A]) : 0.0;
     width_t<R, kScaled> *G = gw + 6 * lane;
     R xm = R(0);
     int nexp = 0, nser = 0;
@@ -1467,7 +1538,7 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
     for (int j = 0; j < 6; ++j) {
         ChanP<R> c;
         if (active) {
-            channel_params<R>(P, L.Z, L.A, Mparent, L.Estar, j, c);
+            channel_params<R>(P, L.Z, L.A, L.Estar, j, c);
         } else {
             c.open = false;
             c.x = R(0);
@@ -1504,7 +1575,7 @@ __device__ void step_evap_warp(const SimParams &P, Lane<R> &L, bool active, Widt
         gw[jb.tag] = job_width<R, kScaled, kCT>(jb, xms[jb.tag / 6], P.ct_table);
     }
     __syncwarp();
-    if (active) evap_emit<R, kScaled, kCT, kCount>(P, L, Mparent, G, C);
+    if (active) evap_emit<R, kScaled, kCT, kCount>(P, L, G, C, em);
     __syncwarp();  // the lists are reused by the next step
 }
 
@@ -1514,7 +1585,8 @@ __device__ __forceinline__ void step(const SimParams &P, const ShellTable<R> *sh
                                      Particle<R> *stack, Counters<kCount> &C)
 {
     if (L.phase == kTransport) {
-        step_transport<R, kCount, false>(P, sh[L.tgt], tabs[L.tgt], L, stack, C);
+        EmitNow em;
+        step_transport<R, kCount, false>(P, sh[L.tgt], tabs[L.tgt], L, stack, C, em);
     } else if (L.phase == kKinWait) {
         finish_collision<R, kCount, false>(P, sh[L.tgt], tabs[L.tgt], L, stack, C);
     } else if (L.phase == kEntry) {

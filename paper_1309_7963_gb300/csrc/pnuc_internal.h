@@ -15,6 +15,13 @@ constexpr int kStackCap = 64;    // particles waiting in one event's cascade
 constexpr int kMassZ = 102;      // nuclide table covers Z in [0, 101]
 constexpr int kMassA = 252;      //                     and A in [0, 251]
 constexpr int kCtStride = 8;     // doubles per daughter in the table of reading M26's constants
+constexpr int kQStride = 8;      // doubles per parent (Z, A) in the Q-value table (six channels used)
+
+// Evaporated ejectiles n, p, d, t, 3He, alpha (paper §2.4: He and lighter): masses (MeV),
+// charge and mass numbers.
+constexpr double kEjectileMass[6] = {939.565, 938.272, 1875.613, 2808.921, 2808.391, 3727.379};
+constexpr int kEjectileZ[6] = {0, 1, 1, 1, 2, 2};
+constexpr int kEjectileA[6] = {1, 1, 2, 3, 3, 4};
 
 // One target's shell table in precision R (paper §2.2). Index [0] = neutrons, [1] = protons.
 template <typename R>
@@ -66,6 +73,9 @@ struct SimParams {
     const double *mass;            // [kMassZ * kMassA] SEMF masses, MeV (0 where undefined)
     const double *cbrtA;           // [kMassA] A^(1/3)
     const double *ct_table;        // [kMassA * kCtStride] reading M26's constants per daughter A
+    // [kMassZ * kMassA * kQStride] Q-values of the six channels of a parent (Z, A):
+    // (M(Z - z_j, A - a_j) + m_j) - M(Z, A), entry j of row Z * kMassA + A
+    const double *qval;
     unsigned long long *queue_head;  // persistent method: next unclaimed event of the cascade kernel
     unsigned long long *evap_head;   // persistent method: next unclaimed event of the evaporation kernel
     int32_t split_evap;              // 1: persistent method (the cascade kernel leaves evaporation to evap_kernel)
@@ -107,6 +117,7 @@ cudaError_t measure_peaks(int sm_count, double out[4]);
 // Table builders (tables.cu).
 cudaError_t launch_mass_table(double *mass, double *cbrtA, cudaStream_t s);
 cudaError_t launch_ct_table(double *tab, cudaStream_t s);
+cudaError_t launch_q_table(double *q, const double *mass, cudaStream_t s);
 cudaError_t launch_target_table(TargetTable *dst, int Z, int A, const double *mass, cudaStream_t s);
 
 }  // namespace pnuc

@@ -44,13 +44,35 @@ __host__ __device__ constexpr size_t smem_bytes(int n_targets, int block)
     return (table_smem_bytes<R>(n_targets) + 15) / 16 * 16 + (size_t)kRing * sizeof(R) * block;
 }
 
-// the evaporation kernel adds each warp's width-job list after the rings
+// each thread's staging slot of the evaporation kernel's deferred emission (DeferredEmit)
+constexpr size_t kStageBytes = 32;
+
+// the persistent cascade kernel: tables and rings
+template <typename R>
+__host__ __device__ constexpr size_t persistent_smem_bytes(int n_targets, int block)
+{
+    return smem_bytes<R>(n_targets, block);
+}
+
+// the evaporation kernel adds each warp's width-job list after the rings, then the staging slots
 template <typename R, bool kScaled = false>
 __host__ __device__ constexpr size_t evap_smem_bytes(int n_targets, int block)
 {
     return smem_bytes<R>(n_targets, block) +
            (size_t)(block / 32) *
-               (kWidthSlots * (sizeof(WidthJob<R>) + sizeof(width_t<R, kScaled>)) + 32 * sizeof(R));
+               (kWidthSlots * (sizeof(WidthJob<R>) + sizeof(width_t<R, kScaled>)) + 32 * sizeof(R)) +
+           kStageBytes * block;
+}
+
+// the thread's deferred emitter on the staging slots at `at` ([2][blockDim.x] 16-byte halves)
+__device__ __forceinline__ DeferredEmit deferred_emitter(unsigned char *at)
+{
+    DeferredEmit em;
+    em.stage = reinterpret_cast<uint4 *>(at) + threadIdx.x;
+    em.stride = (int)blockDim.x;
+    em.base = 0;
+    em.tag = 0;
+    return em;
 }
 
 template <typename R>
@@ -158,8 +180,8 @@ __device__ __forceinline__ unsigned long long queue_share()
 // Persistent cascade kernel: grid = resident blocks only. When at least refill_threshold lanes
 // of a warp are idle (or none is busy) they take events from the warp's queue reservoir.
 // Accepted collisions wait until kin_batch lanes of the warp need their FP64 kinematics (or
-// nothing else can progress). Events with E* > 0 leave their evaporation pending in the
-// residual record for evap_kernel.
+// as many lanes wait as would run transport). Events with E* > 0 leave their evaporation
+// pending in the residual record for evap_kernel.
 template <typename R, bool kCount>
 __device__ __forceinline__ void persistent_body(const SimParams &P)
 {
@@ -181,6 +203,9 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
     L.rng.stride = blockDim.x;
     Particle<R> stack[kStackCap];
     WarpQueue Q;
+    // the cascade emits at once: deferred emission (as in the evaporation kernel) measured 2%
+    // slower here, where it holds three more registers across the loop
+    EmitNow em;
     const unsigned long long share = queue_share();
     while (true) {
         const long long t_top = kCount ? clock64() : 0;
@@ -201,7 +226,9 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
         if (__all_sync(FULL, L.phase == kExhausted)) break;
         const unsigned run = __ballot_sync(FULL, L.phase == kEntry || L.phase == kTransport);
         const unsigned kin = __ballot_sync(FULL, L.phase == kKinWait);
-        const bool do_kin = kin && (__popc(kin) >= P.kin_batch || run == 0);
+        // a batch runs once kin_batch lanes wait, or once no more lanes would run transport
+        // than wait (a transport step with few lanes costs the warp as much as with many)
+        const bool do_kin = kin && (__popc(kin) >= P.kin_batch || __popc(kin) >= __popc(run));
         // the iteration's draws: at most 6 in a transport step, 3 in a collision, 2 at an entry.
         // When a lane must generate, every other live lane with room for a block generates one
         // too, so the warp runs the Philox code less often and with more lanes (the words are
@@ -219,7 +246,7 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
             if (L.phase == kKinWait) {
                 if (do_kin) finish_collision<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
             } else if (L.phase == kTransport) {
-                step_transport<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+                step_transport<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C, em);
             } else if (L.phase == kEntry) {
                 step_entry<R, kCount>(P, sh[L.tgt], ts[L.tgt].R, L, C);
             }
@@ -230,7 +257,7 @@ __device__ __forceinline__ void persistent_body(const SimParams &P)
             if (ph == kKinWait && do_kin) finish_collision<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
             __syncwarp();
             long long t1 = clock64();
-            if (ph == kTransport) step_transport<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+            if (ph == kTransport) step_transport<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C, em);
             else if (ph == kEntry) step_entry<R, kCount>(P, sh[L.tgt], ts[L.tgt].R, L, C);
             __syncwarp();
             long long t2 = clock64();
@@ -271,9 +298,12 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
     WidthJob<R> *jobs = jobs0 + warp * kWidthSlots;
     width_t<R, kScaled> *gw0 = reinterpret_cast<width_t<R, kScaled> *>(jobs0 + nwarps * kWidthSlots);
     width_t<R, kScaled> *gw = gw0 + warp * kWidthSlots;
-    R *xms = reinterpret_cast<R *>(gw0 + nwarps * kWidthSlots) + warp * 32;
+    R *xms0 = reinterpret_cast<R *>(gw0 + nwarps * kWidthSlots);
+    R *xms = xms0 + warp * 32;
+    DeferredEmit em = deferred_emitter(reinterpret_cast<unsigned char *>(xms0 + nwarps * 32));
     while (true) {
         const long long t_top = kCount ? clock64() : 0;
+        em.store(P, L.flags);  // the records of the last iteration's emissions
         if (L.phase == kFinish) {
             write_residual(P, L);
             C.add(PNUC_C_DRAWS, L.rng.position() - d0);
@@ -298,7 +328,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
         const long long t1 = kCount ? clock64() : 0;
         const bool stepping = L.phase == kEvap;
         if (stepping) L.rng.ensure(8);
-        step_evap_warp<R, kScaled, kCT, kCount>(P, L, stepping, jobs, gw, xms, C);
+        step_evap_warp<R, kScaled, kCT, kCount>(P, L, stepping, jobs, gw, xms, C, em);
         if (kCount) {
             __syncwarp();
             if (lane == 0) {
@@ -426,7 +456,10 @@ __device__ __forceinline__ void sorted_body(const SimParams &P, Particle<R> *sta
             Particle<R> *stack = my_stack_base + (size_t)slot * kStackCap;
             if (L.rng.left < 8) L.rng.ensure(8);
             if (L.phase == kKinWait) finish_collision<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
-            else if (L.phase == kTransport) step_transport<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C);
+            else if (L.phase == kTransport) {
+                EmitNow em;
+                step_transport<R, kCount, true>(P, sh[L.tgt], ts[L.tgt], L, stack, C, em);
+            }
             else if (L.phase == kEntry) step_entry<R, kCount>(P, sh[L.tgt], ts[L.tgt].R, L, C);
             *lp = L;
         }
@@ -487,7 +520,7 @@ template <typename R, bool kCount>
 cudaError_t launch_persistent(const SimParams &p, int grid, int block, cudaStream_t s)
 {
     if (p.n == 0) return cudaSuccess;
-    size_t smem = smem_bytes<R>(p.n_targets, block);
+    size_t smem = persistent_smem_bytes<R>(p.n_targets, block);
     cudaError_t e = allow_smem(persistent_kernel<R, kCount>, smem);
     if (e != cudaSuccess) return e;
     persistent_kernel<R, kCount><<<grid, block, smem, s>>>(p);
@@ -541,9 +574,9 @@ template <typename R, bool kCount>
 int occupancy_persistent(int block)
 {
     int nb = 0;
-    allow_smem(persistent_kernel<R, kCount>, smem_bytes<R>(kMaxTargets, block));
+    allow_smem(persistent_kernel<R, kCount>, persistent_smem_bytes<R>(kMaxTargets, block));
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<R, kCount>, block,
-                                                  smem_bytes<R>(kMaxTargets, block));
+                                                  persistent_smem_bytes<R>(kMaxTargets, block));
     return nb;
 }
 

@@ -56,6 +56,30 @@ __global__ void ct_table_kernel(double *tab)
     t[6] = ex * (((xx - 3.0) * xx + 6.0) * xx - 6.0) + 6.0;
 }
 
+// The evaporation Q-values of every parent (Z, A) and channel j (paper §2.4): the daughter's
+// mass plus the ejectile's, less the parent's, summed in that order (the same FP64 operations
+// as the evaporation step would do per channel, so the values are the same bits). Rows whose
+// daughter does not exist (Z_d < 1, N_d < 1, A_d < 5) hold 0; the kernels never read them.
+__global__ void q_table_kernel(double *q, const double *mass)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= kMassZ * kMassA) return;
+    const int Z = idx / kMassA, A = idx % kMassA;
+    const double mj[6] = {kEjectileMass[0], kEjectileMass[1], kEjectileMass[2],
+                          kEjectileMass[3], kEjectileMass[4], kEjectileMass[5]};
+    const int zj[6] = {kEjectileZ[0], kEjectileZ[1], kEjectileZ[2], kEjectileZ[3], kEjectileZ[4], kEjectileZ[5]};
+    const int aj[6] = {kEjectileA[0], kEjectileA[1], kEjectileA[2], kEjectileA[3], kEjectileA[4], kEjectileA[5]};
+    double *row = q + (size_t)kQStride * idx;
+    for (int j = 0; j < kQStride; ++j) {
+        double v = 0.0;
+        if (j < 6) {
+            const int Zd = Z - zj[j], Ad = A - aj[j];
+            if (Zd >= 1 && Ad - Zd >= 1 && Ad >= 5 && Z <= A) v = (mass[Zd * kMassA + Ad] + mj[j]) - mass[idx];
+        }
+        row[j] = v;
+    }
+}
+
 __device__ double fermi_density(double r, double c) { return 1.0 / (1.0 + exp((r - c) / 0.545)); }
 
 // One block of 15 warps: warp i integrates r^2 f(r) over shell i, each lane one 1/32 of it
@@ -136,6 +160,13 @@ __global__ void target_table_kernel(TargetTable *dst, int Z, int A, const double
 cudaError_t launch_ct_table(double *tab, cudaStream_t s)
 {
     ct_table_kernel<<<1, 256, 0, s>>>(tab);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_q_table(double *q, const double *mass, cudaStream_t s)
+{
+    const int n = kMassZ * kMassA;
+    q_table_kernel<<<(n + 255) / 256, 256, 0, s>>>(q, mass);
     return cudaGetLastError();
 }
 
