@@ -39,6 +39,13 @@ ENERGY = 200.0
 PAPER_EVENTS_PER_S = 2 * 2.6e6 / (6.61 + 9.77)
 WORKLOAD = "1e6 p-16O + 1e6 p-40Ca at 200 MeV, one batch of 2e6 events per step"
 
+
+def workload_name(n_each: int) -> str:
+    """The workload's name; a run with another --n-each says so."""
+    if n_each == N_EACH:
+        return WORKLOAD
+    return f"{n_each:.3g} p-16O + {n_each:.3g} p-40Ca at 200 MeV, one batch of {2 * n_each:.3g} events per step"
+
 # Algorithmic FP64 operations of the FP32-mode model per counted unit: the operations the
 # model performs in FP64 there (the NN collision boosts, the event's energy/momentum
 # bookkeeping, the evaporation Q-values, and in the FP32 mode the evaporation widths with
@@ -640,7 +647,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_EVENTS_PER_S, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "events_per_step": n, "precision": PRECISION_NOTE["fp32"],
+        "config": {"workload": workload_name(n // 2), "events_per_step": n, "precision": PRECISION_NOTE["fp32"],
                    "method": "persistent (warp refill)", "tuning": ctx.get_tuning("fp32"),
                    "l2": "256 MiB buffer written between steps (inside the timed region)",
                    "parallelism": f"{world} rank(s), event-id ranges, no collective"},
