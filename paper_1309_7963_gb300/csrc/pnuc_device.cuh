@@ -1021,14 +1021,16 @@ __device__ R sample_t(Stream<R> &rng, R a, R x, R b, int max_trials, int &trials
 // sample_t()'s trial on [0, x], kept if t < x - x_x (U above U_x). Returns U, or -1 after
 // max_trials.
 __device__ double width_integral_ct(const double *T, double a, double Y, double b, double *ct_part);
+__device__ double width_integral_ct_f32(const double *T, float a, float Y, float b, float x, double *ct_part);
 
 // T: the daughter's row of M26's constant table (SimParams.ct_table)
 template <typename R>
 __device__ R sample_U_ct(Stream<R> &rng, const double *T, R a, R Y, R b, R x, int max_trials, int &trials)
 {
     const R Ux = to_R<R>(__ldg(&T[0])), k = to_R<R>(__ldg(&T[1])), xx = R(2) * sqrt(a * Ux);
-    double ict;
-    const double itot = width_integral_ct(T, to_d<R>(a), to_d<R>(Y), to_d<R>(b), &ict);
+    double ict, itot;
+    if constexpr (sizeof(R) == 4) itot = width_integral_ct_f32(T, a, Y, b, x, &ict);
+    else itot = width_integral_ct(T, a, Y, b, &ict);
     if (to_d<R>(rng.next()) * itot < ict) {
         const R L = Y < Ux ? Y : Ux, kL = k * L, c0 = k * (Y + b - L);
         const bool small = kL < R(2);
@@ -1183,6 +1185,47 @@ __device__ double width_integral_ct(const double *T, double a, double Y, double 
     return ict + ((F / (4.0 * a * a) + b * G / (2.0 * a)) - below);
 }
 
+// M26's width integral in the FP32 mode (a, Y, b and x = 2 sqrt(aY) in FP32): the same closed
+// forms as width_integral_ct(), with the daughter's constants as FP64 factors (no division)
+// and the exponentials in double precision on the integer pipes (exp_fixed), as M20's widths
+// take them: e^{kY} for kY >= 1 (below 1, e^{kY} - 1 and e^{kY} - 1 - kY by their series in
+// FP32, as M20's series below x = 1), and e^x above U_x (x >= 2.5 there). The Fermi-gas part
+// is M20's integral in its FP32-mode form, e^x A1 + A0 (channel_width_f32_d), less the
+// daughter's constant part below U_x.
+__device__ double width_integral_ct_f32(const double *T, float a, float Y, float b, float x, double *ct_part)
+{
+    const float Ux = d2f(__ldg(&T[0])), k = d2f(__ldg(&T[1]));
+    double ict;
+    if (Y < Ux) {
+        const float z = k * Y;
+        double em1, emm;  // e^z - 1, e^z - 1 - z
+        if (z >= 1.f) {
+            em1 = exp_fixed(z) - 1.0;
+            emm = em1 - f2d(z);
+        } else {
+            float term = z, s = 0.f;  // term = z^n / n!, s = the sum from n = 2
+#pragma unroll 1
+            for (int n = 2; n <= 12; ++n) {
+                term *= z / float(n);
+                s += term;
+            }
+            em1 = f2d(z + s);
+            emm = f2d(s);
+        }
+        ict = __ldg(&T[11]) * (f2d(b) * em1) + __ldg(&T[12]) * emm;
+    } else {
+        ict = __ldg(&T[7]) * f2d(Y + b - Ux) + __ldg(&T[8]);
+    }
+    *ct_part = ict;
+    if (!(Y > Ux)) return ict;
+    const double ex = x < 256.f ? exp_fixed(x) : exp(f2d(x));
+    const float ia = 1.f / a, q = 0.25f * ia * ia, h = 0.5f * b * ia;
+    const float A1 = (x * x - 3.f * x + 3.f) * q + (x - 1.f) * h;
+    const float A0 = (0.5f * x * x - 3.f) * q + h;
+    const double below = f2d(Y + b) * __ldg(&T[9]) - __ldg(&T[10]);
+    return ict + ((ex * f2d(A1) + f2d(A0)) - below);
+}
+
 // The type the six widths of a step are held and drawn in: FP64 (the FP64 mode, and the
 // FP32 mode's widths with FP64 exponentials), or FP32 for the scaled FP32 widths (below).
 template <typename R, bool kScaled>
@@ -1248,11 +1291,14 @@ template <typename R, bool kScaled, bool kCT = false>
 __device__ width_t<R, kScaled> channel_width(const ChanP<R> &c, R xm, const double *ct_table)
 {
     static_assert(!(kScaled && kCT), "the scaled FP32 widths take the Fermi-gas level density");
-    if constexpr (kCT) {  // M26, FP64 in both modes
+    if constexpr (kCT) {  // M26: FP64 widths in both modes (the FP32 mode's from FP32 factors)
         if (!c.open) return 0.0;
         double part;
         const double a = to_d<R>(c.a);
-        return to_d<R>(c.w0) * width_integral_ct(ct_row(ct_table, a), a, to_d<R>(c.Y), to_d<R>(c.b), &part);
+        if constexpr (sizeof(R) == 4)
+            return f2d(c.w0) * width_integral_ct_f32(ct_row(ct_table, a), c.a, c.Y, c.b, c.x, &part);
+        else
+            return c.w0 * width_integral_ct(ct_row(ct_table, a), a, c.Y, c.b, &part);
     } else if constexpr (sizeof(R) == 8) {
         if (!c.open) return 0.0;
         double F, G;

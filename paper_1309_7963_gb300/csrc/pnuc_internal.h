@@ -14,7 +14,7 @@ constexpr int kMaxTargets = 16;  // targets per context
 constexpr int kStackCap = 64;    // particles waiting in one event's cascade
 constexpr int kMassZ = 102;      // nuclide table covers Z in [0, 101]
 constexpr int kMassA = 252;      //                     and A in [0, 251]
-constexpr int kCtStride = 8;     // doubles per daughter in the table of reading M26's constants
+constexpr int kCtStride = 16;    // doubles per daughter in the table of reading M26's constants
 constexpr int kQStride = 8;      // doubles per parent (Z, A) in the Q-value table (six channels used)
 
 // Evaporated ejectiles n, p, d, t, 3He, alpha (paper §2.4: He and lighter): masses (MeV),

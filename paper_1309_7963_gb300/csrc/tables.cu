@@ -33,10 +33,13 @@ __global__ void mass_table_kernel(double *mass, double *cbrtA)
 }
 
 // Reading M26's constants of a daughter of mass number A (a = A/8; the level density is
-// constant-temperature below the matching energy U_x = 2.5 + 150/A MeV): U_x, k = 1/T =
-// sqrt(a / U_x), C = e^{sqrt(a U_x)}, e^{k U_x} - 1, e^{k U_x} - 1 - k U_x (k U_x >= 4.3 for
-// A >= 5, so no series is needed), and with x_x = 2 sqrt(a U_x) the Fermi-gas integrals below
-// U_x, G(x_x) = e^x_x (x_x - 1) + 1 and H(x_x) = e^x_x (x_x^3 - 3 x_x^2 + 6 x_x - 6) + 6.
+// constant-temperature below the matching energy U_x = 2.5 + 150/A MeV): [0] U_x, [1] k = 1/T
+// = sqrt(a / U_x), [2] C = e^{sqrt(a U_x)}, [3] e^{k U_x} - 1, [4] e^{k U_x} - 1 - k U_x (k U_x
+// >= 4.3 for A >= 5, so no series is needed), and with x_x = 2 sqrt(a U_x) the Fermi-gas
+// integrals below U_x, [5] G(x_x) = e^x_x (x_x - 1) + 1 and [6] H(x_x) = e^x_x (x_x^3 - 3 x_x^2
+// + 6 x_x - 6) + 6. The FP32 mode's widths take them as factors, so that they divide by
+// nothing: [7] C [3] / k, [8] C [4] / k^2, [9] [5] / (2a), [10] [6] / (8 a^2), [11] C / k,
+// [12] C / k^2.
 __global__ void ct_table_kernel(double *tab)
 {
     const int A = blockIdx.x * blockDim.x + threadIdx.x;
@@ -54,6 +57,12 @@ __global__ void ct_table_kernel(double *tab)
     t[4] = expm1(kU) - kU;
     t[5] = ex * (xx - 1.0) + 1.0;
     t[6] = ex * (((xx - 3.0) * xx + 6.0) * xx - 6.0) + 6.0;
+    t[7] = t[2] * t[3] / k;
+    t[8] = t[2] * t[4] / (k * k);
+    t[9] = t[5] / (2.0 * a);
+    t[10] = t[6] / (8.0 * a * a);
+    t[11] = t[2] / k;
+    t[12] = t[2] / (k * k);
 }
 
 // The evaporation Q-values of every parent (Z, A) and channel j (paper §2.4): the daughter's
