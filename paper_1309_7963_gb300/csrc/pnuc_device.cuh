@@ -68,6 +68,20 @@ __device__ __forceinline__ void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t
     o3 = c3;
 }
 
+// A Philox block out of line, its four words returned by value (in registers): the
+// evaporation's draws take it, since the evaporation kernel's loop is bound partly by
+// instruction fetch and has three places that may generate (inline, the kernel ran 5%
+// slower); the cascade kernel, with one such place, keeps it inline (1.5% faster).
+struct PhiloxWords {
+    uint64_t w[4];
+};
+__device__ __noinline__ PhiloxWords philox_block(uint64_t c0, uint64_t c1, uint64_t k0)
+{
+    PhiloxWords o;
+    philox4x64_10(c0, c1, k0, 0, o.w[0], o.w[1], o.w[2], o.w[3]);
+    return o;
+}
+
 // One 32-bit half h of a Philox word -> uniform in (0, 1).
 template <typename R> __device__ __forceinline__ R to_uniform(uint32_t h);
 template <> __device__ __forceinline__ double to_uniform<double>(uint32_t h)
@@ -87,7 +101,8 @@ template <> __device__ __forceinline__ float to_uniform<float>(uint32_t h)
 // Converted draws wait in a 32-slot ring in shared memory (slot k of thread t at
 // buf[k * stride], stride = block size: conflict-free). Draws are generated only by
 // ensure(k), which the kernels call once per loop iteration (and the evaporation sampler
-// once per trial), so lanes generate together and the Philox code exists twice.
+// once per trial), so lanes generate together; ensure<true> generates through the
+// out-of-line philox_block().
 constexpr int kRing = 32;
 constexpr int kDrawsPerBlock = 8;
 
@@ -107,12 +122,19 @@ struct Stream {
         head = 0;
     }
     // at least k (<= kRing - kDrawsPerBlock + 1) draws available afterwards
+    template <bool kCall = false>
     __device__ __forceinline__ void ensure(int k)
     {
 #pragma unroll 1
         while (left < k) {
             uint64_t w[4];
-            philox4x64_10(block, event, seed, 0, w[0], w[1], w[2], w[3]);
+            if constexpr (kCall) {
+                const PhiloxWords pw = philox_block(block, event, seed);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) w[q] = pw.w[q];
+            } else {
+                philox4x64_10(block, event, seed, 0, w[0], w[1], w[2], w[3]);
+            }
             ++block;
             const int t = head + left;
 #pragma unroll
@@ -129,7 +151,7 @@ struct Stream {
         block = (uint32_t)(d / kDrawsPerBlock);
         left = 0;
         head = 0;
-        ensure(kDrawsPerBlock);
+        ensure<true>(kDrawsPerBlock);
         head = (int)(d % kDrawsPerBlock);
         left -= (int)(d % kDrawsPerBlock);
     }
@@ -996,7 +1018,7 @@ __device__ R sample_t(Stream<R> &rng, R a, R x, R b, int max_trials, int &trials
     bool small = x < R(2);
     R pmix = small ? W1 * x / (W1 * x + R(2) * W2) : W1 / (W1 + W2);
     for (int k = 0; k < max_trials; ++k) {
-        rng.ensure(6);  // four for this trial, and the two decay angles if it is accepted
+        rng.template ensure<true>(6);  // four for this trial, and the two decay angles if it is accepted
         R um = rng.next(), u1 = rng.next(), u2 = rng.next(), ua = rng.next();
         ++trials;
         bool first = um < pmix;
@@ -1022,6 +1044,7 @@ __device__ R sample_t(Stream<R> &rng, R a, R x, R b, int max_trials, int &trials
 // max_trials.
 __device__ double width_integral_ct(const double *T, double a, double Y, double b, double *ct_part);
 __device__ double width_integral_ct_f32(const double *T, float a, float Y, float b, float x, double *ct_part);
+__device__ __noinline__ double exp_beyond_fixed(float x);
 
 // T: the daughter's row of M26's constant table (SimParams.ct_table)
 template <typename R>
@@ -1036,7 +1059,7 @@ __device__ R sample_U_ct(Stream<R> &rng, const double *T, R a, R Y, R b, R x, in
         const bool small = kL < R(2);
         const R pmix = small ? c0 * kL / (c0 * kL + R(0.5) * kL * kL) : c0 / (c0 + R(1));
         for (int n = 0; n < max_trials; ++n) {
-            rng.ensure(6);  // four for this trial, and the two decay angles if it is accepted
+            rng.template ensure<true>(6);  // four for this trial, and the two decay angles if it is accepted
             const R um = rng.next(), u1 = rng.next(), u2 = rng.next(), ua = rng.next();
             ++trials;
             const bool first = um < pmix;
@@ -1057,7 +1080,7 @@ __device__ R sample_U_ct(Stream<R> &rng, const double *T, R a, R Y, R b, R x, in
     const R pmix = small ? W1 * x / (W1 * x + R(2) * W2) : W1 / (W1 + W2);
     const R tmax = x - xx;
     for (int n = 0; n < max_trials; ++n) {
-        rng.ensure(6);
+        rng.template ensure<true>(6);
         const R um = rng.next(), u1 = rng.next(), u2 = rng.next(), ua = rng.next();
         ++trials;
         const bool first = um < pmix;
@@ -1218,7 +1241,7 @@ __device__ double width_integral_ct_f32(const double *T, float a, float Y, float
     }
     *ct_part = ict;
     if (!(Y > Ux)) return ict;
-    const double ex = x < 256.f ? exp_fixed(x) : exp(f2d(x));
+    const double ex = x < 256.f ? exp_fixed(x) : exp_beyond_fixed(x);
     const float ia = 1.f / a, q = 0.25f * ia * ia, h = 0.5f * b * ia;
     const float A1 = (x * x - 3.f * x + 3.f) * q + (x - 1.f) * h;
     const float A0 = (0.5f * x * x - 3.f) * q + h;
@@ -1254,16 +1277,11 @@ __device__ __forceinline__ W as_width(R x)
 // b (x - 1)/(2a) and A0 = (x^2/2 - 3)/(4a^2) + b/(2a), both FP32; the exponential (up to e^160,
 // beyond FP32's range, and computed on the integer pipes, expfixed.h) and the two products
 // that carry it are FP64. The series below x = 1 needs no exponential and runs in FP32.
-__device__ __forceinline__ double channel_width_f32_d(const ChanP<float> &c)
+// The series below x = 1 (M20) and e^x beyond exp_fixed's range (x >= 256, which no nucleus
+// the library accepts reaches) are rare, and out of line: the evaporation kernel's loop is
+// bound partly by instruction fetch, and with this code inlined it ran 4% slower.
+__device__ __noinline__ double width_series_f32_d(float x, float a, float b, float w0)
 {
-    const float x = c.x;
-    if (x >= 1.f) {
-        const double ex = x < 256.f ? exp_fixed(x) : exp(f2d(x));
-        const float ia = 1.f / c.a, q = 0.25f * ia * ia, h = 0.5f * c.b * ia;
-        const float A1 = (x * x - 3.f * x + 3.f) * q + (x - 1.f) * h;
-        const float A0 = (0.5f * x * x - 3.f) * q + h;
-        return f2d(c.w0) * (ex * f2d(A1) + f2d(A0));
-    }
     double F, G;
     {
         float term = x, f = 0.f, g = 0.f;  // term = x^n / n!
@@ -1276,8 +1294,20 @@ __device__ __forceinline__ double channel_width_f32_d(const ChanP<float> &c)
         F = f2d(f);
         G = f2d(g);
     }
-    const float ia = 1.f / c.a;
-    return f2d(c.w0) * (F * f2d(0.25f * ia * ia) + G * f2d(0.5f * c.b * ia));
+    const float ia = 1.f / a;
+    return f2d(w0) * (F * f2d(0.25f * ia * ia) + G * f2d(0.5f * b * ia));
+}
+__device__ __noinline__ double exp_beyond_fixed(float x) { return exp(f2d(x)); }
+
+__device__ __forceinline__ double channel_width_f32_d(const ChanP<float> &c)
+{
+    const float x = c.x;
+    if (!(x >= 1.f)) return width_series_f32_d(x, c.a, c.b, c.w0);
+    const double ex = x < 256.f ? exp_fixed(x) : exp_beyond_fixed(x);
+    const float ia = 1.f / c.a, q = 0.25f * ia * ia, h = 0.5f * c.b * ia;
+    const float A1 = (x * x - 3.f * x + 3.f) * q + (x - 1.f) * h;
+    const float A0 = (0.5f * x * x - 3.f) * q + h;
+    return f2d(c.w0) * (ex * f2d(A1) + f2d(A0));
 }
 
 // The width of one open channel, FP64 in the FP64 mode and in the FP32 mode (the scale

@@ -327,7 +327,7 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
         if (__all_sync(FULL, L.phase == kExhausted)) break;
         const long long t1 = kCount ? clock64() : 0;
         const bool stepping = L.phase == kEvap;
-        if (stepping) L.rng.ensure(8);
+        if (stepping) L.rng.template ensure<true>(8);
         step_evap_warp<R, kScaled, kCT, kCount>(P, L, stepping, jobs, gw, xms, C, em);
         if (kCount) {
             __syncwarp();
