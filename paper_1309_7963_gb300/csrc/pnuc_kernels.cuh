@@ -54,11 +54,13 @@ __host__ __device__ constexpr size_t persistent_smem_bytes(int n_targets, int bl
     return smem_bytes<R>(n_targets, block);
 }
 
-// the evaporation kernel adds each warp's width-job list after the rings, then the staging slots
+// the evaporation kernel, which reads no shell table: its rings, each warp's width-job list,
+// then the staging slots (45.5 KB for 128-thread FP32 blocks: five blocks fit an SM, where a
+// table region sized for the most targets left room for four)
 template <typename R, bool kScaled = false>
 __host__ __device__ constexpr size_t evap_smem_bytes(int n_targets, int block)
 {
-    return smem_bytes<R>(n_targets, block) +
+    return (size_t)kRing * sizeof(R) * block +
            (size_t)(block / 32) *
                (kWidthSlots * (sizeof(WidthJob<R>) + sizeof(width_t<R, kScaled>)) + 32 * sizeof(R)) +
            kStageBytes * block;
@@ -288,13 +290,13 @@ __device__ __forceinline__ void evap_body(const SimParams &P)
     Lane<R> L;
     L.phase = kIdle;
     L.rng.reset(0, 0);
-    L.rng.buf = ring_base<R>(P, smem);
+    L.rng.buf = reinterpret_cast<R *>(smem) + threadIdx.x;  // the rings first (no tables here)
     L.rng.stride = blockDim.x;
     uint32_t d0 = 0;  // draw index at which the lane's evaporation resumed
     WarpQueue Q;
     const unsigned long long share = queue_share();
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    WidthJob<R> *jobs0 = reinterpret_cast<WidthJob<R> *>(smem + smem_bytes<R>(P.n_targets, blockDim.x));
+    WidthJob<R> *jobs0 = reinterpret_cast<WidthJob<R> *>(smem + (size_t)kRing * sizeof(R) * blockDim.x);
     WidthJob<R> *jobs = jobs0 + warp * kWidthSlots;
     width_t<R, kScaled> *gw0 = reinterpret_cast<width_t<R, kScaled> *>(jobs0 + nwarps * kWidthSlots);
     width_t<R, kScaled> *gw = gw0 + warp * kWidthSlots;
