@@ -153,6 +153,9 @@ pnuc_status launch_batch(pnuc_ctx *ctx, pnuc_precision precision, pnuc_method me
                          const Placement &seg)
 {
     CU(ctx, cudaSetDevice(ctx->cfg.device));
+    // an error an earlier, failed runtime call left pending is not this launch's (errors of
+    // earlier kernels that are sticky still show)
+    (void)cudaGetLastError();
     CU(ctx, cudaMemsetAsync(out->count, 0, sizeof(unsigned long long), s));
     if (batch->n == 0) return PNUC_OK;
     SimParams p;

@@ -501,7 +501,10 @@ cudaError_t launch_evap(const SimParams &p, int grid, int block, cudaStream_t s)
     if (p.n == 0) return cudaSuccess;
     size_t smem = evap_smem_bytes<R, kScaled>(p.n_targets, block);
     cudaError_t e = allow_smem(evap_kernel<R, kCount, kScaled, kCT>, smem);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();  // leave no error pending for the next launch's check
+        return e;
+    }
     evap_kernel<R, kCount, kScaled, kCT><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -512,7 +515,10 @@ cudaError_t launch_plain(const SimParams &p, int block, cudaStream_t s)
     if (p.n == 0) return cudaSuccess;
     size_t smem = smem_bytes<R>(p.n_targets, block);
     cudaError_t e = allow_smem(plain_kernel<R, kCount, kScaled, kCT>, smem);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();  // leave no error pending for the next launch's check
+        return e;
+    }
     unsigned long long grid = (p.n + block - 1) / block;
     plain_kernel<R, kCount, kScaled, kCT><<<(unsigned)grid, block, smem, s>>>(p);
     return cudaGetLastError();
@@ -524,7 +530,10 @@ cudaError_t launch_persistent(const SimParams &p, int grid, int block, cudaStrea
     if (p.n == 0) return cudaSuccess;
     size_t smem = persistent_smem_bytes<R>(p.n_targets, block);
     cudaError_t e = allow_smem(persistent_kernel<R, kCount>, smem);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();  // leave no error pending for the next launch's check
+        return e;
+    }
     persistent_kernel<R, kCount><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
@@ -535,7 +544,10 @@ cudaError_t launch_sorted(const SimParams &p, void *stacks, int grid, int block,
     if (p.n == 0) return cudaSuccess;
     size_t smem = sorted_smem_bytes<R>(p.n_targets, block);
     cudaError_t e = allow_smem(sorted_kernel<R, kCount>, smem);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();  // leave no error pending for the next launch's check
+        return e;
+    }
     sorted_kernel<R, kCount><<<grid, block, smem, s>>>(p, static_cast<Particle<R> *>(stacks));
     return cudaGetLastError();
 }
@@ -545,17 +557,26 @@ cudaError_t launch_kernel(K kernel, size_t smem, const SimParams &p, int grid, i
 {
     if (p.n == 0) return cudaSuccess;
     cudaError_t e = allow_smem(kernel, smem);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();  // leave no error pending for the next launch's check
+        return e;
+    }
     kernel<<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
+// Resident blocks per SM of `kernel` at a block size and dynamic shared memory, 0 when it does
+// not fit. A query that fails (shared memory beyond what a block can have) leaves no error
+// pending, so the next launch's cudaGetLastError() does not report it.
 template <typename K>
 int occupancy_of(K kernel, size_t smem, int block)
 {
     int nb = 0;
-    allow_smem(kernel, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem);
+    if (allow_smem(kernel, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
     return nb;
 }
 
@@ -575,11 +596,7 @@ int occupancy_evap(int block)
 template <typename R, bool kCount>
 int occupancy_persistent(int block)
 {
-    int nb = 0;
-    allow_smem(persistent_kernel<R, kCount>, persistent_smem_bytes<R>(kMaxTargets, block));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<R, kCount>, block,
-                                                  persistent_smem_bytes<R>(kMaxTargets, block));
-    return nb;
+    return occupancy_of(persistent_kernel<R, kCount>, persistent_smem_bytes<R>(kMaxTargets, block), block);
 }
 
 }  // namespace

@@ -50,6 +50,27 @@ def test_invalid_tuning_rejected(ctx):
             ctx.set_tuning("fp32", **bad)
 
 
+def test_a_refused_launch_leaves_the_next_one_clean(ctx):
+    """A launch refused for its tuning (the sorted method's FP64 slots at 512 threads do not fit
+    an SM's shared memory) fails with PNUC_ERR_ARG and leaves no CUDA error behind: the next
+    launch of the same context, with a tuning that fits, succeeds and matches a fresh run."""
+    import torch
+    w = inputs.oxygen_calcium(n_each=2_000)
+    e, t = device_inputs(ctx, w)
+    saved = ctx.get_tuning("fp64")
+    ref = results(ctx.simulate(e, t, seed=5, precision="fp64", method="persistent"))
+    try:
+        ctx.set_tuning("fp64", block_size=512)
+        with pytest.raises(pnuc.PnucError) as err:
+            ctx.simulate(e, t, seed=5, precision="fp64", method="sorted")
+        assert err.value.status == 1  # PNUC_ERR_ARG
+    finally:
+        ctx.set_tuning("fp64", **saved)
+    got = results(ctx.simulate(e, t, seed=5, precision="fp64", method="persistent"))
+    torch.cuda.synchronize()
+    assert same(got, ref)
+
+
 def test_graph_plan_replays_and_updates(ctx):
     import torch
     w = inputs.mixed(20_000, seed=4)
