@@ -424,7 +424,9 @@ pnuc_status pnuc_server_trace_read(pnuc_server *server, pnuc_server_trace_entry 
  *   energy E in [E_min, E_max), Z_final <= Z_max (<= 255) and A_final <= A_max (<= 511):
  *   iE = floor((E - E_min) * sE) with sE = n_E / (E_max - E_min), histogram
  *   [n_E][Z_max + 1][A_max + 1].
- * All bin arithmetic in FP64, each operation rounded to nearest in the order written. Either
+ * The bins are those of FP64 arithmetic, each operation rounded to nearest in the order
+ * written (the kernels decide most of them in FP32 where an error bound proves the same
+ * result, and take the FP64 expression near a bin edge). Either
  * histogram may be NULL (that part is skipped). sec and
  * res/energies are the device arrays of one batch (n_sec records, n events).
  * PNUC_ERR_ARG for a bad spec (empty or inverted ranges, more than 2^28 cells). */

@@ -3,13 +3,16 @@
 // plots (§4.1, Figs. 1-2) and the positron-emitter yields it proposes (§4.2).
 //
 // Both kernels are one streaming pass over the output records: coalesced 16-byte loads
-// (the residual kernel reads only the first 32 bytes of each 64-byte record), per-block
-// shared-memory histograms when the histogram fits, and warp-aggregated 64-bit atomics
-// (lanes that hit the same cell add once) otherwise. The bin arithmetic is FP64 with
-// explicit round-to-nearest operations, so the host can reproduce every bin index; the
-// floors and range tests are taken from the bit fields on the integer pipes.
+// (the residual kernel reads only the first 32 bytes of each 64-byte record), shared-memory
+// counters per block when the histogram fits, and warp-aggregated 64-bit global atomics
+// (lanes that hit the same cell add once) otherwise. The bins are those of FP64
+// arithmetic with each operation rounded to nearest (so the host can reproduce every bin
+// index); the kernels decide almost every bin in FP32 with a proven error bound and fall back
+// to the FP64 expression only near a bin edge (bin_of below), keeping the FP64 pipe, GB300's
+// scarce one, free; floors and range tests come from bit fields on the integer pipes.
 #include <algorithm>
 #include <climits>
+#include <cmath>
 
 #include "api_internal.h"
 #include "fpconv.h"
@@ -20,6 +23,7 @@ namespace {
 constexpr int kTallyBlock = 256;
 constexpr int kSmemBins = 12288;  // 32-bit shared counters per block (48 KB)
 constexpr int kUnroll = 4;        // records in flight per thread
+constexpr int kBlocksPerSM = 4;   // resident blocks per SM
 
 // floor(t) from the bit fields of t on the integer pipes (the FP64 pipe, GB300's scarce one,
 // would otherwise take a conversion and two comparisons per record): -1 for t < 0, INT_MAX
@@ -35,6 +39,43 @@ __device__ __forceinline__ int floor_bits(double t)
     return (int)(m >> (52 - e));
 }
 
+// One axis of a histogram: bin t = RN(RN(x - x0) * s) in FP64, floor taken by floor_bits,
+// bins 0 .. n-1. The FP32 copy of the map decides the bin when it provably agrees.
+struct BinMap {
+    double x0, s;
+    float x0f, sf;   // x0 and s rounded to FP32
+    float errs;      // s * 2^-20 rounded up
+    float abs_err;   // max(s * 2^-120, 2^-126) rounded up
+    int n;
+    int fast;        // 0: every bin from the FP64 expression (parameters outside the proof's range)
+};
+
+// Bin of x (xf: x rounded to FP32 to nearest, or flushed to zero below the smallest normal
+// float). Error bound, with u = 2^-24 and B = s * (|x| + |x0|):
+//   the FP32 value t = RN32(RN32(xf - x0f) * sf) is within 4.0002 u B of the exact (x - x0) s
+//   (relative roundings in xf, x0f, the subtraction, sf and the product), plus less than
+//   2 s 2^-126 + 2^-149 from values below the normal range;
+//   the FP64 value is within 2^-52 B (+ 2^-1074 s) of the exact one.
+// err >= 16 u B (1 - 5u) + abs_err, with abs_err >= max(64 s 2^-126, 2^-126), exceeds the
+// sum by a factor of about 4. So when t lies farther than err from every integer, t and the
+// FP64 value have the same floor; below -err or above n + err both are out of range. The
+// distances t - f and (f + 1) - t are exact for t >= 1/2 (Sterbenz); for 0 <= t < 1/2 the
+// upper distance 1 - t exceeds 1/2 > t > err whenever the lower test passes; a NaN or an
+// infinity fails every comparison. What is left (about 2 err of each unit interval) takes
+// the FP64 expression.
+__device__ __forceinline__ int bin_of(float xf, double x, const BinMap &m)
+{
+    if (m.fast) {
+        const float t = __fmul_rn(__fsub_rn(xf, m.x0f), m.sf);
+        const float err = __fadd_rn(__fmul_rn(__fadd_rn(fabsf(xf), fabsf(m.x0f)), m.errs), m.abs_err);
+        if (__fadd_rn(t, err) < 0.f) return -1;
+        if (__fsub_rn(t, err) > (float)m.n) return m.n;
+        const float f = floorf(t);
+        if (__fsub_rn(t, f) > err && __fsub_rn(__fadd_rn(f, 1.f), t) > err) return (int)f;
+    }
+    return floor_bits(__dmul_rn(__dsub_rn(x, m.x0), m.s));
+}
+
 __device__ __forceinline__ void add_cell(unsigned long long *hist, int idx)
 {
     // lanes of the warp that reach here with the same cell add once
@@ -44,28 +85,31 @@ __device__ __forceinline__ void add_cell(unsigned long long *hist, int idx)
 
 __device__ __forceinline__ void add_cell_shared(unsigned int *cells, int idx)
 {
-    // the same for shared counters: most records fall in a few low-energy bins, and lanes
-    // adding to one address would otherwise serialise
-    const unsigned peers = __match_any_sync(__activemask(), idx);
-    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cells[idx], (unsigned int)__popc(peers));
+    // one shared atomic per record: lanes that add to one address serialise in the atomic
+    // unit, but that costs less than finding them first (__match_any_sync runs on the SM's
+    // address-divergence pipe, which it kept 75% busy; measured 17% slower over the pass)
+    atomicAdd(&cells[idx], 1u);
 }
 
+__host__ __device__ inline int secondary_copies(long nbins) { return 2 * nbins <= kSmemBins ? 2 : 1; }
+
 __global__ void __launch_bounds__(kTallyBlock)
-    secondary_tally_kernel(const uint4 *__restrict__ rec, uint64_t n, double T_min, double sT, int nT, double hc,
-                           int ncos, unsigned long long *hist, int nbins)
+    secondary_tally_kernel(const uint4 *__restrict__ rec, uint64_t n, const BinMap mT, const BinMap mc, int ncos,
+                           unsigned long long *hist, int nbins)
 {
-    // shared counters: one copy per warp when they fit (the low-energy evaporation bins
-    // take most records, so per-warp copies spread the contention), else one per block
+    // shared counters: two copies per block when they fit (odd and even warps), else one;
+    // more copies (one per warp) measured no faster and leave less of the SM's 256 KB to L1
     extern __shared__ unsigned int cells[];
     const bool priv = nbins <= kSmemBins;
-    const int copies = priv && nbins * (kTallyBlock / 32) <= kSmemBins ? kTallyBlock / 32 : 1;
+    const int copies = secondary_copies(nbins);
     const int total = priv ? nbins * copies : 0;
     if (priv) {
         for (int i = threadIdx.x; i < total; i += blockDim.x) cells[i] = 0u;
         __syncthreads();
     }
-    unsigned int *mine = cells + (copies > 1 ? (int)(threadIdx.x >> 5) * nbins : 0);
+    unsigned int *mine = cells + (copies > 1 ? (int)((threadIdx.x >> 5) & 1) * nbins : 0);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const int nT = mT.n;
     // four records in flight per thread: the loads of a group are issued together
     for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kUnroll * stride) {
         uint4 ra[kUnroll], rb[kUnroll];
@@ -85,11 +129,12 @@ __global__ void __launch_bounds__(kTallyBlock)
             const uint4 a = ra[u], b = rb[u];
             const unsigned sp = a.y & 0xffu, org = (a.y >> 8) & 0xffu;
             const double T = __hiloint2double((int)a.w, (int)a.z);
-            const int iT = floor_bits(__dmul_rn(__dsub_rn(T, T_min), sT));
+            const int iT = bin_of(d2f(T), T, mT);
             if (iT < 0 || iT >= nT || sp > 5u || org > 1u) continue;
             int ic = 0;
             if (ncos > 1) {
-                ic = floor_bits(__dmul_rn(__dadd_rn(f2d(__uint_as_float(b.z)), 1.0), hc));
+                const float c = __uint_as_float(b.z);  // x - x0 = uz + 1, exact in FP64
+                ic = bin_of(c, f2d(c), mc);
                 if (ic < 0) ic = 0;
                 if (ic > ncos - 1) ic = ncos - 1;
             }
@@ -110,7 +155,7 @@ __global__ void __launch_bounds__(kTallyBlock)
 
 __global__ void __launch_bounds__(kTallyBlock)
     residual_tally_kernel(const uint4 *__restrict__ res, const double *__restrict__ energies, uint64_t n,
-                          double E_min, double sE, int nE, int Zmax, int Amax, unsigned long long *hist, int nbins)
+                          const BinMap mE, int Zmax, int Amax, unsigned long long *hist, int nbins)
 {
     extern __shared__ unsigned int cells[];
     const bool priv = nbins <= kSmemBins;
@@ -119,6 +164,7 @@ __global__ void __launch_bounds__(kTallyBlock)
         __syncthreads();
     }
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const int nE = mE.n;
     for (uint64_t i0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += kUnroll * stride) {
         uint4 ra[kUnroll], rb[kUnroll];
         double re[kUnroll];
@@ -138,7 +184,7 @@ __global__ void __launch_bounds__(kTallyBlock)
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             if (rb[u].x & (PNUC_FLAG_BAD_INPUT | PNUC_FLAG_ATTEMPT_CAP)) continue;
-            const int iE = floor_bits(__dmul_rn(__dsub_rn(re[u], E_min), sE));
+            const int iE = bin_of(d2f(re[u]), re[u], mE);
             const int Z = (int)(ra[u].y & 0xffffu), A = (int)(ra[u].y >> 16);
             if (iE < 0 || iE >= nE || Z > Zmax || A > Amax) continue;
             const int idx = (iE * (Zmax + 1) + Z) * (Amax + 1) + A;
@@ -153,12 +199,37 @@ __global__ void __launch_bounds__(kTallyBlock)
     }
 }
 
-// two resident blocks per SM: enough loads in flight with four records per thread, and few
-// per-block histograms to add up at the end
+// four resident blocks per SM: the loads in flight are what bounds this pass (two blocks
+// measured 18% slower), while each block's counters are added to the histogram at its end
 int tally_grid(uint64_t n, int sm_count)
 {
     const uint64_t need = (n + kTallyBlock - 1) / kTallyBlock;
-    return (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)sm_count * 2));
+    return (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)sm_count * kBlocksPerSM));
+}
+
+float round_up_f32(double v)
+{
+    float f = (float)v;
+    if ((double)f < v) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+// The map of bin_of, its FP32 decision enabled where the error bound holds: x0 zero or a
+// normal float, s a normal float at least 2^-100 with s * 2^-20 finite, and n < 2^24 (so
+// that n and f + 1 are exact in FP32).
+BinMap bin_map(double x0, double s, int n)
+{
+    BinMap m{};
+    m.x0 = x0;
+    m.s = s;
+    m.n = n;
+    m.x0f = (float)x0;
+    m.sf = (float)s;
+    m.errs = round_up_f32(s * 0x1p-20);
+    m.abs_err = std::max(round_up_f32(s * 0x1p-120), 0x1p-126f);
+    m.fast = std::isfinite(m.x0f) && std::isfinite(m.sf) && std::isfinite(m.errs) && m.sf >= 0x1p-100f &&
+             n < (1 << 24) && (x0 == 0.0 || std::fabs(x0) >= 0x1p-100);
+    return m;
 }
 
 }  // namespace
@@ -184,11 +255,11 @@ extern "C" pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, co
         if (n_secondaries > 0) {
             const double sT = (double)s.n_T / (s.T_max - s.T_min);
             const double hc = 0.5 * (double)s.n_cos;
-            const uint64_t copies = cells * (kTallyBlock / 32) <= (uint64_t)kSmemBins ? kTallyBlock / 32 : 1;
-            const size_t smem = cells <= (uint64_t)kSmemBins ? cells * copies * sizeof(unsigned int) : 0;
+            const size_t smem =
+                cells <= (uint64_t)kSmemBins ? cells * secondary_copies((long)cells) * sizeof(unsigned int) : 0;
             secondary_tally_kernel<<<tally_grid(n_secondaries, ctx->sm_count), kTallyBlock, smem, st>>>(
-                reinterpret_cast<const uint4 *>(secondaries), n_secondaries, s.T_min, sT, s.n_T, hc, s.n_cos,
-                secondary_hist, (int)cells);
+                reinterpret_cast<const uint4 *>(secondaries), n_secondaries, bin_map(s.T_min, sT, s.n_T),
+                bin_map(-1.0, hc, s.n_cos), s.n_cos, secondary_hist, (int)cells);
             CU(ctx, cudaGetLastError());
         }
     }
@@ -202,8 +273,8 @@ extern "C" pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, co
             const double sE = (double)s.n_E / (s.E_max - s.E_min);
             const size_t smem = cells <= (uint64_t)kSmemBins ? cells * sizeof(unsigned int) : 0;
             residual_tally_kernel<<<tally_grid(n, ctx->sm_count), kTallyBlock, smem, st>>>(
-                reinterpret_cast<const uint4 *>(residuals), energies, n, s.E_min, sE, s.n_E, s.Z_max, s.A_max,
-                residual_hist, (int)cells);
+                reinterpret_cast<const uint4 *>(residuals), energies, n, bin_map(s.E_min, sE, s.n_E), s.Z_max,
+                s.A_max, residual_hist, (int)cells);
             CU(ctx, cudaGetLastError());
         }
     }

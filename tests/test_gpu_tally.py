@@ -52,6 +52,54 @@ def test_fp64_tallies_equal_the_oracle_events(ctx):
     assert np.array_equal(rh.cpu().numpy(), want_r)
 
 
+class Records:
+    """records placed by the test (the layout of the library's output)"""
+
+    def __init__(self, sec, res):
+        import torch
+        self.secondaries = torch.from_numpy(sec.view(np.uint8).reshape(len(sec), 32).copy()).cuda()
+        self.residuals = torch.from_numpy(res.view(np.uint8).reshape(len(res), 64).copy()).cuda()
+
+    def n_secondaries(self):
+        return int(self.secondaries.shape[0])
+
+
+def near_edges(rng, lo, hi, n, f32=False):
+    """values on every bin edge of [lo, hi) in n bins and 1-3 ulps either side, plus random ones"""
+    dt = np.float32 if f32 else np.float64
+    e = np.repeat((lo + np.arange(-1, n + 2) * ((hi - lo) / n)).astype(dt), 13)
+    k = np.tile(np.arange(-6, 7), len(e) // 13)
+    x = e.copy()
+    for i in range(len(x)):
+        for _ in range(abs(int(k[i]))):
+            x[i] = np.nextafter(x[i], dt(np.inf) if k[i] > 0 else dt(-np.inf))
+    return np.concatenate([x, rng.uniform(lo - 1, hi + 1, 4000).astype(dt)])
+
+
+@pytest.mark.parametrize("T_range,n_T,n_cos,E_range,n_E", [((0.0, 250.0), 125, 1, (199.0, 201.0), 1),
+                                                           ((0.3, 217.7), 113, 7, (20.0, 250.0), 23),
+                                                           ((-3.0, 41.0), 11, 40, (0.1, 0.7), 3)])
+def test_bins_at_the_edges_equal_the_reference(ctx, T_range, n_T, n_cos, E_range, n_E):
+    import torch
+    rng = np.random.default_rng(n_T)
+    T = near_edges(rng, *T_range, n_T)
+    uz = rng.choice(near_edges(rng, -1.0, 1.0, n_cos, f32=True), len(T)).astype(np.float32)
+    sec = np.zeros(len(T), pnuc.SECONDARY_DTYPE)
+    sec["T"], sec["uz"] = T, uz
+    sec["species"], sec["origin"] = rng.integers(0, 6, len(T)), rng.integers(0, 2, len(T))
+    E = near_edges(rng, *E_range, n_E)
+    res = np.zeros(len(E), pnuc.RESIDUAL_DTYPE)
+    res["Z_final"], res["A_final"] = rng.integers(0, 9, len(E)), rng.integers(0, 17, len(E))
+    res["flags"] = np.where(rng.random(len(E)) < 0.1, 1, 0)
+    r = Records(sec, res)
+    sh, rh = ctx.tally(r, torch.tensor(E, device="cuda"), T_range=T_range, n_T=n_T, n_cos=n_cos, E_range=E_range,
+                       n_E=n_E, Z_max=8, A_max=16)
+    assert np.array_equal(sh.cpu().numpy(), ref.secondary_hist(T, uz, sec["species"], sec["origin"], T_range, n_T,
+                                                               n_cos))
+    assert np.array_equal(rh.cpu().numpy(), ref.residual_hist(res["Z_final"], res["A_final"], res["flags"], E,
+                                                               E_range, n_E, 8, 16))
+
+
 def test_positron_emitter_yields_and_edge_cases(ctx):
     import torch
     w = inputs.fixed(inputs.O16, 200.0, 50_000)
