@@ -4,8 +4,9 @@
 //
 // Both kernels are one streaming pass over the output records: coalesced 16-byte loads
 // (the residual kernel reads only the first 32 bytes of each 64-byte record), shared-memory
-// counters per block when the histogram fits, and warp-aggregated 64-bit global atomics
-// (lanes that hit the same cell add once) otherwise. The bins are those of FP64
+// counters per block when the histogram fits (four 256-thread blocks per SM up to 48 KB of
+// counters, one 1024-thread block per SM up to the block limit of 227 KB), and
+// warp-aggregated 64-bit global atomics (lanes that hit the same cell add once) otherwise. The bins are those of FP64
 // arithmetic with each operation rounded to nearest (so the host can reproduce every bin
 // index); the kernels decide almost every bin in FP32 with a proven error bound and fall back
 // to the FP64 expression only near a bin edge (bin_of below), keeping the FP64 pipe, GB300's
@@ -21,7 +22,7 @@ namespace pnuc {
 namespace {
 
 constexpr int kTallyBlock = 256;
-constexpr int kSmemBins = 12288;  // 32-bit shared counters per block (48 KB)
+constexpr int kSmemBins = 12288;  // 32-bit shared counters of a 256-thread block (48 KB)
 constexpr int kUnroll = 4;        // records in flight per thread
 constexpr int kBlocksPerSM = 4;   // resident blocks per SM
 
@@ -91,18 +92,16 @@ __device__ __forceinline__ void add_cell_shared(unsigned int *cells, int idx)
     atomicAdd(&cells[idx], 1u);
 }
 
-__host__ __device__ inline int secondary_copies(long nbins) { return 2 * nbins <= kSmemBins ? 2 : 1; }
-
-__global__ void __launch_bounds__(kTallyBlock)
+template <int kBlock>
+__global__ void __launch_bounds__(kBlock)
     secondary_tally_kernel(const uint4 *__restrict__ rec, uint64_t n, const BinMap mT, const BinMap mc, int ncos,
-                           unsigned long long *hist, int nbins)
+                           unsigned long long *hist, int nbins, int copies)
 {
     // shared counters: two copies per block when they fit (odd and even warps), else one;
     // more copies (one per warp) measured no faster and leave less of the SM's 256 KB to L1
     extern __shared__ unsigned int cells[];
-    const bool priv = nbins <= kSmemBins;
-    const int copies = secondary_copies(nbins);
-    const int total = priv ? nbins * copies : 0;
+    const bool priv = copies > 0;
+    const int total = nbins * copies;
     if (priv) {
         for (int i = threadIdx.x; i < total; i += blockDim.x) cells[i] = 0u;
         __syncthreads();
@@ -153,12 +152,13 @@ __global__ void __launch_bounds__(kTallyBlock)
     }
 }
 
-__global__ void __launch_bounds__(kTallyBlock)
+template <int kBlock>
+__global__ void __launch_bounds__(kBlock)
     residual_tally_kernel(const uint4 *__restrict__ res, const double *__restrict__ energies, uint64_t n,
-                          const BinMap mE, int Zmax, int Amax, unsigned long long *hist, int nbins)
+                          const BinMap mE, int Zmax, int Amax, unsigned long long *hist, int nbins, int shared)
 {
     extern __shared__ unsigned int cells[];
-    const bool priv = nbins <= kSmemBins;
+    const bool priv = shared != 0;
     if (priv) {
         for (int i = threadIdx.x; i < nbins; i += blockDim.x) cells[i] = 0u;
         __syncthreads();
@@ -199,12 +199,36 @@ __global__ void __launch_bounds__(kTallyBlock)
     }
 }
 
-// four resident blocks per SM: the loads in flight are what bounds this pass (two blocks
-// measured 18% slower), while each block's counters are added to the histogram at its end
-int tally_grid(uint64_t n, int sm_count)
+template <typename K>
+cudaError_t allow_shared(K kernel, size_t bytes)
 {
-    const uint64_t need = (n + kTallyBlock - 1) / kTallyBlock;
-    return (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)sm_count * kBlocksPerSM));
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) (void)cudaGetLastError();  // leave no error pending for the next launch's check
+    return e;
+}
+
+// Launch shape of a pass over n records with a histogram of nbins cells: 256-thread blocks,
+// four per SM, with their counters in shared memory when two copies (else one) fit 48 KB;
+// else one 1024-thread block per SM (the same 32 warps) when one copy fits the block's
+// shared-memory limit; else the 256-thread blocks with global atomics. 32 resident warps per
+// SM keep enough loads in flight (16 measured 18% slower, 48 or 64 no faster); each block
+// adds its counters to the histogram at its end.
+struct TallyShape {
+    int block, grid, copies;
+    size_t smem;
+};
+
+TallyShape tally_shape(uint64_t n, uint64_t nbins, int max_copies, int sm_count, int smem_optin)
+{
+    TallyShape t{kTallyBlock, kBlocksPerSM, 0, 0};
+    if (nbins * max_copies <= (uint64_t)kSmemBins) t.copies = max_copies;
+    else if (nbins <= (uint64_t)kSmemBins) t.copies = 1;
+    else if (nbins * sizeof(unsigned int) <= (uint64_t)smem_optin) t = TallyShape{1024, 1, 1, 0};
+    t.smem = (size_t)(nbins * t.copies) * sizeof(unsigned int);
+    const uint64_t need = (n + t.block - 1) / t.block;
+    t.grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)sm_count * t.grid));
+    return t;
 }
 
 float round_up_f32(double v)
@@ -246,6 +270,8 @@ extern "C" pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, co
     const pnuc_tally_spec &s = *spec;
     cudaStream_t st = (cudaStream_t)stream;
     CU(ctx, cudaSetDevice(ctx->cfg.device));
+    int smem_optin = 0;
+    CU(ctx, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device));
     if (secondary_hist) {
         if (s.n_T < 1 || s.n_cos < 1 || !(s.T_max > s.T_min))
             return fail(ctx, PNUC_ERR_ARG, "secondary tally: bad T bins or range");
@@ -255,11 +281,17 @@ extern "C" pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, co
         if (n_secondaries > 0) {
             const double sT = (double)s.n_T / (s.T_max - s.T_min);
             const double hc = 0.5 * (double)s.n_cos;
-            const size_t smem =
-                cells <= (uint64_t)kSmemBins ? cells * secondary_copies((long)cells) * sizeof(unsigned int) : 0;
-            secondary_tally_kernel<<<tally_grid(n_secondaries, ctx->sm_count), kTallyBlock, smem, st>>>(
-                reinterpret_cast<const uint4 *>(secondaries), n_secondaries, bin_map(s.T_min, sT, s.n_T),
-                bin_map(-1.0, hc, s.n_cos), s.n_cos, secondary_hist, (int)cells);
+            const TallyShape t = tally_shape(n_secondaries, cells, 2, ctx->sm_count, smem_optin);
+            const BinMap mT = bin_map(s.T_min, sT, s.n_T), mc = bin_map(-1.0, hc, s.n_cos);
+            const uint4 *rec = reinterpret_cast<const uint4 *>(secondaries);
+            if (t.block == 1024) {
+                CU(ctx, allow_shared(secondary_tally_kernel<1024>, t.smem));
+                secondary_tally_kernel<1024><<<t.grid, 1024, t.smem, st>>>(rec, n_secondaries, mT, mc, s.n_cos,
+                                                                            secondary_hist, (int)cells, t.copies);
+            } else {
+                secondary_tally_kernel<kTallyBlock><<<t.grid, kTallyBlock, t.smem, st>>>(
+                    rec, n_secondaries, mT, mc, s.n_cos, secondary_hist, (int)cells, t.copies);
+            }
             CU(ctx, cudaGetLastError());
         }
     }
@@ -271,10 +303,17 @@ extern "C" pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, co
         if (n > 0 && (!residuals || !energies)) return fail(ctx, PNUC_ERR_ARG, "null residuals or energies");
         if (n > 0) {
             const double sE = (double)s.n_E / (s.E_max - s.E_min);
-            const size_t smem = cells <= (uint64_t)kSmemBins ? cells * sizeof(unsigned int) : 0;
-            residual_tally_kernel<<<tally_grid(n, ctx->sm_count), kTallyBlock, smem, st>>>(
-                reinterpret_cast<const uint4 *>(residuals), energies, n, bin_map(s.E_min, sE, s.n_E), s.Z_max,
-                s.A_max, residual_hist, (int)cells);
+            const TallyShape t = tally_shape(n, cells, 1, ctx->sm_count, smem_optin);
+            const BinMap mE = bin_map(s.E_min, sE, s.n_E);
+            const uint4 *rr = reinterpret_cast<const uint4 *>(residuals);
+            if (t.block == 1024) {
+                CU(ctx, allow_shared(residual_tally_kernel<1024>, t.smem));
+                residual_tally_kernel<1024><<<t.grid, 1024, t.smem, st>>>(rr, energies, n, mE, s.Z_max, s.A_max,
+                                                                           residual_hist, (int)cells, t.copies);
+            } else {
+                residual_tally_kernel<kTallyBlock><<<t.grid, kTallyBlock, t.smem, st>>>(
+                    rr, energies, n, mE, s.Z_max, s.A_max, residual_hist, (int)cells, t.copies);
+            }
             CU(ctx, cudaGetLastError());
         }
     }

@@ -21,20 +21,24 @@ def run(ctx, w, precision):
     return e, r
 
 
-@pytest.mark.parametrize("n_cos,n_T,n_E", [(1, 125, 2), (4, 125, 2), (40, 125, 23)])  # per-warp, per-block, global
-def test_tally_equals_reference_on_the_same_records(ctx, n_cos, n_T, n_E):
+# counter paths: secondaries 1500 cells (two shared copies per 256-thread block), 12000 (one
+# copy), 30000 (one 1024-thread block per SM), 60000 (global atomics); residuals 4030 cells
+# (256-thread blocks), 46345 (1024-thread blocks), 583,073 (global atomics)
+@pytest.mark.parametrize("n_cos,n_T,n_E,Z_max,A_max", [(1, 125, 2, 30, 64), (8, 125, 23, 30, 64),
+                                                       (20, 125, 1, 30, 64), (40, 125, 23, 100, 250)])
+def test_tally_equals_reference_on_the_same_records(ctx, n_cos, n_T, n_E, Z_max, A_max):
     import torch
     w = inputs.mixed(60_000, seed=8)
     e, r = run(ctx, w, "fp32")
-    sh, rh = ctx.tally(r, e, n_T=n_T, n_cos=n_cos, n_E=n_E, Z_max=30, A_max=64)
+    sh, rh = ctx.tally(r, e, n_T=n_T, n_cos=n_cos, n_E=n_E, Z_max=Z_max, A_max=A_max)
     torch.cuda.synchronize()
     sec, res = r.secondaries_np(), r.residuals_np()
     assert np.array_equal(sh.cpu().numpy(), ref.secondary_hist(sec["T"], sec["uz"], sec["species"], sec["origin"],
                                                                 (0.0, 250.0), n_T, n_cos))
     assert np.array_equal(rh.cpu().numpy(), ref.residual_hist(res["Z_final"], res["A_final"], res["flags"], w.energies,
-                                                               (20.0, 250.0), n_E, 30, 64))
+                                                               (20.0, 250.0), n_E, Z_max, A_max))
     # accumulation: a second call adds the same counts
-    ctx.tally(r, e, n_T=n_T, n_cos=n_cos, n_E=n_E, Z_max=30, A_max=64, hists=(sh, rh))
+    ctx.tally(r, e, n_T=n_T, n_cos=n_cos, n_E=n_E, Z_max=Z_max, A_max=A_max, hists=(sh, rh))
     assert np.array_equal(sh.cpu().numpy(), 2 * ref.secondary_hist(sec["T"], sec["uz"], sec["species"], sec["origin"],
                                                                     (0.0, 250.0), n_T, n_cos))
 
