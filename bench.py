@@ -54,25 +54,26 @@ def workload_name(n_each: int) -> str:
 # Conversions between float and double are not arithmetic (the kernels do them on the integer
 # pipes). The units are the kernels' own counters.
 CASCADE_FP64_OPS = {
-    # pair sums and energies 6, s 4, 1/sqrt(s) 1, 1/E_t 1, beta and gamma 4,
-    # gamma^2/(gamma+1) 3, CM direction 8, p* 1, K 3, CM energies 8, back boost 10, q1 and q2
-    # 6, T1 and T2 6; the Pauli and cutoff tests 4
-    "kinematics": 65,
+    # the FP32 mode's collision (collide_mixed): pair sums 3, E1 and E_t 3, s 4, 1/sqrt(s) 1,
+    # sqrt(s) 1, D = 1/(E_t + sqrt(s)) 2, the CM direction 8, p* 1, K 3, CM energies 4, P.K and
+    # D P.K 4, the boost factors 4, q1 and q2 6, T1 and T2 6; the Pauli tests 2, the cutoffs 4
+    "kinematics": 56,
     "escapes": 5,  # energy and momentum sums of an escaping nucleon
 }
 EVAP_FP64_OPS_COMMON = {
-    "settled": 11,      # E* from the energy balance (p0 with its square root, the sums)
-    "evap_passes": 18,  # six Q-values and excitations X = E* - Q
+    "settled": 11,     # E* from the energy balance (p0 with its square root, the sums)
+    "evap_passes": 6,  # excitations X = E* - Q of the six channels (Q tabulated per parent)
     # the parent's mass + E*, the release, the daughter's mass, and the parent's energy and
     # momentum bookkeeping
     "evap_steps": 9,
 }
 EVAP_FP64_OPS = {
     "fp32": {**EVAP_FP64_OPS_COMMON,
-             # widths in FP64: the exponential 1, F 3, G 2, the width 4 per open channel with
-             # x >= 1 (the series of a channel with x < 1 runs in FP32: the width 4); the sum
-             # of the six and its test 6 per pass, the channel draw 13 per step
-             "evap_exps": 10, "evap_series": 4},
+             # widths in FP64 from FP32 factors: per open channel with x >= 1 the exponential
+             # and w0 (e^x A1 + A0), 3; with x < 1 the series runs in FP32 and the width
+             # w0 (F q + G h) takes 3; the sum of the six and its test 6 per pass, the channel
+             # draw 13 per step
+             "evap_exps": 3, "evap_series": 3},
     # the widths, the channel draw, U_d and the decay with its boost are FP32 arithmetic
     "fp32_scaled": dict(EVAP_FP64_OPS_COMMON),
 }
@@ -663,6 +664,7 @@ def main():
         "phase_split": phase_split,
         "p50_ms": serving["runs"][-1]["p50_ms"] if serving else None,
         "p99_ms": serving["runs"][-1]["p99_ms"] if serving else None,
+        "latency_load": serving["runs"][-1]["load"] if serving else None,  # fraction of capacity
         "serving": serving,
         "e2e": e2e, "roofline": roofline, "cpu_baseline": cb, "clocks": clk, "gpu_launches": 2 * args.steps,
         "tally": tally, "divergence_bound": divergence,
