@@ -580,6 +580,20 @@ def main():
             torch.cuda.synchronize()
             tms.append(a.elapsed_time(b))
         t_ms = float(np.median(tms[3:]))
+        # the paper's Fig. 2 spectra: 1-degree windows at 7.5, 30, 60 and 150 degrees
+        hw = torch.zeros((2, 6, 4, 125), dtype=torch.int64, device="cuda")
+        twm = []
+        for k in range(8):
+            torch.cuda.synchronize()
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.tally_windows(out, hist=hw, n_secondaries=n_sec_out)
+            b.record(stream)
+            torch.cuda.synchronize()
+            twm.append(a.elapsed_time(b))
+        tw_ms = float(np.median(twm[3:]))
+        del hw
         tbytes = 32 * n_sec_out + (32 + 8) * n
         # what DRAM delivers: HBM reads the residual records whole (64 bytes, of which the
         # kernel asks for the first 32), so 72 bytes per event instead of 40
@@ -587,6 +601,8 @@ def main():
         tally = {"ms": t_ms, "algorithmic_bytes": tbytes, "GB_s": tbytes / (t_ms * 1e-3) / 1e9,
                  "hbm_peak_GB_s": hbm_peak, "frac": (tbytes / (t_ms * 1e-3) / 1e9) / hbm_peak if hbm_peak else None,
                  "dram_bytes": dbytes, "dram_GB_s": dbytes / (t_ms * 1e-3) / 1e9,
+                 "fig2_windows": {"ms": tw_ms, "GB_s": 32 * n_sec_out / (tw_ms * 1e-3) / 1e9,
+                                  "spec": "secondaries in 1-degree windows at 7.5, 30, 60, 150 degrees x 125 T bins"},
                  "spec": "secondaries 2 x 6 x 125 T bins (2 MeV, angle-integrated as in the paper's Fig. 1; "
                          "shared-memory counters), residuals 1 x 31 x 65 (Z, A) (shared-memory counters); "
                          "L2 flushed before each launch, the host's launch hidden behind the flush",

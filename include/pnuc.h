@@ -441,6 +441,22 @@ pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, const pnuc_se
                        uint64_t n_secondaries, const pnuc_residual *residuals, const double *energies, uint64_t n,
                        unsigned long long *secondary_hist, unsigned long long *residual_hist, void *stream);
 
+/* Secondary yields in angular windows (paper §4.1, Fig. 2: energy spectra of the secondaries
+ * in narrow windows around fixed laboratory angles). Window k holds the records with
+ *   cos_lo[k] <= uz < cos_hi[k],
+ * uz being the record's direction cosine to the beam (a float, compared exactly with the
+ * double edges); T bins as in pnuc_tally (n_T bins over [T_min, T_max), the bins of FP64
+ * arithmetic). cos_lo and cos_hi are host arrays of n_windows (1 .. PNUC_MAX_WINDOWS) finite
+ * values with cos_lo[k] < cos_hi[k]; windows must not overlap. One pass over the records on
+ * the device, accumulated (+=) into the caller's device histogram of unsigned 64-bit counts
+ * [2 origins][6 species][n_windows][n_T]; records outside every window or the T range are not
+ * counted. Asynchronous on stream. PNUC_ERR_ARG for a bad window list or T range, or a null
+ * pointer with records to count. */
+#define PNUC_MAX_WINDOWS 64
+pnuc_status pnuc_tally_windows(pnuc_ctx *ctx, int32_t n_T, double T_min, double T_max, const double *cos_lo,
+                               const double *cos_hi, int32_t n_windows, const pnuc_secondary *secondaries,
+                               uint64_t n_secondaries, unsigned long long *hist, void *stream);
+
 /* Per-kernel timing of pnuc_simulate's launches (measurement support; the paper has no
  * counterpart). pnuc_kernel_timing(ctx, 1) clears the record and makes later launches
  * through pnuc_simulate and the entry points built on it record CUDA events on the

@@ -92,10 +92,20 @@ __device__ __forceinline__ void add_cell_shared(unsigned int *cells, int idx)
     atomicAdd(&cells[idx], 1u);
 }
 
-template <int kBlock>
+// Angular windows of pnuc_tally_windows: window k holds lo[k] <= uz < hi[k], the edges being
+// the smallest floats at or above the caller's double edges (for a float uz, uz >= c exactly
+// when uz >= that float of c), so the test is two FP32 comparisons and exact.
+struct Windows {
+    float lo[PNUC_MAX_WINDOWS], hi[PNUC_MAX_WINDOWS];
+    int n;
+};
+
+// kWin: the second axis is the window of uz (records in none are skipped), else ncos uniform
+// bins of cos theta (ncos = 1: angle-integrated).
+template <int kBlock, bool kWin>
 __global__ void __launch_bounds__(kBlock)
     secondary_tally_kernel(const uint4 *__restrict__ rec, uint64_t n, const BinMap mT, const BinMap mc, int ncos,
-                           unsigned long long *hist, int nbins, int copies)
+                           const Windows W, unsigned long long *hist, int nbins, int copies)
 {
     // shared counters: two copies per block when they fit (odd and even warps), else one;
     // more copies (one per warp) measured no faster and leave less of the SM's 256 KB to L1
@@ -131,7 +141,16 @@ __global__ void __launch_bounds__(kBlock)
             const int iT = bin_of(d2f(T), T, mT);
             if (iT < 0 || iT >= nT || sp > 5u || org > 1u) continue;
             int ic = 0;
-            if (ncos > 1) {
+            if (kWin) {
+                const float c = __uint_as_float(b.z);
+                ic = -1;
+                for (int k = 0; k < W.n; ++k)
+                    if (c >= W.lo[k] && c < W.hi[k]) {
+                        ic = k;
+                        break;
+                    }
+                if (ic < 0) continue;
+            } else if (ncos > 1) {
                 const float c = __uint_as_float(b.z);  // x - x0 = uz + 1, exact in FP64
                 ic = bin_of(c, f2d(c), mc);
                 if (ic < 0) ic = 0;
@@ -231,6 +250,22 @@ TallyShape tally_shape(uint64_t n, uint64_t nbins, int max_copies, int sm_count,
     return t;
 }
 
+template <bool kWin>
+pnuc_status launch_secondary(pnuc_ctx *ctx, const TallyShape &t, const uint4 *rec, uint64_t n, const BinMap &mT,
+                             const BinMap &mc, int ncos, const Windows &W, unsigned long long *hist, int nbins,
+                             cudaStream_t st)
+{
+    if (t.block == 1024) {
+        CU(ctx, allow_shared(secondary_tally_kernel<1024, kWin>, t.smem));
+        secondary_tally_kernel<1024, kWin><<<t.grid, 1024, t.smem, st>>>(rec, n, mT, mc, ncos, W, hist, nbins, t.copies);
+    } else {
+        secondary_tally_kernel<kTallyBlock, kWin>
+            <<<t.grid, kTallyBlock, t.smem, st>>>(rec, n, mT, mc, ncos, W, hist, nbins, t.copies);
+    }
+    CU(ctx, cudaGetLastError());
+    return PNUC_OK;
+}
+
 float round_up_f32(double v)
 {
     float f = (float)v;
@@ -284,15 +319,9 @@ extern "C" pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, co
             const TallyShape t = tally_shape(n_secondaries, cells, 2, ctx->sm_count, smem_optin);
             const BinMap mT = bin_map(s.T_min, sT, s.n_T), mc = bin_map(-1.0, hc, s.n_cos);
             const uint4 *rec = reinterpret_cast<const uint4 *>(secondaries);
-            if (t.block == 1024) {
-                CU(ctx, allow_shared(secondary_tally_kernel<1024>, t.smem));
-                secondary_tally_kernel<1024><<<t.grid, 1024, t.smem, st>>>(rec, n_secondaries, mT, mc, s.n_cos,
-                                                                            secondary_hist, (int)cells, t.copies);
-            } else {
-                secondary_tally_kernel<kTallyBlock><<<t.grid, kTallyBlock, t.smem, st>>>(
-                    rec, n_secondaries, mT, mc, s.n_cos, secondary_hist, (int)cells, t.copies);
-            }
-            CU(ctx, cudaGetLastError());
+            const pnuc_status ls = launch_secondary<false>(ctx, t, rec, n_secondaries, mT, mc, s.n_cos, Windows{},
+                                                           secondary_hist, (int)cells, st);
+            if (ls != PNUC_OK) return ls;
         }
     }
     if (residual_hist) {
@@ -318,4 +347,36 @@ extern "C" pnuc_status pnuc_tally(pnuc_ctx *ctx, const pnuc_tally_spec *spec, co
         }
     }
     return PNUC_OK;
+}
+
+extern "C" pnuc_status pnuc_tally_windows(pnuc_ctx *ctx, int32_t n_T, double T_min, double T_max, const double *cos_lo,
+                                          const double *cos_hi, int32_t n_windows, const pnuc_secondary *secondaries,
+                                          uint64_t n_secondaries, unsigned long long *hist, void *stream)
+{
+    if (!ctx || !cos_lo || !cos_hi || !hist) return fail(ctx, PNUC_ERR_ARG, "null argument");
+    if (n_T < 1 || !(T_max > T_min)) return fail(ctx, PNUC_ERR_ARG, "window tally: bad T bins or range");
+    if (n_windows < 1 || n_windows > PNUC_MAX_WINDOWS)
+        return fail(ctx, PNUC_ERR_ARG, "window tally: %d windows (1 .. %d)", n_windows, PNUC_MAX_WINDOWS);
+    Windows W{};
+    W.n = n_windows;
+    for (int k = 0; k < n_windows; ++k) {
+        if (!std::isfinite(cos_lo[k]) || !std::isfinite(cos_hi[k]) || !(cos_lo[k] < cos_hi[k]))
+            return fail(ctx, PNUC_ERR_ARG, "window tally: window %d is not a finite [lo, hi) with lo < hi", k);
+        for (int j = 0; j < k; ++j)
+            if (cos_lo[k] < cos_hi[j] && cos_lo[j] < cos_hi[k])
+                return fail(ctx, PNUC_ERR_ARG, "window tally: windows %d and %d overlap", j, k);
+        W.lo[k] = round_up_f32(cos_lo[k]);
+        W.hi[k] = round_up_f32(cos_hi[k]);
+    }
+    const uint64_t cells = 12ull * (uint64_t)n_windows * (uint64_t)n_T;
+    if (cells > (1ull << 28)) return fail(ctx, PNUC_ERR_ARG, "window tally: %llu cells", (unsigned long long)cells);
+    if (n_secondaries == 0) return PNUC_OK;
+    if (!secondaries) return fail(ctx, PNUC_ERR_ARG, "null secondaries");
+    CU(ctx, cudaSetDevice(ctx->cfg.device));
+    int smem_optin = 0;
+    CU(ctx, cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->cfg.device));
+    const TallyShape t = tally_shape(n_secondaries, cells, 2, ctx->sm_count, smem_optin);
+    return launch_secondary<true>(ctx, t, reinterpret_cast<const uint4 *>(secondaries), n_secondaries,
+                                  bin_map(T_min, (double)n_T / (T_max - T_min), n_T), BinMap{}, n_windows, W, hist,
+                                  (int)cells, (cudaStream_t)stream);
 }

@@ -139,6 +139,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
     L.pnuc_kernel_timing.argtypes = [vp, C.c_int32]
     L.pnuc_kernel_times.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(u64)]
     L.pnuc_tally.argtypes = [vp, C.POINTER(pnuc_tally_spec), vp, u64, vp, vp, u64, vp, vp, vp]
+    L.pnuc_tally_windows.argtypes = [vp, C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.c_int32, vp, u64, vp, vp]
     L.pnuc_autotune.argtypes = [vp, C.c_int, C.POINTER(pnuc_batch), C.POINTER(pnuc_output), C.c_int32,
                                 C.POINTER(pnuc_tuning), C.POINTER(C.c_double), vp]
     L.pnuc_save_tuning.argtypes = [vp, C.c_char_p]
@@ -318,6 +320,39 @@ class Context:
                                         _ptr(result.residuals), _ptr(energies), n, _ptr(hists[0]), _ptr(hists[1]),
                                         C.c_void_p(s)))
         return hists
+
+    @staticmethod
+    def angle_windows(angles_deg=(7.5, 30.0, 60.0, 150.0), width_deg: float = 1.0):
+        """cos theta edges of windows theta in (a - w/2, a + w/2] around the given angles
+        (degrees): cos_lo = cos(a + w/2), cos_hi = cos(a - w/2); a window that reaches 0
+        degrees keeps uz = 1."""
+        import math
+        lo, hi = [], []
+        for a in angles_deg:
+            t0, t1 = max(a - 0.5 * width_deg, 0.0), min(a + 0.5 * width_deg, 180.0)
+            lo.append(-1.0 if t1 >= 180.0 else math.cos(math.radians(t1)))
+            hi.append(math.nextafter(1.0, 2.0) if t0 <= 0.0 else math.cos(math.radians(t0)))
+        return lo, hi
+
+    def tally_windows(self, result: "Result", angles_deg=(7.5, 30.0, 60.0, 150.0), width_deg: float = 1.0,
+                      T_range=(0.0, 250.0), n_T=125, hist=None, stream=None, n_secondaries: int | None = None,
+                      cos_edges=None):
+        """pnuc_tally_windows: secondary spectra in angular windows (the paper's Fig. 2), an
+        int64 tensor [2 origins][6 species][windows][n_T] on the device (accumulated into
+        `hist` if given). The windows are angle_windows(angles_deg, width_deg) unless
+        cos_edges = (cos_lo, cos_hi) gives them."""
+        torch = self._torch
+        lo, hi = cos_edges if cos_edges is not None else self.angle_windows(angles_deg, width_deg)
+        k = len(lo)
+        if hist is None:
+            hist = torch.zeros((2, 6, k, n_T), dtype=torch.int64, device=torch.device("cuda", self.device))
+        s = (stream or torch.cuda.current_stream(self.device)).cuda_stream
+        n_sec = min(result.n_secondaries() if n_secondaries is None else n_secondaries,
+                    int(result.secondaries.shape[0]))
+        D = C.c_double * max(k, 1)
+        self._check(self.lib.pnuc_tally_windows(self.handle, n_T, T_range[0], T_range[1], D(*lo), D(*hi), k,
+                                                _ptr(result.secondaries), n_sec, _ptr(hist), C.c_void_p(s)))
+        return hist
 
     def _structs(self, energies, target_ids, seed, first_event_id, out, projectiles=None, event_ids=None):
         b = pnuc_batch(_ptr(energies), _ptr(target_ids), int(energies.shape[0]), seed, first_event_id,

@@ -49,6 +49,7 @@ def test_host_side_status_strings_without_gpu():
     assert lib.pnuc_server_view(None, 1, None, None, None) == 1
     assert lib.pnuc_server_release(None, 1) == 1
     assert lib.pnuc_tally(None, None, None, 0, None, None, 0, None, None, None) == 1
+    assert lib.pnuc_tally_windows(None, 125, 0.0, 250.0, None, None, 4, None, 0, None, None) == 1
 
 
 def test_binding_refuses_without_gpu():

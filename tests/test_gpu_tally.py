@@ -104,6 +104,41 @@ def test_bins_at_the_edges_equal_the_reference(ctx, T_range, n_T, n_cos, E_range
                                                                E_range, n_E, 8, 16))
 
 
+def test_angle_windows_equal_the_reference(ctx):
+    """the Fig. 2 windows (1 degree at 7.5, 30, 60 and 150 degrees) on the library's records,
+    and 40 adjacent windows on records placed at and next to every edge"""
+    import torch
+    w = inputs.mixed(60_000, seed=9)
+    e, r = run(ctx, w, "fp32")
+    h = ctx.tally_windows(r, T_range=(0.0, 250.0), n_T=125)
+    sec = r.secondaries_np()
+    lo, hi = ctx.angle_windows()
+    want = ref.secondary_window_hist(sec["T"], sec["uz"], sec["species"], sec["origin"], (0.0, 250.0), 125, lo, hi)
+    assert want.sum() > 1000
+    assert np.array_equal(h.cpu().numpy(), want)
+    # adjacent windows of 0.05 in cos theta; uz on each edge's float and 1-3 floats either side
+    lo2 = list(np.linspace(-1.0, 0.95, 40))
+    hi2 = lo2[1:] + [1.0]
+    rng = np.random.default_rng(2)
+    uz = near_edges(rng, -1.0, 1.0, 40, f32=True)
+    T = rng.uniform(0.0, 250.0, len(uz))
+    rec = np.zeros(len(uz), pnuc.SECONDARY_DTYPE)
+    rec["T"], rec["uz"] = T, uz
+    rec["species"], rec["origin"] = rng.integers(0, 6, len(uz)), rng.integers(0, 2, len(uz))
+    rr = Records(rec, np.zeros(1, pnuc.RESIDUAL_DTYPE))
+    h2 = ctx.tally_windows(rr, n_T=50, cos_edges=(lo2, hi2))
+    assert np.array_equal(h2.cpu().numpy(), ref.secondary_window_hist(T, uz, rec["species"], rec["origin"],
+                                                                      (0.0, 250.0), 50, lo2, hi2))
+    # accumulation, and bad window lists
+    ctx.tally_windows(rr, n_T=50, cos_edges=(lo2, hi2), hist=h2)
+    assert int(h2.sum()) == 2 * int(ref.secondary_window_hist(T, uz, rec["species"], rec["origin"], (0.0, 250.0), 50,
+                                                               lo2, hi2).sum())
+    for bad in (([0.1, 0.15], [0.2, 0.3]), ([0.3], [0.2]), ([0.0] * 65, [0.1] * 65), ([float("nan")], [0.5])):
+        with pytest.raises(pnuc.PnucError):
+            ctx.tally_windows(rr, cos_edges=bad)
+    torch.cuda.synchronize()
+
+
 def test_positron_emitter_yields_and_edge_cases(ctx):
     import torch
     w = inputs.fixed(inputs.O16, 200.0, 50_000)

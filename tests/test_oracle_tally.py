@@ -37,6 +37,32 @@ def test_secondary_hist_matches_brute_force_and_edges():
     assert h[0, 0, 39, 0] == 1 and h.sum() == 2 and h[1, 1, 0, 1] == 1  # uz = 1 -> last bin; T = 250 out
 
 
+def test_window_hist_matches_brute_force_and_edges():
+    rng = np.random.default_rng(5)
+    n = 4000
+    lo, hi = [0.99, 0.86, -0.2, -0.871], [0.9925, 0.871, 0.1, -0.86]
+    T = rng.uniform(-5, 260, n)
+    uz = rng.uniform(-1, 1, n).astype(np.float32)
+    # values on and next to every edge (as floats), and the ends
+    edges = np.array(lo + hi, np.float64)
+    near = np.concatenate([np.nextafter(edges.astype(np.float32), np.float32(d)) for d in (-2, 2)] +
+                          [edges.astype(np.float32)])
+    uz[:len(near)] = near
+    sp, org = rng.integers(0, 6, n), rng.integers(0, 2, n)
+    got = tally.secondary_window_hist(T, uz, sp, org, (0.0, 250.0), 125, lo, hi)
+    want = np.zeros((2, 6, 4, 125), np.int64)
+    for t, u, a, o in zip(T, uz, sp, org):
+        x = (t - 0.0) * (125 / 250.0)
+        k = [j for j in range(4) if lo[j] <= float(u) < hi[j]]
+        if 0.0 <= x < 125 and k:
+            want[o, a, k[0], math.floor(x)] += 1
+    assert np.array_equal(got, want)
+    # a record on a lower edge counts, on an upper edge not
+    h = tally.secondary_window_hist([10.0, 10.0], [np.float32(0.5), np.float32(0.75)], [0, 0], [0, 0], (0.0, 250.0),
+                                    125, [0.5], [0.75])
+    assert h.sum() == 1 and h[0, 0, 0, 5] == 1
+
+
 def test_residual_hist_filters_and_bins():
     Z = np.array([8, 8, 6, 7, 100, 8])
     A = np.array([15, 15, 11, 13, 250, 15])
