@@ -1,16 +1,18 @@
-// Yield tallies (pnuc_tally): histograms of a batch's secondaries by (origin, species,
-// cos theta, T) and of its residual nuclei by (incident energy, Z, A), the outputs the paper
-// plots (§4.1, Figs. 1-2) and the positron-emitter yields it proposes (§4.2).
+// Yield tallies (pnuc_tally, pnuc_tally_windows): histograms of a batch's secondaries by
+// (origin, species, cos theta or angular window, T) and of its residual nuclei by (incident
+// energy, Z, A), the outputs the paper plots (§4.1, Figs. 1-2) and the positron-emitter
+// yields it proposes (§4.2).
 //
 // Both kernels are one streaming pass over the output records: coalesced 16-byte loads
-// (the residual kernel reads only the first 32 bytes of each 64-byte record), shared-memory
-// counters per block when the histogram fits (four 256-thread blocks per SM up to 48 KB of
-// counters, one 1024-thread block per SM up to the block limit of 227 KB), and
-// warp-aggregated 64-bit global atomics (lanes that hit the same cell add once) otherwise. The bins are those of FP64
-// arithmetic with each operation rounded to nearest (so the host can reproduce every bin
-// index); the kernels decide almost every bin in FP32 with a proven error bound and fall back
-// to the FP64 expression only near a bin edge (bin_of below), keeping the FP64 pipe, GB300's
-// scarce one, free; floors and range tests come from bit fields on the integer pipes.
+// (the residual kernel asks for the first 32 bytes of each 64-byte record, though DRAM
+// returns the whole record), shared-memory counters per block when the histogram fits (four
+// 256-thread blocks per SM up to 48 KB of counters, one 1024-thread block per SM up to the
+// block limit of 227 KB), and warp-aggregated 64-bit global atomics (lanes that hit the same
+// cell add once) otherwise. The bins are those of FP64 arithmetic with each operation rounded
+// to nearest (so the host can reproduce every bin index); the kernels decide almost every bin
+// in FP32 with a proven error bound and fall back to the FP64 expression only near a bin edge
+// (bin_of below), keeping the FP64 pipe, GB300's scarce one, free; floors and range tests
+// come from bit fields on the integer pipes.
 #include <algorithm>
 #include <climits>
 #include <cmath>
