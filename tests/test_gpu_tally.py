@@ -136,6 +136,7 @@ def test_angle_windows_equal_the_reference(ctx):
     for bad in (([0.1, 0.15], [0.2, 0.3]), ([0.3], [0.2]), ([0.0] * 65, [0.1] * 65), ([float("nan")], [0.5])):
         with pytest.raises(pnuc.PnucError):
             ctx.tally_windows(rr, cos_edges=bad)
+    assert int(ctx.tally_windows(ctx.alloc(0)).sum()) == 0  # an empty batch
     torch.cuda.synchronize()
 
 
