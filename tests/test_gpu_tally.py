@@ -155,3 +155,26 @@ def test_positron_emitter_yields_and_edge_cases(ctx):
     assert int(sh.sum()) == 0 and int(rh.sum()) == 0
     with pytest.raises(pnuc.PnucError):
         ctx.tally(r, e, T_range=(10.0, 10.0))
+
+
+def test_full_size_bench_batch_tallies_equal_the_reference(ctx):
+    """the bench's workload (1e6 p-16O + 1e6 p-40Ca at 200 MeV, FP32 persistent, its tuning and
+    output capacity) and the bench's tally specs: every count equal to the reference's"""
+    import torch
+    w = inputs.oxygen_calcium(n_each=1_000_000, energy=200.0)
+    tids = np.array([ctx.create_target(*za) for za in w.targets], np.int32)
+    e = torch.tensor(w.energies, device="cuda")
+    t = torch.tensor(tids[w.tidx], device="cuda")
+    r = ctx.simulate(e, t, seed=w.seed, precision="fp32", method="persistent", capacity=8 * w.n)
+    sh, rh = ctx.tally(r, e, n_T=125, n_cos=1, n_E=1, E_range=(199.0, 201.0), Z_max=30, A_max=64)
+    hw = ctx.tally_windows(r)
+    torch.cuda.synchronize()
+    sec, res = r.secondaries_np(), r.residuals_np()
+    assert len(sec) > 9_000_000
+    assert np.array_equal(sh.cpu().numpy(), ref.secondary_hist(sec["T"], sec["uz"], sec["species"], sec["origin"],
+                                                                (0.0, 250.0), 125, 1))
+    assert np.array_equal(rh.cpu().numpy(), ref.residual_hist(res["Z_final"], res["A_final"], res["flags"], w.energies,
+                                                               (199.0, 201.0), 1, 30, 64))
+    lo, hi = ctx.angle_windows()
+    assert np.array_equal(hw.cpu().numpy(), ref.secondary_window_hist(sec["T"], sec["uz"], sec["species"],
+                                                                       sec["origin"], (0.0, 250.0), 125, lo, hi))
